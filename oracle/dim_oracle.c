@@ -1,0 +1,905 @@
+/*
+ * dim_oracle.c -- plain FP64 CPU oracle of the split time step of the reduced
+ * two-temperature Baer-Nunziato (six-equation) model of Zhang, Menshov, Wang &
+ * Shen, "Diffuse interface relaxation model for two-phase compressible flows
+ * with diffusion processes" (arXiv:2106.00282).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * restatement that the CUDA path is checked against.  Only tests/, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or helper with the CUDA library.
+ *
+ * Every stage follows the paper's order and notation, one loop over cells or
+ * faces per formula, no blocking and no fusion:
+ *   - stiffened-gas EOS, Eqs. (eos_stiffened), (eos_stiffened2), q_k = 0;
+ *   - mixture sound speed c^2 = Y1 c1^2 + Y2 c2^2 (Sec. 3.1);
+ *   - vector form U, F = uU + (a1p1+a2p2)D, R (Eq. vectorForm);
+ *   - Godunov/HLLC update with the non-conservative R term (Sec. 3.1),
+ *     dimensional splitting;
+ *   - PVT-consistent MUSCL: one homogeneous limiter (minmod) for alpha_2 and
+ *     alpha_k rho_k (Sec. 3.6, Eqs. rhostar_high1/2, rec_scheme1/2);
+ *   - viscous step by the local-iteration method (Sec. 3.2);
+ *   - pressure relaxation in the three steps of Sec. 3.3;
+ *   - temperature relaxation (Sec. 3.4.1) as the exact p,T-equilibrium;
+ *   - heat conduction by Algorithm 1 with the Chebyshev local-iteration
+ *     method, Eqs. (LIM), (LIM_last), (ht_eq2_ht), (qk_dis).
+ * Where the paper is silent or inconsistent the reading taken is stated at the
+ * point of use (sign of B2, Chebyshev root order, sign of L_h, face
+ * coefficients, v^(0), ...).
+ *
+ * State layout: 8 planes of nx*ny doubles, cell (i,j) at j*nx+i, planes
+ *   0 m1 = a1 rho1, 1 m2 = a2 rho2, 2 rho u, 3 rho v,
+ *   4 E1 = a1 rho1 e1, 5 E2 = a2 rho2 e2, 6 rho E, 7 alpha_2.
+ * Phase 1 is the dense phase (liquid / solid), phase 2 the gas.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
+ * oracle rounds every operation exactly as written).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NQ 8
+#define ORC_PI 3.14159265358979323846
+
+/* status bits returned by every entry point (0 = fine) */
+#define ORC_NONPHYS 1u /* alpha outside (0,1), m_k <= 0, p+pinf <= 0, T <= 0 */
+#define ORC_NAN 2u
+#define ORC_NOROOT 4u
+#define ORC_TRANSIENT 8u /* a relaxation stage met an inadmissible phase state that a later stage of the
+                          * same step repaired (e.g. the first step at a sharp interface); not an error */
+#define ORC_PCAP 32u /* the formula asked for more than p_max Chebyshev parameters; P = p_max used */
+#define ORC_EINVAL 64u
+
+typedef struct {
+    double gamma[2], pinf[2], cv[2];
+    double k0[2], k_exp, T_ref; /* lambda_k(T) = k0_k (T/T_ref)^k_exp */
+    double mu[2];
+    double cfl;
+    int limiter;  /* 0: first order (no reconstruction), 1: minmod MUSCL */
+    int bc[2];    /* per axis: 0 transmissive, 1 periodic */
+    int trelax;   /* 0: off (no T relaxation, no conduction), 1: equilibrium */
+    int n_outer;  /* outer iterations of Algorithm 1 */
+    int p_policy; /* 0: P by formula, 1: fixed p_fixed, 2: clamp(formula, p_min, p_max) */
+    int p_fixed, p_min, p_max;
+} orc_params;
+
+/* ------------------------------------------------------------------------- */
+/* Thermodynamics: stiffened gas, Eqs. (eos_stiffened), (eos_stiffened2).    */
+/* ------------------------------------------------------------------------- */
+
+/* phase pressure from E_k = a_k rho_k e_k:  p_k = (g_k-1) E_k / a_k - g_k pinf_k */
+static double phase_p(const orc_params *P, int k, double Ek, double ak)
+{
+    return (P->gamma[k] - 1.0) * Ek / ak - P->gamma[k] * P->pinf[k];
+}
+
+/* phase energy per mixture volume from (p, a_k): E_k = a_k (p + g pinf)/(g-1) */
+static double phase_E(const orc_params *P, int k, double p, double ak)
+{
+    return ak * (p + P->gamma[k] * P->pinf[k]) / (P->gamma[k] - 1.0);
+}
+
+/* squared phase sound speed c_k^2 = g_k (p_k + pinf_k) / rho_k  (Eq. AK) */
+static double phase_c2(const orc_params *P, int k, double p, double rho)
+{
+    return P->gamma[k] * (p + P->pinf[k]) / rho;
+}
+
+/* conductivity law lambda_k(T) = k0_k (T / T_ref)^k_exp */
+static double lambda_k(const orc_params *P, int k, double T)
+{
+    double t = T / P->T_ref;
+    double e = P->k_exp;
+    if (e == 0.0) return P->k0[k];
+    if (e == floor(e) && e > 0.0 && e <= 8.0) {
+        double r = t;
+        for (int n = 1; n < (int)e; n++) r = r * t;
+        return P->k0[k] * r;
+    }
+    return P->k0[k] * pow(t, e);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Initial data: (alpha_2, p, T, u, v) with both phases at the cell's (p, T). */
+/* ------------------------------------------------------------------------- */
+unsigned orc_from_primitive(const orc_params *P, int nx, int ny, const double *prim, double *U)
+{
+    int n = nx * ny;
+    unsigned st = 0;
+    for (int c = 0; c < n; c++) {
+        double a2 = prim[0 * n + c], p = prim[1 * n + c], T = prim[2 * n + c];
+        double u = prim[3 * n + c], v = prim[4 * n + c];
+        double a1 = 1.0 - a2;
+        /* Eq. eos_stiffened2 with q = 0: rho_k = (p + pinf_k) / ((g_k - 1) Cv_k T) */
+        double rho1 = (p + P->pinf[0]) / ((P->gamma[0] - 1.0) * P->cv[0] * T);
+        double rho2 = (p + P->pinf[1]) / ((P->gamma[1] - 1.0) * P->cv[1] * T);
+        double m1 = a1 * rho1, m2 = a2 * rho2, rho = m1 + m2;
+        double E1 = phase_E(P, 0, p, a1), E2 = phase_E(P, 1, p, a2);
+        U[0 * n + c] = m1;
+        U[1 * n + c] = m2;
+        U[2 * n + c] = rho * u;
+        U[3 * n + c] = rho * v;
+        U[4 * n + c] = E1;
+        U[5 * n + c] = E2;
+        U[6 * n + c] = E1 + E2 + 0.5 * rho * (u * u + v * v);
+        U[7 * n + c] = a2;
+        if (!(a2 > 0.0 && a2 < 1.0 && T > 0.0 && p + P->pinf[0] > 0.0 && p + P->pinf[1] > 0.0))
+            st |= ORC_NONPHYS;
+    }
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Time step from the CFL condition with the mixture sound speed (Sec. 3.1): */
+/*   dt = cfl / max_cells max_d (|u_d| + c) / h_d  over the active axes.     */
+/* ------------------------------------------------------------------------- */
+static double cell_sound_speed(const orc_params *P, const double *U, int n, int c)
+{
+    double m1 = U[0 * n + c], m2 = U[1 * n + c];
+    double a2 = U[7 * n + c], a1 = 1.0 - a2;
+    double rho = m1 + m2;
+    double p1 = phase_p(P, 0, U[4 * n + c], a1);
+    double p2 = phase_p(P, 1, U[5 * n + c], a2);
+    double c1 = phase_c2(P, 0, p1, m1 / a1);
+    double c2 = phase_c2(P, 1, p2, m2 / a2);
+    /* c^2 = Y1 c1^2 + Y2 c2^2 with Y_k = m_k / rho */
+    return sqrt((m1 * c1 + m2 * c2) / rho);
+}
+
+double orc_dt(const orc_params *P, int nx, int ny, double dx, double dy, const double *U)
+{
+    int n = nx * ny;
+    double smax = 0.0;
+    for (int c = 0; c < n; c++) {
+        double rho = U[0 * n + c] + U[1 * n + c];
+        double cs = cell_sound_speed(P, U, n, c);
+        if (nx > 1) {
+            double s = (fabs(U[2 * n + c] / rho) + cs) / dx;
+            if (s > smax) smax = s;
+        }
+        if (ny > 1) {
+            double s = (fabs(U[3 * n + c] / rho) + cs) / dy;
+            if (s > smax) smax = s;
+        }
+    }
+    return P->cfl / smax;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Hyperbolic sweep along one axis (Sec. 3.1, 3.6).                          */
+/* ------------------------------------------------------------------------- */
+
+/* primitive vector W = (alpha_2, m1, m2, u_n, u_t, p1, p2) of a line cell;
+ * the line-local conserved order is (m1, m2, rho u_n, rho u_t, E1, E2, rhoE, a2) */
+static void line_prims(const orc_params *P, const double *q, double *w)
+{
+    double a2 = q[7], a1 = 1.0 - a2;
+    double rho = q[0] + q[1];
+    w[0] = a2;
+    w[1] = q[0];
+    w[2] = q[1];
+    w[3] = q[2] / rho;
+    w[4] = q[3] / rho;
+    w[5] = phase_p(P, 0, q[4], a1);
+    w[6] = phase_p(P, 1, q[5], a2);
+}
+
+static double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return a < b ? a : b;
+    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+    return 0.0;
+}
+
+typedef struct {
+    double a2, m1, m2, un, ut, rho, p, c;
+    double q[NQ]; /* conserved face state, line-local order */
+} face_state;
+
+/* conserved state and mixture quantities from a reconstructed W */
+static void face_from_w(const orc_params *P, const double *w, face_state *s)
+{
+    double a2 = w[0], a1 = 1.0 - a2;
+    double m1 = w[1], m2 = w[2], un = w[3], ut = w[4], p1 = w[5], p2 = w[6];
+    double rho = m1 + m2;
+    double E1 = phase_E(P, 0, p1, a1), E2 = phase_E(P, 1, p2, a2);
+    double c1 = phase_c2(P, 0, p1, m1 / a1), c2 = phase_c2(P, 1, p2, m2 / a2);
+    s->a2 = a2; s->m1 = m1; s->m2 = m2; s->un = un; s->ut = ut;
+    s->rho = rho;
+    s->p = a1 * p1 + a2 * p2;
+    s->c = sqrt((m1 * c1 + m2 * c2) / rho);
+    s->q[0] = m1; s->q[1] = m2;
+    s->q[2] = rho * un; s->q[3] = rho * ut;
+    s->q[4] = E1; s->q[5] = E2;
+    s->q[6] = E1 + E2 + 0.5 * rho * (un * un + ut * ut);
+    s->q[7] = a2;
+}
+
+/* HLLC solution at xi = x/t = 0 and its flux F(U*) = u* U* + p* D(u*) with
+ * D = [0 0 1 0 0 0 u* 0] (Eq. vectorForm).  Davis wave-speed bounds; across the
+ * acoustic waves the phase masses and phase energies scale like the density
+ * and alpha_2 is unchanged, so an isolated contact is resolved exactly. */
+static void hllc(const face_state *L, const face_state *R, double *F, double *ustar)
+{
+    double SL = fmin(L->un - L->c, R->un - R->c);
+    double SR = fmax(L->un + L->c, R->un + R->c);
+    double Ss = (R->p - L->p + L->rho * L->un * (SL - L->un) - R->rho * R->un * (SR - R->un)) /
+                (L->rho * (SL - L->un) - R->rho * (SR - R->un));
+    double q[NQ], us, ps;
+    const face_state *K;
+    double SK;
+    if (0.0 <= SL) {
+        for (int k = 0; k < NQ; k++) q[k] = L->q[k];
+        us = L->un; ps = L->p;
+    } else if (0.0 <= SR) {
+        if (0.0 <= Ss) { K = L; SK = SL; } else { K = R; SK = SR; }
+        double chi = (SK - K->un) / (SK - Ss);
+        q[0] = chi * K->q[0];
+        q[1] = chi * K->q[1];
+        q[2] = chi * K->rho * Ss;
+        q[3] = chi * K->rho * K->ut;
+        q[4] = chi * K->q[4];
+        q[5] = chi * K->q[5];
+        q[6] = chi * (K->q[6] + (Ss - K->un) * (K->rho * Ss + K->p / (SK - K->un)));
+        q[7] = K->a2;
+        us = Ss;
+        ps = K->p + K->rho * (SK - K->un) * (Ss - K->un);
+    } else {
+        for (int k = 0; k < NQ; k++) q[k] = R->q[k];
+        us = R->un; ps = R->p;
+    }
+    F[0] = us * q[0];
+    F[1] = us * q[1];
+    F[2] = us * q[2] + ps;
+    F[3] = us * q[3];
+    F[4] = us * q[4];
+    F[5] = us * q[5];
+    F[6] = us * (q[6] + ps);
+    F[7] = us * q[7];
+    *ustar = us;
+}
+
+/* one line of n cells, ext holds n+4 cells (2 ghosts per side) in the
+ * line-local order, 8 values per cell; out receives the n updated cells */
+static void line_update(const orc_params *P, int n, double dtdx, const double *ext, double *out)
+{
+    int ne = n + 4;
+    double *W = (double *)malloc(sizeof(double) * 7 * ne);
+    double *S = (double *)calloc(7 * ne, sizeof(double));
+    double *F = (double *)malloc(sizeof(double) * NQ * (n + 1));
+    double *us = (double *)malloc(sizeof(double) * (n + 1));
+    for (int e = 0; e < ne; e++) line_prims(P, ext + NQ * e, W + 7 * e);
+    /* MUSCL slopes: sigma_e = minmod(W_e - W_{e-1}, W_{e+1} - W_e) on every
+     * component of W, the same limiter for alpha_2 and m_k (Sec. 3.6) */
+    if (P->limiter == 1)
+        for (int e = 1; e <= n + 2; e++)
+            for (int k = 0; k < 7; k++)
+                S[7 * e + k] = minmod(W[7 * e + k] - W[7 * (e - 1) + k], W[7 * (e + 1) + k] - W[7 * e + k]);
+    /* face f (f = 0..n) lies between extended cells f+1 and f+2 */
+    for (int f = 0; f <= n; f++) {
+        double wl[7], wr[7];
+        face_state sl, sr;
+        for (int k = 0; k < 7; k++) {
+            wl[k] = W[7 * (f + 1) + k] + 0.5 * S[7 * (f + 1) + k];
+            wr[k] = W[7 * (f + 2) + k] - 0.5 * S[7 * (f + 2) + k];
+        }
+        face_from_w(P, wl, &sl);
+        face_from_w(P, wr, &sr);
+        hllc(&sl, &sr, F + NQ * f, us + f);
+    }
+    /* Godunov update with the non-conservative term R(U_i^n)(u*_{i+1/2} - u*_{i-1/2}),
+     * R = [0 0 0 0 a1p1 a2p2 0 -a2] (Sec. 3.1) */
+    for (int i = 0; i < n; i++) {
+        const double *q = ext + NQ * (i + 2);
+        const double *w = W + 7 * (i + 2);
+        double a2 = w[0], a1 = 1.0 - a2;
+        double Rv[NQ] = {0.0, 0.0, 0.0, 0.0, a1 * w[5], a2 * w[6], 0.0, -a2};
+        double du = us[i + 1] - us[i];
+        for (int k = 0; k < NQ; k++)
+            out[NQ * i + k] = q[k] - dtdx * (F[NQ * (i + 1) + k] - F[NQ * i + k]) - dtdx * Rv[k] * du;
+    }
+    free(W); free(S); free(F); free(us);
+}
+
+/* ghost index of extended position e (0..n+3) of a line of n cells */
+static int ghost_src(int e, int n, int bc)
+{
+    int i = e - 2;
+    if (i >= 0 && i < n) return i;
+    if (bc == 1) return ((i % n) + n) % n;
+    return i < 0 ? 0 : n - 1;
+}
+
+/* one directional sweep (axis 0: x, 1: y) without relaxation */
+unsigned orc_sweep(const orc_params *P, int nx, int ny, double dx, double dy, int axis, double dt, double *U)
+{
+    int n = nx * ny;
+    int len = axis == 0 ? nx : ny, nlines = axis == 0 ? ny : nx;
+    double h = axis == 0 ? dx : dy;
+    int qn = axis == 0 ? 2 : 3, qt = axis == 0 ? 3 : 2;
+    int map[NQ] = {0, 1, qn, qt, 4, 5, 6, 7};
+    double *ext = (double *)malloc(sizeof(double) * NQ * (len + 4));
+    double *out = (double *)malloc(sizeof(double) * NQ * len);
+    for (int l = 0; l < nlines; l++) {
+        for (int e = 0; e < len + 4; e++) {
+            int i = ghost_src(e, len, P->bc[axis]);
+            int c = axis == 0 ? l * nx + i : i * nx + l;
+            for (int k = 0; k < NQ; k++) ext[NQ * e + k] = U[map[k] * n + c];
+        }
+        line_update(P, len, dt / h, ext, out);
+        for (int i = 0; i < len; i++) {
+            int c = axis == 0 ? l * nx + i : i * nx + l;
+            for (int k = 0; k < NQ; k++) U[map[k] * n + c] = out[NQ * i + k];
+        }
+    }
+    free(ext); free(out);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Instantaneous pressure relaxation, the three steps of Sec. 3.3.           */
+/* ------------------------------------------------------------------------- */
+/* (1) with p_I equal to the relaxed pressure p, dE_k = -p da_k and the SG EOS
+ *     give a_k(p) = (g_k-1)(E_k^0 + p a_k^0) / (g_k (p + pinf_k)); the
+ *     saturation sum a_1(p) + a_2(p) = 1 is a quadratic A p^2 + B p + C = 0
+ *     whose larger root is the unique one with p + pinf_k > 0 for both k;
+ * (2) p2 = p(a^(1), rho e) from the mixture energy rho e = rho E - |rho u|^2/(2 rho);
+ * (3) E_k = E_k(p2, a_k^(1)). */
+static unsigned prelax_cell(const orc_params *P, double *U, int n, int c)
+{
+    unsigned st = 0;
+    double g1 = P->gamma[0], g2 = P->gamma[1], pi1 = P->pinf[0], pi2 = P->pinf[1];
+    double m1 = U[0 * n + c], m2 = U[1 * n + c];
+    double a2 = U[7 * n + c], a1 = 1.0 - a2;
+    double E1 = U[4 * n + c], E2 = U[5 * n + c];
+    /* a_k(p) = (ak + bk p) / (dk p + ek) */
+    double ak1 = (g1 - 1.0) * E1, bk1 = (g1 - 1.0) * a1, dk1 = g1, ek1 = g1 * pi1;
+    double ak2 = (g2 - 1.0) * E2, bk2 = (g2 - 1.0) * a2, dk2 = g2, ek2 = g2 * pi2;
+    double A = dk1 * dk2 - bk1 * dk2 - bk2 * dk1;
+    double B = dk1 * ek2 + ek1 * dk2 - (ak1 * dk2 + bk1 * ek2 + ak2 * dk1 + bk2 * ek1);
+    double C = ek1 * ek2 - ak1 * ek2 - ak2 * ek1;
+    double disc = B * B - 4.0 * A * C;
+    if (disc < 0.0) { st |= ORC_NOROOT; disc = 0.0; }
+    double sq = sqrt(disc);
+    double p = B <= 0.0 ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
+    double a2n = (ak2 + bk2 * p) / (dk2 * p + ek2);
+    double a1n = 1.0 - a2n;
+    /* step (2): pressure from the conservative mixture energy */
+    double rho = m1 + m2;
+    double mu = U[2 * n + c], mv = U[3 * n + c];
+    double rhoe = U[6 * n + c] - 0.5 * (mu * mu + mv * mv) / rho;
+    double p2 = (rhoe - (a1n * g1 * pi1 / (g1 - 1.0) + a2n * g2 * pi2 / (g2 - 1.0))) /
+                (a1n / (g1 - 1.0) + a2n / (g2 - 1.0));
+    /* step (3) */
+    U[4 * n + c] = phase_E(P, 0, p2, a1n);
+    U[5 * n + c] = phase_E(P, 1, p2, a2n);
+    U[7 * n + c] = a2n;
+    if (!(a2n > 0.0 && a2n < 1.0 && m1 > 0.0 && m2 > 0.0 && p2 + pi1 > 0.0 && p2 + pi2 > 0.0))
+        st |= ORC_NONPHYS;
+    if (isnan(p2) || isnan(a2n)) st |= ORC_NAN;
+    return st;
+}
+
+unsigned orc_prelax(const orc_params *P, int ncell, double *U)
+{
+    unsigned st = 0;
+    for (int c = 0; c < ncell; c++) st |= prelax_cell(P, U, ncell, c);
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Temperature relaxation (Sec. 3.4.1): exact p,T equilibrium.              */
+/* ------------------------------------------------------------------------- */
+/* At fixed m_k (C_k = m_k Cv_k) and fixed rho e the SG phase energies are
+ * E_k = C_k T_k + a_k pinf_k, so with T1 = T2 = T
+ *   rho e = C T + pinf_1 - B1 alpha,  C = C1 + C2,  B1 = pinf_1 - pinf_2,
+ * and p1 = p2 reads  G1 C1 T/(1-alpha) - G2 C2 T/alpha = B1  (G_k = g_k - 1).
+ * Eliminating T gives  qa alpha^2 + qb alpha + qc = 0 with
+ *   qa = B1 (G + C), qb = E G - B1 G2C2 - C B1, qc = -E G2C2,
+ *   G = G1C1 + G2C2, E = rho e - pinf_1;
+ * the admissible root (alpha in (0,1), T > 0) is (sqrt(disc) - qb)/(2 qa) for
+ * either sign of qa, evaluated without cancellation.  This is the state the
+ * relaxation ODEs (ht_eq2_TR), (ht_eq3_TR) drive to, with B2 taken with the
+ * sign that keeps p1 = p2 along the path (B2 = pinf_2 - p/r0). */
+static unsigned equilibrium(const orc_params *P, double m1, double m2, double rhoe, double *T, double *a2)
+{
+    double C1 = m1 * P->cv[0], C2 = m2 * P->cv[1], C = C1 + C2;
+    double G1C1 = (P->gamma[0] - 1.0) * C1, G2C2 = (P->gamma[1] - 1.0) * C2, G = G1C1 + G2C2;
+    double B1 = P->pinf[0] - P->pinf[1];
+    double E = rhoe - P->pinf[0];
+    double qa = B1 * (G + C);
+    double qb = E * G - B1 * G2C2 - C * B1;
+    double qc = -E * G2C2;
+    double disc = qb * qb - 4.0 * qa * qc;
+    unsigned st = 0;
+    if (disc < 0.0) { st |= ORC_NOROOT; disc = 0.0; }
+    double sq = sqrt(disc);
+    double a = qb > 0.0 ? (-2.0 * qc) / (qb + sq) : (sq - qb) / (2.0 * qa);
+    *a2 = a;
+    *T = (E + B1 * a) / C;
+    if (!(a > 0.0 && a < 1.0 && *T > 0.0)) st |= ORC_NONPHYS;
+    if (isnan(a) || isnan(*T)) st |= ORC_NAN;
+    return st;
+}
+
+/* mixture temperature of a cell in thermal equilibrium, from the energy:
+ * rho e = C T + a1 pinf_1 + a2 pinf_2  (Eq. Taverage with T1 = T2) */
+static double cell_T(const orc_params *P, const double *U, int n, int c)
+{
+    double a2 = U[7 * n + c], a1 = 1.0 - a2;
+    double C = U[0 * n + c] * P->cv[0] + U[1 * n + c] * P->cv[1];
+    return (U[4 * n + c] + U[5 * n + c] - a1 * P->pinf[0] - a2 * P->pinf[1]) / C;
+}
+
+unsigned orc_trelax(const orc_params *P, int ncell, double *U)
+{
+    unsigned st = 0;
+    int n = ncell;
+    for (int c = 0; c < n; c++) {
+        double m1 = U[0 * n + c], m2 = U[1 * n + c];
+        double rhoe = U[4 * n + c] + U[5 * n + c];
+        double T, a2;
+        st |= equilibrium(P, m1, m2, rhoe, &T, &a2);
+        U[4 * n + c] = m1 * P->cv[0] * T + (1.0 - a2) * P->pinf[0];
+        U[5 * n + c] = m2 * P->cv[1] * T + a2 * P->pinf[1];
+        U[7 * n + c] = a2;
+    }
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Chebyshev local-iteration method (Sec. 3.2, Eqs. LIM, LIM_last).           */
+/* ------------------------------------------------------------------------- */
+/* P = ceil(pi/4 sqrt(tau lambda_max + 1)) (Sec. 3.2), then the policy: fixed P,
+ * or clamp to [p_min, p_max].  The formula is capped at p_max as well: with the
+ * paper's parameter order the roundoff of the recurrence grows with P
+ * (intermediate factors reach tau lambda_max), so large P is not usable in
+ * finite precision. */
+static int cheb_P_formula(double tau, double lam_max)
+{
+    return (int)ceil(ORC_PI / 4.0 * sqrt(tau * lam_max + 1.0));
+}
+
+int orc_cheb_P(const orc_params *P, double tau, double lam_max)
+{
+    int pf = cheb_P_formula(tau, lam_max);
+    if (P->p_policy == 1) return P->p_fixed;
+    if (P->p_policy == 2 && pf < P->p_min) pf = P->p_min;
+    if (pf > P->p_max) pf = P->p_max;
+    return pf;
+}
+
+static unsigned cheb_capped(const orc_params *P, double tau, double lam_max, int Pn)
+{
+    return (P->p_policy != 1 && Pn < cheb_P_formula(tau, lam_max)) ? ORC_PCAP : 0u;
+}
+
+/* b_1..b_{2P-1} = (a_P .. a_2, a_P .. a_1), a_m = lam (beta_1 - beta_m)/(1 + beta_1),
+ * beta_m = cos((2m-1) pi / (2P)) the roots of T_P.  The roots are taken in their
+ * natural (decreasing) order so that beta_1 is the largest and every a_m >= 0
+ * (the ascending order the text names makes a_m negative and the iteration
+ * unstable). */
+void orc_cheb_schedule(int Pn, double lam, double *b)
+{
+    double *beta = (double *)malloc(sizeof(double) * (Pn + 1));
+    double *a = (double *)malloc(sizeof(double) * (Pn + 1));
+    for (int m = 1; m <= Pn; m++) beta[m] = cos((2.0 * m - 1.0) * ORC_PI / (2.0 * Pn));
+    for (int m = 1; m <= Pn; m++) a[m] = lam * (beta[1] - beta[m]) / (1.0 + beta[1]);
+    for (int s = 0; s < Pn - 1; s++) b[s] = a[Pn - s];
+    for (int s = 0; s < Pn; s++) b[Pn - 1 + s] = a[Pn - s];
+    free(beta); free(a);
+}
+
+/* Discrete operator L_h v = div(Lam grad v) in flux-difference form (Eq. qk_dis):
+ * (L v)_i = Fx_{i+1/2} - Fx_{i-1/2} + Fy_{j+1/2} - Fy_{j-1/2},
+ * F_{i+1/2} = Lam_{i+1/2} (v_{i+1} - v_i) / h^2; Lam on faces is given.
+ * Face arrays: lx[j*(nx+1)+i] is the face left of cell i, ly[j*nx+i] the face
+ * below cell (i,j) (ny+1 rows).  Transmissive walls carry zero face
+ * coefficient; periodic axes wrap.  An axis of extent 1 is inactive. */
+typedef struct {
+    int nx, ny;
+    double dx, dy;
+    int bc[2];
+    double *lx, *ly;
+} orc_op;
+
+static void op_apply(const orc_op *o, const double *v, double *out)
+{
+    int nx = o->nx, ny = o->ny;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            double r = 0.0;
+            if (nx > 1) {
+                int il = i == 0 ? nx - 1 : i - 1, ir = i == nx - 1 ? 0 : i + 1;
+                double fl = o->lx[j * (nx + 1) + i] * (v[j * nx + i] - v[j * nx + il]) / (o->dx * o->dx);
+                double fr = o->lx[j * (nx + 1) + i + 1] * (v[j * nx + ir] - v[j * nx + i]) / (o->dx * o->dx);
+                r += fr - fl;
+            }
+            if (ny > 1) {
+                int jl = j == 0 ? ny - 1 : j - 1, jr = j == ny - 1 ? 0 : j + 1;
+                double fl = o->ly[j * nx + i] * (v[j * nx + i] - v[jl * nx + i]) / (o->dy * o->dy);
+                double fr = o->ly[(j + 1) * nx + i] * (v[jr * nx + i] - v[j * nx + i]) / (o->dy * o->dy);
+                r += fr - fl;
+            }
+            out[j * nx + i] = r;
+        }
+}
+
+/* face coefficients as the arithmetic mean of the two cell values (the paper
+ * does not specify Lam_{k,i+1/2}); zero on transmissive walls */
+static void op_faces(orc_op *o, const double *lam)
+{
+    int nx = o->nx, ny = o->ny;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i <= nx; i++) {
+            double v;
+            if (i == 0 || i == nx)
+                v = o->bc[0] == 1 ? 0.5 * (lam[j * nx + nx - 1] + lam[j * nx + 0]) : 0.0;
+            else
+                v = 0.5 * (lam[j * nx + i - 1] + lam[j * nx + i]);
+            o->lx[j * (nx + 1) + i] = v;
+        }
+    for (int j = 0; j <= ny; j++)
+        for (int i = 0; i < nx; i++) {
+            double v;
+            if (j == 0 || j == ny)
+                v = o->bc[1] == 1 ? 0.5 * (lam[(ny - 1) * nx + i] + lam[i]) : 0.0;
+            else
+                v = 0.5 * (lam[(j - 1) * nx + i] + lam[j * nx + i]);
+            o->ly[j * nx + i] = v;
+        }
+}
+
+/* Gershgorin bound of the spectrum of A = -V L_h: max_i 2 V_i sum_f Lam_f / h_f^2 */
+static double op_lam_max(const orc_op *o, const double *V)
+{
+    int nx = o->nx, ny = o->ny;
+    double lm = 0.0;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            double s = 0.0;
+            if (nx > 1) s += (o->lx[j * (nx + 1) + i] + o->lx[j * (nx + 1) + i + 1]) / (o->dx * o->dx);
+            if (ny > 1) s += (o->ly[j * nx + i] + o->ly[(j + 1) * nx + i]) / (o->dy * o->dy);
+            double r = 2.0 * V[j * nx + i] * s;
+            if (r > lm) lm = r;
+        }
+    return lm;
+}
+
+/* The first 2P-2 local iterations of Eq. (LIM) for dv/dt = V L_h v:
+ *   v^(m) = (v^n + tau b_m v^(m-1) + tau V L_h v^(m-1)) / (1 + tau b_m),
+ * v^(0) = v^n; L_h is the (negative semi-definite) discrete diffusion operator,
+ * so the sweeps add +tau V L_h (Sec. 3.2's "-tau L_h" is written for the
+ * positive operator -L_h).  Returns the predictor u_hat = v^(2P-2); the final,
+ * explicit sweep (b_{2P-1} = 0, Eq. LIM_last) is applied by the caller in
+ * conservative form. */
+static void lim_predict(const orc_op *o, int Pn, const double *b, double tau, const double *V,
+                        const double *v0, double *uhat)
+{
+    int n = o->nx * o->ny;
+    double *cur = (double *)malloc(sizeof(double) * n);
+    double *nxt = (double *)malloc(sizeof(double) * n);
+    double *Lv = (double *)malloc(sizeof(double) * n);
+    memcpy(cur, v0, sizeof(double) * n);
+    for (int m = 1; m <= 2 * Pn - 2; m++) {
+        double bm = b[m - 1];
+        op_apply(o, cur, Lv);
+        for (int c = 0; c < n; c++)
+            nxt[c] = (v0[c] + tau * bm * cur[c] + tau * V[c] * Lv[c]) / (1.0 + tau * bm);
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    memcpy(uhat, cur, sizeof(double) * n);
+    free(cur); free(nxt); free(Lv);
+}
+
+/* exported for tests: one complete LIM solve (2P-1 iterations, the last one
+ * explicit) of dv/dt = V L_h v with cell coefficient lam, returns P */
+int orc_lim_solve(const orc_params *P, int nx, int ny, double dx, double dy, double tau,
+                  const double *lam, const double *V, const double *v0, double *v1, double *lam_max_out)
+{
+    int n = nx * ny;
+    orc_op o = {nx, ny, dx, dy, {P->bc[0], P->bc[1]}, NULL, NULL};
+    o.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
+    o.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+    op_faces(&o, lam);
+    double lm = op_lam_max(&o, V);
+    int Pn = orc_cheb_P(P, tau, lm);
+    double *b = (double *)malloc(sizeof(double) * (2 * Pn - 1));
+    orc_cheb_schedule(Pn, lm, b);
+    double *uh = (double *)malloc(sizeof(double) * n);
+    double *Lu = (double *)malloc(sizeof(double) * n);
+    lim_predict(&o, Pn, b, tau, V, v0, uh);
+    op_apply(&o, uh, Lu);
+    for (int c = 0; c < n; c++) v1[c] = v0[c] + tau * V[c] * Lu[c];
+    if (lam_max_out) *lam_max_out = lm;
+    free(o.lx); free(o.ly); free(b); free(uh); free(Lu);
+    return Pn;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Heat conduction under p,T equilibrium: Algorithm 1 with the LIM.         */
+/* ------------------------------------------------------------------------- */
+/* On the equilibrium manifold rho e = C T + pinf_1 - B1 alpha with p1 = p2, so
+ * dT/d(rho e) = V = 1 / (C + B1^2 / K), K = T sum_k (p + pinf_k)/alpha_k,
+ * d alpha/d(rho e) = -B1 V / K, and q1 + q2 = div(Lam grad T), Lam = a1 l1 + a2 l2.
+ * Eq. (ht_eq2_ht) is then dT/dt = V L_h T.  Each outer iteration freezes V and
+ * Lam at the latest (T, alpha), runs the 2P-2 predictor sweeps from T^n, and
+ * applies the last (explicit) sweep conservatively to the mixture energy:
+ * rho E += tau L_h u_hat, rho e += tau L_h u_hat, followed by the projection
+ * (T, alpha) = equilibrium(m1, m2, rho e) and E_k = C_k T + a_k pinf_k. */
+unsigned orc_heat(const orc_params *P, int nx, int ny, double dx, double dy, double tau, double *U, int *P_used)
+{
+    int n = nx * ny;
+    unsigned st = 0;
+    double B1 = P->pinf[0] - P->pinf[1];
+    double *T0 = (double *)malloc(sizeof(double) * n);
+    double *re0 = (double *)malloc(sizeof(double) * n);
+    double *rE0 = (double *)malloc(sizeof(double) * n);
+    double *Ti = (double *)malloc(sizeof(double) * n);
+    double *ai = (double *)malloc(sizeof(double) * n);
+    double *V = (double *)malloc(sizeof(double) * n);
+    double *lam = (double *)malloc(sizeof(double) * n);
+    double *uh = (double *)malloc(sizeof(double) * n);
+    double *q = (double *)malloc(sizeof(double) * n);
+    orc_op o = {nx, ny, dx, dy, {P->bc[0], P->bc[1]}, NULL, NULL};
+    o.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
+    o.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+    for (int c = 0; c < n; c++) {
+        T0[c] = cell_T(P, U, n, c);
+        re0[c] = U[4 * n + c] + U[5 * n + c];
+        rE0[c] = U[6 * n + c];
+        Ti[c] = T0[c];
+        ai[c] = U[7 * n + c];
+    }
+    int pmax_used = 0;
+    int nout = P->n_outer < 1 ? 1 : P->n_outer;
+    for (int it = 0; it < nout; it++) {
+        for (int c = 0; c < n; c++) {
+            double m1 = U[0 * n + c], m2 = U[1 * n + c];
+            double T = Ti[c], a2 = ai[c], a1 = 1.0 - a2;
+            double C1 = m1 * P->cv[0], C2 = m2 * P->cv[1];
+            /* p + pinf_k = G_k C_k T / a_k on the manifold */
+            double r1 = (P->gamma[0] - 1.0) * C1 * T / (a1 * a1);
+            double r2 = (P->gamma[1] - 1.0) * C2 * T / (a2 * a2);
+            double K = T * (r1 + r2);
+            V[c] = 1.0 / (C1 + C2 + B1 * B1 / K);
+            lam[c] = a1 * lambda_k(P, 0, T) + a2 * lambda_k(P, 1, T);
+        }
+        op_faces(&o, lam);
+        double lm = op_lam_max(&o, V);
+        int Pn = orc_cheb_P(P, tau, lm);
+        st |= cheb_capped(P, tau, lm, Pn);
+        if (Pn > pmax_used) pmax_used = Pn;
+        double *b = (double *)malloc(sizeof(double) * (2 * Pn - 1));
+        orc_cheb_schedule(Pn, lm, b);
+        lim_predict(&o, Pn, b, tau, V, T0, uh);
+        free(b);
+        op_apply(&o, uh, q);
+        for (int c = 0; c < n; c++) {
+            double T, a2;
+            st |= equilibrium(P, U[0 * n + c], U[1 * n + c], re0[c] + tau * q[c], &T, &a2);
+            Ti[c] = T;
+            ai[c] = a2;
+        }
+    }
+    for (int c = 0; c < n; c++) {
+        double a2 = ai[c], T = Ti[c];
+        U[4 * n + c] = U[0 * n + c] * P->cv[0] * T + (1.0 - a2) * P->pinf[0];
+        U[5 * n + c] = U[1 * n + c] * P->cv[1] * T + a2 * P->pinf[1];
+        U[6 * n + c] = rE0[c] + tau * q[c];
+        U[7 * n + c] = a2;
+    }
+    if (P_used) *P_used = pmax_used;
+    free(T0); free(re0); free(rE0); free(Ti); free(ai); free(V); free(lam); free(uh); free(q);
+    free(o.lx); free(o.ly);
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Viscous step along one axis (Sec. 3.2).                                   */
+/* ------------------------------------------------------------------------- */
+/* rho du_n/dt = d/dx(4/3 mu du_n/dx) and rho du_t/dt = d/dx(mu du_t/dx) by the
+ * LIM with V = 1/rho and mu = a1 mu1 + a2 mu2 (cross-derivative terms are
+ * dropped by the directional splitting); the last sweep updates rho u
+ * conservatively from the predicted velocity u_hat; rho E and E_k follow the
+ * face-flux formulas of Sec. 3.2 with face values taken as two-cell means and
+ * u_hat_i in place of u_i. */
+unsigned orc_viscous(const orc_params *P, int nx, int ny, double dx, double dy, int axis, double tau, double *U,
+                     int *P_used)
+{
+    int n = nx * ny;
+    int len = axis == 0 ? nx : ny;
+    double h = axis == 0 ? dx : dy;
+    int qn = axis == 0 ? 2 : 3, qt = axis == 0 ? 3 : 2;
+    if (len < 2) { if (P_used) *P_used = 0; return 0; }
+    double *V = (double *)malloc(sizeof(double) * n);
+    double *mu = (double *)malloc(sizeof(double) * n);
+    double *ln = (double *)malloc(sizeof(double) * n);
+    double *un0 = (double *)malloc(sizeof(double) * n);
+    double *ut0 = (double *)malloc(sizeof(double) * n);
+    double *unh = (double *)malloc(sizeof(double) * n);
+    double *uth = (double *)malloc(sizeof(double) * n);
+    for (int c = 0; c < n; c++) {
+        double rho = U[0 * n + c] + U[1 * n + c];
+        double a2 = U[7 * n + c];
+        V[c] = 1.0 / rho;
+        mu[c] = (1.0 - a2) * P->mu[0] + a2 * P->mu[1];
+        ln[c] = 4.0 / 3.0 * mu[c];
+        un0[c] = U[qn * n + c] / rho;
+        ut0[c] = U[qt * n + c] / rho;
+    }
+    orc_op o = {nx, ny, dx, dy, {P->bc[0], P->bc[1]}, NULL, NULL};
+    o.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
+    o.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+    orc_op ot = o;
+    ot.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
+    ot.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+    op_faces(&o, ln);
+    op_faces(&ot, mu);
+    /* restrict both operators to the sweep axis */
+    if (axis == 0) {
+        memset(o.ly, 0, sizeof(double) * nx * (ny + 1));
+        memset(ot.ly, 0, sizeof(double) * nx * (ny + 1));
+    } else {
+        memset(o.lx, 0, sizeof(double) * (nx + 1) * ny);
+        memset(ot.lx, 0, sizeof(double) * (nx + 1) * ny);
+    }
+    double lm = op_lam_max(&o, V);
+    int Pn = orc_cheb_P(P, tau, lm);
+    unsigned st = cheb_capped(P, tau, lm, Pn);
+    double *b = (double *)malloc(sizeof(double) * (2 * Pn - 1));
+    orc_cheb_schedule(Pn, lm, b);
+    lim_predict(&o, Pn, b, tau, V, un0, unh);
+    lim_predict(&ot, Pn, b, tau, V, ut0, uth);
+    free(b);
+    /* conservative last sweep and energy updates, line by line */
+    double *newU = (double *)malloc(sizeof(double) * NQ * n);
+    memcpy(newU, U, sizeof(double) * NQ * n);
+    for (int c = 0; c < n; c++) {
+        int i = c % nx, j = c / nx;
+        int pos = axis == 0 ? i : j;
+        /* neighbours and face coefficients on the two faces of cell c */
+        double Fn[2], Ft[2], W[2], aF1[2], aF2[2];
+        for (int s = 0; s < 2; s++) {
+            /* s = 0: face minus (between pos-1 and pos), s = 1: face plus */
+            int fp = pos + s; /* face index 0..len */
+            double lnf, lmf;
+            int cl, cr;
+            if (axis == 0) {
+                lnf = o.lx[j * (nx + 1) + fp];
+                lmf = ot.lx[j * (nx + 1) + fp];
+                int il = fp == 0 ? nx - 1 : fp - 1, ir = fp == nx ? 0 : fp;
+                cl = j * nx + il; cr = j * nx + ir;
+            } else {
+                lnf = o.ly[fp * nx + i];
+                lmf = ot.ly[fp * nx + i];
+                int jl = fp == 0 ? ny - 1 : fp - 1, jr = fp == ny ? 0 : fp;
+                cl = jl * nx + i; cr = jr * nx + i;
+            }
+            Fn[s] = lnf * (unh[cr] - unh[cl]) / h;
+            Ft[s] = lmf * (uth[cr] - uth[cl]) / h;
+            double ubar = 0.5 * (unh[cl] + unh[cr]);
+            double wbar = 0.5 * (uth[cl] + uth[cr]);
+            W[s] = ubar * Fn[s] + wbar * Ft[s];
+            double a2l = U[7 * n + cl], a2r = U[7 * n + cr];
+            aF2[s] = 0.5 * (a2l + a2r);
+            aF1[s] = 0.5 * ((1.0 - a2l) + (1.0 - a2r));
+        }
+        newU[qn * n + c] = U[qn * n + c] + tau * (Fn[1] - Fn[0]) / h;
+        newU[qt * n + c] = U[qt * n + c] + tau * (Ft[1] - Ft[0]) / h;
+        newU[6 * n + c] = U[6 * n + c] + tau * (W[1] - W[0]) / h;
+        newU[4 * n + c] = U[4 * n + c] + tau * (aF1[1] * W[1] - aF1[0] * W[0]) / h -
+                          tau * (unh[c] * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + uth[c] * (aF1[1] * Ft[1] - aF1[0] * Ft[0])) / h;
+        newU[5 * n + c] = U[5 * n + c] + tau * (aF2[1] * W[1] - aF2[0] * W[0]) / h -
+                          tau * (unh[c] * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + uth[c] * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) / h;
+    }
+    memcpy(U, newU, sizeof(double) * NQ * n);
+    if (P_used) *P_used = Pn;
+    free(newU); free(V); free(mu); free(ln); free(un0); free(ut0); free(unh); free(uth);
+    free(o.lx); free(o.ly); free(ot.lx); free(ot.ly);
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One split step: mechanical stage (hyperbolic sweeps x then y, each followed */
+/* by pressure relaxation; viscous step; pressure relaxation), temperature    */
+/* relaxation, heat conduction (Sec. 3 opening, Sec. 2.4).                    */
+/* ------------------------------------------------------------------------- */
+static int viscous_on(const orc_params *P) { return P->mu[0] > 0.0 || P->mu[1] > 0.0; }
+static int heat_on(const orc_params *P) { return P->trelax == 1 && (P->k0[0] > 0.0 || P->k0[1] > 0.0); }
+
+/* end-of-step admissibility: alpha_2 in (0,1), m_k > 0, p_k + pinf_k > 0 */
+static unsigned final_check(const orc_params *P, int n, const double *U)
+{
+    unsigned st = 0;
+    for (int c = 0; c < n; c++) {
+        double a2 = U[7 * n + c], a1 = 1.0 - a2;
+        double p1 = phase_p(P, 0, U[4 * n + c], a1), p2 = phase_p(P, 1, U[5 * n + c], a2);
+        if (!(a2 > 0.0 && a2 < 1.0 && U[0 * n + c] > 0.0 && U[1 * n + c] > 0.0 && p1 + P->pinf[0] > 0.0 &&
+              p2 + P->pinf[1] > 0.0))
+            st |= ORC_NONPHYS;
+        for (int k = 0; k < NQ; k++)
+            if (isnan(U[k * n + c])) st |= ORC_NAN;
+    }
+    return st;
+}
+
+unsigned orc_step(const orc_params *P, int nx, int ny, double dx, double dy, double *U, int nsteps, double dt_fixed,
+                  double *dt_last, int *P_heat)
+{
+    int n = nx * ny;
+    unsigned st = 0, tr = 0;
+    int ph = 0;
+    for (int s = 0; s < nsteps; s++) {
+        double dt = dt_fixed > 0.0 ? dt_fixed : orc_dt(P, nx, ny, dx, dy, U);
+        if (nx > 1) { tr |= orc_sweep(P, nx, ny, dx, dy, 0, dt, U); tr |= orc_prelax(P, n, U); }
+        if (ny > 1) { tr |= orc_sweep(P, nx, ny, dx, dy, 1, dt, U); tr |= orc_prelax(P, n, U); }
+        if (viscous_on(P)) {
+            int pv;
+            if (nx > 1) tr |= orc_viscous(P, nx, ny, dx, dy, 0, dt, U, &pv);
+            if (ny > 1) tr |= orc_viscous(P, nx, ny, dx, dy, 1, dt, U, &pv);
+            tr |= orc_prelax(P, n, U);
+        }
+        if (P->trelax == 1) {
+            tr |= orc_trelax(P, n, U);
+            if (heat_on(P)) tr |= orc_heat(P, nx, ny, dx, dy, dt, U, &ph);
+        }
+        st |= final_check(P, n, U);
+        if (dt_last) *dt_last = dt;
+    }
+    if (tr & (ORC_NONPHYS | ORC_NOROOT)) st |= ORC_TRANSIENT;
+    if (tr & ORC_NAN) st |= ORC_NAN;
+    st |= tr & ORC_PCAP;
+    if (P_heat) *P_heat = ph;
+    return st;
+}
+
+/* diagnostics used by the tests: per-cell phase pressures and temperatures */
+void orc_diagnostics(const orc_params *P, int ncell, const double *U, double *out /* 6 planes */)
+{
+    int n = ncell;
+    for (int c = 0; c < n; c++) {
+        double m1 = U[0 * n + c], m2 = U[1 * n + c];
+        double a2 = U[7 * n + c], a1 = 1.0 - a2;
+        double rho = m1 + m2;
+        double p1 = phase_p(P, 0, U[4 * n + c], a1);
+        double p2 = phase_p(P, 1, U[5 * n + c], a2);
+        double r1 = m1 / a1, r2 = m2 / a2;
+        /* T_k = (p_k + pinf_k) / ((g_k - 1) rho_k Cv_k), Eq. eos_stiffened2 */
+        out[0 * n + c] = p1;
+        out[1 * n + c] = p2;
+        out[2 * n + c] = (p1 + P->pinf[0]) / ((P->gamma[0] - 1.0) * r1 * P->cv[0]);
+        out[3 * n + c] = (p2 + P->pinf[1]) / ((P->gamma[1] - 1.0) * r2 * P->cv[1]);
+        out[4 * n + c] = U[2 * n + c] / rho;
+        out[5 * n + c] = U[3 * n + c] / rho;
+    }
+}
+
+/* heat-stage coefficients at a cell state, exported for the tests:
+ * out = (T, V, U_alpha, Lam) with U_alpha = -B1 V / K */
+void orc_heat_coeffs(const orc_params *P, int ncell, const double *U, double *out /* 4 planes */)
+{
+    int n = ncell;
+    double B1 = P->pinf[0] - P->pinf[1];
+    for (int c = 0; c < n; c++) {
+        double m1 = U[0 * n + c], m2 = U[1 * n + c];
+        double a2 = U[7 * n + c], a1 = 1.0 - a2;
+        double T = cell_T(P, U, n, c);
+        double C1 = m1 * P->cv[0], C2 = m2 * P->cv[1];
+        double r1 = (P->gamma[0] - 1.0) * C1 * T / (a1 * a1);
+        double r2 = (P->gamma[1] - 1.0) * C2 * T / (a2 * a2);
+        double K = T * (r1 + r2);
+        double V = 1.0 / (C1 + C2 + B1 * B1 / K);
+        out[0 * n + c] = T;
+        out[1 * n + c] = V;
+        out[2 * n + c] = -B1 * V / K;
+        out[3 * n + c] = a1 * lambda_k(P, 0, T) + a2 * lambda_k(P, 1, T);
+    }
+}
+
+/* exported for tests: the equilibrium projection of one state */
+unsigned orc_equilibrium(const orc_params *P, double m1, double m2, double rhoe, double *T, double *a2)
+{
+    return equilibrium(P, m1, m2, rhoe, T, a2);
+}

@@ -1,0 +1,200 @@
+"""ctypes binding of the FP64 CPU oracle (``dim_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+CPU-baseline / reference leg of the benchmark.  The product path never loads
+this module.  Arrays are numpy float64, state shape (8, ny, nx).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dim_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction)."""
+    out = _LIB if not openmp else os.path.join(_HERE, "liboracle_omp.so")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return out
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("gamma", C.c_double * 2), ("pinf", C.c_double * 2), ("cv", C.c_double * 2),
+        ("k0", C.c_double * 2), ("k_exp", C.c_double), ("T_ref", C.c_double),
+        ("mu", C.c_double * 2), ("cfl", C.c_double),
+        ("limiter", C.c_int), ("bc", C.c_int * 2), ("trelax", C.c_int), ("n_outer", C.c_int),
+        ("p_policy", C.c_int), ("p_fixed", C.c_int), ("p_min", C.c_int), ("p_max", C.c_int),
+    ]
+
+
+def _params(p) -> _Params:
+    s = _Params()
+    s.gamma[:] = list(p.gamma)
+    s.pinf[:] = list(p.pinf)
+    s.cv[:] = list(p.cv)
+    s.k0[:] = list(p.k0)
+    s.k_exp = p.k_exp
+    s.T_ref = p.T_ref
+    s.mu[:] = list(p.mu)
+    s.cfl = p.cfl
+    s.limiter = p.limiter
+    s.bc[:] = list(p.bc)
+    s.trelax = p.trelax
+    s.n_outer = p.n_outer
+    s.p_policy = p.p_policy
+    s.p_fixed = p.p_fixed
+    s.p_min = p.p_min
+    s.p_max = p.p_max
+    return s
+
+
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        P = C.POINTER(_Params)
+        i, d, u = C.c_int, C.c_double, C.c_uint
+        L.orc_from_primitive.argtypes = [P, i, i, _D, _D]; L.orc_from_primitive.restype = u
+        L.orc_dt.argtypes = [P, i, i, d, d, _D]; L.orc_dt.restype = d
+        L.orc_sweep.argtypes = [P, i, i, d, d, i, d, _D]; L.orc_sweep.restype = u
+        L.orc_prelax.argtypes = [P, i, _D]; L.orc_prelax.restype = u
+        L.orc_trelax.argtypes = [P, i, _D]; L.orc_trelax.restype = u
+        L.orc_heat.argtypes = [P, i, i, d, d, d, _D, C.POINTER(i)]; L.orc_heat.restype = u
+        L.orc_viscous.argtypes = [P, i, i, d, d, i, d, _D, C.POINTER(i)]; L.orc_viscous.restype = u
+        L.orc_step.argtypes = [P, i, i, d, d, _D, i, d, _D, C.POINTER(i)]; L.orc_step.restype = u
+        L.orc_cheb_P.argtypes = [P, d, d]; L.orc_cheb_P.restype = i
+        L.orc_cheb_schedule.argtypes = [i, d, _D]; L.orc_cheb_schedule.restype = None
+        L.orc_lim_solve.argtypes = [P, i, i, d, d, d, _D, _D, _D, _D, _D]; L.orc_lim_solve.restype = i
+        L.orc_diagnostics.argtypes = [P, i, _D, _D]; L.orc_diagnostics.restype = None
+        L.orc_heat_coeffs.argtypes = [P, i, _D, _D]; L.orc_heat_coeffs.restype = None
+        L.orc_equilibrium.argtypes = [P, d, d, d, _D, _D]; L.orc_equilibrium.restype = u
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _state(U: np.ndarray) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    assert U.shape[0] == 8
+    return U
+
+
+def from_primitive(params, prim: np.ndarray) -> np.ndarray:
+    prim = np.ascontiguousarray(prim, dtype=np.float64)
+    _, ny, nx = prim.shape
+    U = np.empty((8, ny, nx))
+    st = lib().orc_from_primitive(C.byref(_params(params)), nx, ny, _ptr(prim), _ptr(U))
+    if st:
+        raise ValueError(f"non-physical initial data (status {st})")
+    return U
+
+
+def dt(params, U, dx, dy) -> float:
+    U = _state(U)
+    return lib().orc_dt(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, _ptr(U))
+
+
+def sweep(params, U, dx, dy, axis, dt_):
+    U = _state(U).copy()
+    st = lib().orc_sweep(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, axis, dt_, _ptr(U))
+    return U, st
+
+
+def prelax(params, U):
+    U = _state(U).copy()
+    st = lib().orc_prelax(C.byref(_params(params)), U.shape[1] * U.shape[2], _ptr(U))
+    return U, st
+
+
+def trelax(params, U):
+    U = _state(U).copy()
+    st = lib().orc_trelax(C.byref(_params(params)), U.shape[1] * U.shape[2], _ptr(U))
+    return U, st
+
+
+def heat(params, U, dx, dy, tau):
+    U = _state(U).copy()
+    pu = C.c_int(0)
+    st = lib().orc_heat(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, tau, _ptr(U), C.byref(pu))
+    return U, st, pu.value
+
+
+def viscous(params, U, dx, dy, axis, tau):
+    U = _state(U).copy()
+    pu = C.c_int(0)
+    st = lib().orc_viscous(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, axis, tau, _ptr(U),
+                           C.byref(pu))
+    return U, st, pu.value
+
+
+def step(params, U, dx, dy, nsteps=1, dt_fixed=0.0):
+    """nsteps full split steps; returns (U, status, dt_last, P_heat)."""
+    U = _state(U).copy()
+    dtl = C.c_double(0.0)
+    ph = C.c_int(0)
+    st = lib().orc_step(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, _ptr(U), nsteps, dt_fixed,
+                        C.byref(dtl), C.byref(ph))
+    return U, st, dtl.value, ph.value
+
+
+def cheb_P(params, tau, lam_max) -> int:
+    return lib().orc_cheb_P(C.byref(_params(params)), tau, lam_max)
+
+
+def cheb_schedule(P: int, lam: float) -> np.ndarray:
+    b = np.zeros(2 * P - 1)
+    lib().orc_cheb_schedule(P, lam, _ptr(b))
+    return b
+
+
+def lim_solve(params, lam, V, v0, dx, dy, tau):
+    """One full LIM solve of dv/dt = V L_h v; arrays of shape (ny, nx)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64)
+    ny, nx = v0.shape
+    v1 = np.empty_like(v0)
+    lm = C.c_double(0.0)
+    Pn = lib().orc_lim_solve(C.byref(_params(params)), nx, ny, dx, dy, tau, _ptr(lam), _ptr(V), _ptr(v0),
+                             _ptr(v1), C.byref(lm))
+    return v1, Pn, lm.value
+
+
+def diagnostics(params, U):
+    """(p1, p2, T1, T2, u, v), each shaped like one plane."""
+    U = _state(U)
+    out = np.empty((6,) + U.shape[1:])
+    lib().orc_diagnostics(C.byref(_params(params)), U.shape[1] * U.shape[2], _ptr(U), _ptr(out))
+    return out
+
+
+def heat_coeffs(params, U):
+    """(T, V, U_alpha, Lam) at each cell."""
+    U = _state(U)
+    out = np.empty((4,) + U.shape[1:])
+    lib().orc_heat_coeffs(C.byref(_params(params)), U.shape[1] * U.shape[2], _ptr(U), _ptr(out))
+    return out
+
+
+def equilibrium(params, m1, m2, rhoe):
+    T = C.c_double(0.0)
+    a = C.c_double(0.0)
+    st = lib().orc_equilibrium(C.byref(_params(params)), m1, m2, rhoe, C.byref(T), C.byref(a))
+    return T.value, a.value, st
