@@ -1,0 +1,166 @@
+/*
+ * dim.h -- C ABI of the GB300 (sm_103a) split time step of the reduced
+ * two-temperature Baer-Nunziato model (Zhang, Menshov, Wang & Shen,
+ * arXiv:2106.00282): a diffuse-interface model of two compressible phases with
+ * phase masses, phase internal energies, mixture momentum, mixture total
+ * energy and volume fraction, stiffened-gas EOS, viscosity and heat conduction.
+ *
+ * Conventions
+ * -----------
+ *  - State U: 8 planes of nx*ny doubles in DEVICE memory, row-major, cell
+ *    (i, j) at j*nx + i, plane q at q*nx*ny:
+ *      0 m1 = alpha_1 rho_1   1 m2 = alpha_2 rho_2   2 rho u   3 rho v
+ *      4 E1 = alpha_1 rho_1 e_1   5 E2 = alpha_2 rho_2 e_2   6 rho E   7 alpha_2
+ *    (the conservative vector of Sec. 3.1, Eq. vectorForm).  Phase 1 is the
+ *    dense phase (liquid/solid), phase 2 the gas.  The caller owns U; it must
+ *    be 256-byte aligned (any cudaMalloc / torch allocation is).
+ *  - Every call is stream-ordered on the stream given to dim_init and does not
+ *    synchronize unless it returns a host value (dt_last, P_used, status).
+ *  - Return value: 0 on success, a negative DIM_E* code otherwise.  After an
+ *    error U is unspecified; restore it from a copy.
+ *  - The library owns only the scratch it allocates in dim_init (about
+ *    16 planes of nx*ny doubles plus a few device scalars).
+ */
+#ifndef DIM_H
+#define DIM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define DIM_OK 0
+#define DIM_EINVAL (-1)   /* bad parameter, size or pointer */
+#define DIM_ECUDA (-2)    /* a CUDA call failed (launch, allocation, copy) */
+#define DIM_ENONPHYS (-3) /* the end-of-step state is not admissible: alpha_2 outside (0,1),
+                             m_k <= 0, p + pinf_k <= 0, or a NaN */
+#define DIM_ENOROOT (-4)  /* a relaxation quadratic had no real root */
+#define DIM_ETIMEOUT (-5) /* a bounded grid-wide wait inside a kernel gave up */
+#define DIM_ENOTIMPL (-6) /* entry point not implemented in this build */
+
+/* device status word bits (dim_status) */
+#define DIM_ST_NONPHYS 1u   /* end-of-step state inadmissible */
+#define DIM_ST_NAN 2u       /* NaN met */
+#define DIM_ST_NOROOT 4u    /* negative discriminant in a relaxation quadratic */
+#define DIM_ST_TRANSIENT 8u /* an intermediate stage met an inadmissible phase state that a later
+                               stage of the same step repaired (informational) */
+#define DIM_ST_PCAP 16u     /* the P formula exceeded p_max; P = p_max was used (informational) */
+#define DIM_ST_TIMEOUT 32u  /* a grid barrier wait gave up */
+
+/* flag values of dim_params */
+#define DIM_LIMITER_NONE 0   /* first-order Godunov */
+#define DIM_LIMITER_MINMOD 1 /* PVT-consistent MUSCL, Sec. 3.6 */
+#define DIM_BC_TRANSMISSIVE 0
+#define DIM_BC_PERIODIC 1
+#define DIM_TRELAX_OFF 0         /* no temperature relaxation and no conduction */
+#define DIM_TRELAX_EQUILIBRIUM 1 /* exact p,T equilibrium, Sec. 3.4.1 */
+#define DIM_P_FORMULA 0          /* P = ceil(pi/4 sqrt(tau lambda_max + 1)), capped at p_max */
+#define DIM_P_FIXED 1            /* P = p_fixed */
+#define DIM_P_CLAMP 2            /* P = clamp(formula, p_min, p_max) */
+
+#define DIM_RELAX_PRESSURE 0    /* dim_relax: Sec. 3.3 three-step pressure relaxation */
+#define DIM_RELAX_TEMPERATURE 1 /* dim_relax: Sec. 3.4.1 temperature relaxation */
+
+#define DIM_PARABOLIC_HEAT 0      /* dim_cheb_parabolic: Sec. 3.4.2 heat conduction, Algorithm 1 */
+#define DIM_PARABOLIC_VISCOUS_X 1 /* dim_cheb_parabolic: Sec. 3.2 viscous step along x */
+#define DIM_PARABOLIC_VISCOUS_Y 2 /* dim_cheb_parabolic: Sec. 3.2 viscous step along y */
+
+/* Phase and solver parameters.  Stiffened-gas EOS per phase k (Eqs.
+ * eos_stiffened, eos_stiffened2, q_k = 0):
+ *   rho_k e_k = (p_k + gamma_k pinf_k)/(gamma_k - 1) = rho_k Cv_k T_k + pinf_k.
+ * Conductivity lambda_k(T) = k0_k (T/T_ref)^k_exp; viscosity mu_k constant;
+ * mixture coefficients are volume-fraction means (Sec. 4.2). */
+typedef struct dim_params {
+    double gamma[2], pinf[2], cv[2];
+    double k0[2], k_exp, T_ref;
+    double mu[2];
+    double cfl;
+    int limiter;
+    int bc[2]; /* per axis (x, y) */
+    int trelax;
+    int n_outer; /* outer iterations of Algorithm 1 (>= 1) */
+    int p_policy, p_fixed, p_min, p_max;
+} dim_params;
+
+typedef struct dim_ctx dim_ctx; /* opaque: parameters, grid, stream, scratch */
+
+/* Create a context for an nx x ny grid of spacing (dx, dy) and allocate its
+ * scratch.  A 1D problem is ny = 1 (or nx = 1); an axis of extent 1 is inactive.
+ * cuda_stream is a cudaStream_t (NULL: legacy default stream).
+ * Errors: DIM_EINVAL for non-positive sizes/spacings, gamma_k <= 1, Cv_k <= 0,
+ * cfl <= 0, unknown flags, p_max outside [1, 64]; DIM_ECUDA on allocation
+ * failure.  The paper's parameters: Sec. 2 (EOS), Sec. 3 (scheme). */
+int dim_init(dim_ctx **out, const dim_params *p, int nx, int ny, double dx, double dy, void *cuda_stream);
+
+/* Release the scratch and the context (synchronizes its stream). */
+void dim_destroy(dim_ctx *c);
+
+/* Fill U from primitive fields prim (device, 5 planes of nx*ny doubles:
+ * alpha_2, p, T, u, v) with both phases at the cell's (p, T): rho_k from Eq.
+ * eos_stiffened2, E_k = alpha_k (p + gamma_k pinf_k)/(gamma_k - 1) from Eq.
+ * eos_stiffened, rho E = E1 + E2 + rho |u|^2 / 2.  prim and U must not overlap. */
+int dim_from_primitive(dim_ctx *c, const double *prim, double *U);
+
+/* Time step of the CFL condition (Sec. 3.1 mixture sound speed
+ * c^2 = Y1 c1^2 + Y2 c2^2): dt = cfl / max_cells max_axis (|u_axis| + c)/h_axis.
+ * Writes the host double *dt (synchronizes). */
+int dim_cfl_dt(dim_ctx *c, const double *U, double *dt);
+
+/* nsteps split steps in place on U (Sec. 3): per step dt from the CFL
+ * condition; hyperbolic sweep along x then y (MUSCL + HLLC + non-conservative
+ * term, Sec. 3.1/3.6), each followed by pressure relaxation (Sec. 3.3);
+ * viscous steps along x and y (Sec. 3.2, only if some mu_k > 0) and pressure
+ * relaxation; temperature relaxation (Sec. 3.4.1) and heat conduction
+ * (Sec. 3.4.2, Algorithm 1; only if some k0_k > 0), unless trelax is OFF.
+ * dt_last: host out (may be NULL).  If dt_last is non-NULL the call
+ * synchronizes and also returns DIM_ENONPHYS / DIM_ENOROOT / DIM_ETIMEOUT when
+ * the status word says so; with dt_last NULL it is fully asynchronous (check
+ * dim_status later). */
+int dim_step(dim_ctx *c, double *U, int nsteps, double *dt_last);
+
+/* The same nsteps split steps on a HOST state U_host (8 planes as above, any
+ * alignment): copies it to a context-owned device buffer, steps, copies it
+ * back; synchronizes; returns the status like dim_step with dt_last. */
+int dim_step_host(dim_ctx *c, double *U_host, int nsteps, double *dt_last);
+
+/* One hyperbolic sweep along axis (0 = x, 1 = y) with time step dt (> 0),
+ * followed by the pressure relaxation of Sec. 3.3 when relax != 0; in place on
+ * U (the sweep itself is computed out of place into scratch). */
+int dim_hllc_sweep(dim_ctx *c, double *U, int axis, double dt, int relax);
+
+/* Pointwise relaxation in place: DIM_RELAX_PRESSURE (Sec. 3.3, steps 1-3) or
+ * DIM_RELAX_TEMPERATURE (Sec. 3.4.1, exact p,T equilibrium). */
+int dim_relax(dim_ctx *c, double *U, int which);
+
+/* Parabolic stage by the Chebyshev local-iteration method (Sec. 3.2, Eqs. LIM,
+ * LIM_last) with time step dt: DIM_PARABOLIC_HEAT (Sec. 3.4.2; the input must be
+ * in p,T equilibrium, e.g. after dim_relax(TEMPERATURE)) or
+ * DIM_PARABOLIC_VISCOUS_X / _Y (Sec. 3.2, no pressure relaxation).  P_used: host
+ * out, the number of Chebyshev parameters used (may be NULL; non-NULL
+ * synchronizes). */
+int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used);
+
+/* Gradients of a final-time objective through nsteps steps (adjoint).  Not
+ * implemented in this build: returns DIM_ENOTIMPL. */
+int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const double *dJ_dUT, double *dJ_dU0,
+             double *dJ_dparams);
+
+/* Read (and clear if reset != 0) the device status word (DIM_ST_* bits);
+ * synchronizes. */
+int dim_status(dim_ctx *c, unsigned *flags, int reset);
+
+/* Per-kernel timing with CUDA events on the context stream.  enable != 0 turns
+ * it on (events around every launch), 0 off.  dim_kernel_time returns the
+ * accumulated launches and milliseconds of kernel `name` ("sweep_x",
+ * "sweep_y", "heat", "viscous_x", "viscous_y", "wave_max", "relax") since the
+ * last reset; synchronizes. */
+int dim_profile(dim_ctx *c, int enable, int reset);
+int dim_kernel_time(dim_ctx *c, const char *name, int *launches, double *ms);
+
+/* Message of a return code. */
+const char *dim_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIM_H */

@@ -1,0 +1,112 @@
+"""Thin Python binding of libdim (names follow include/dim.h).
+
+PyTorch provides device memory and the stream; every computation runs in the
+CUDA kernels behind the C ABI.  There is no CPU fallback: without a CUDA device
+or without libdim.so the calls raise.
+
+    s = Solver(params, nx, ny, dx, dy)
+    U = s.from_primitive(prim)          # prim: (5, ny, nx) float64 alpha_2, p, T, u, v
+    dt = s.step(U, nsteps=10)           # U: (8, ny, nx) float64 on the device, in place
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+def _dev_ptr(t: torch.Tensor, shape=None) -> int:
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+class Solver:
+    """One grid, one parameter set, one CUDA stream (a dim_ctx)."""
+
+    def __init__(self, params, nx: int, ny: int, dx: float, dy: float, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdim needs a CUDA device")
+        self.L = _lib.load()
+        self.params, self.nx, self.ny, self.dx, self.dy = params, nx, ny, dx, dy
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._p = _lib.make_params(params)
+        self._ctx = C.c_void_p()
+        check(self.L.dim_init(C.byref(self._ctx), C.byref(self._p), nx, ny, dx, dy,
+                              C.c_void_p(self.stream.cuda_stream)), "dim_init")
+
+    @property
+    def state_shape(self):
+        return (8, self.ny, self.nx)
+
+    def close(self):
+        if self._ctx:
+            self.L.dim_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def from_primitive(self, prim: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        U = out if out is not None else torch.empty(self.state_shape, dtype=torch.float64, device=prim.device)
+        check(self.L.dim_from_primitive(self._ctx, _dev_ptr(prim, (5, self.ny, self.nx)),
+                                        _dev_ptr(U, self.state_shape)), "dim_from_primitive")
+        return U
+
+    def cfl_dt(self, U: torch.Tensor) -> float:
+        dt = C.c_double(0.0)
+        check(self.L.dim_cfl_dt(self._ctx, _dev_ptr(U, self.state_shape), C.byref(dt)), "dim_cfl_dt")
+        return dt.value
+
+    def step(self, U: torch.Tensor, nsteps: int = 1, sync: bool = True):
+        """nsteps split steps in place; with sync returns dt of the last step
+        and raises on an inadmissible end-of-step state."""
+        if sync:
+            dt = C.c_double(0.0)
+            check(self.L.dim_step(self._ctx, _dev_ptr(U, self.state_shape), nsteps, C.byref(dt)), "dim_step")
+            return dt.value
+        check(self.L.dim_step(self._ctx, _dev_ptr(U, self.state_shape), nsteps, None), "dim_step")
+        return None
+
+    def step_host(self, U_host: torch.Tensor, nsteps: int = 1) -> float:
+        """The same on a host (ideally pinned) float64 tensor: H2D, steps, D2H."""
+        if U_host.is_cuda or U_host.dtype != torch.float64 or not U_host.is_contiguous():
+            raise ValueError("expected a contiguous float64 host tensor")
+        dt = C.c_double(0.0)
+        check(self.L.dim_step_host(self._ctx, U_host.data_ptr(), nsteps, C.byref(dt)), "dim_step_host")
+        return dt.value
+
+    def hllc_sweep(self, U: torch.Tensor, axis: int, dt: float, relax: bool = True):
+        check(self.L.dim_hllc_sweep(self._ctx, _dev_ptr(U, self.state_shape), axis, dt, int(relax)),
+              "dim_hllc_sweep")
+
+    def relax(self, U: torch.Tensor, which: int):
+        check(self.L.dim_relax(self._ctx, _dev_ptr(U, self.state_shape), which), "dim_relax")
+
+    def cheb_parabolic(self, U: torch.Tensor, kind: int, dt: float) -> int:
+        P = C.c_int(0)
+        check(self.L.dim_cheb_parabolic(self._ctx, _dev_ptr(U, self.state_shape), kind, dt, C.byref(P)),
+              "dim_cheb_parabolic")
+        return P.value
+
+    def status(self, reset: bool = False) -> int:
+        f = C.c_uint(0)
+        check(self.L.dim_status(self._ctx, C.byref(f), int(reset)), "dim_status")
+        return f.value
+
+    def profile(self, enable: bool = True, reset: bool = True):
+        check(self.L.dim_profile(self._ctx, int(enable), int(reset)), "dim_profile")
+
+    def kernel_time(self, name: str):
+        n = C.c_int(0)
+        ms = C.c_double(0.0)
+        check(self.L.dim_kernel_time(self._ctx, name.encode(), C.byref(n), C.byref(ms)), "dim_kernel_time")
+        return n.value, ms.value

@@ -1,0 +1,447 @@
+// dim_api.cu -- host side of the C ABI declared in include/dim.h.
+//
+// Owns the context (parameters, grid, stream, scratch planes, device scalars)
+// and sequences the stage kernels of one split step (Sec. 3): CFL reduction,
+// x sweep, y sweep (each with the pressure relaxation fused in its epilogue),
+// viscous steps, temperature relaxation fused into the heat-conduction
+// launch.  Every call is stream-ordered on the context stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/dim.h"
+#include "dim_device.cuh"
+
+namespace dimk {
+cudaError_t sweep_setup();
+cudaError_t parabolic_setup(int nsm);
+cudaError_t launch_sweep(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
+                         int relax, int check, cudaStream_t s);
+cudaError_t launch_from_primitive(const DevParams &p, const double *prim, double *U, Scalars *sc, cudaStream_t s);
+cudaError_t launch_wave_max(const DevParams &p, const double *U, Scalars *sc, cudaStream_t s);
+cudaError_t launch_relax(const DevParams &p, double *U, Scalars *sc, int which, int check, cudaStream_t s);
+cudaError_t launch_heat(const DevParams &p, double *U, const HeatScratch &s, Scalars *sc, double dt_host,
+                        int trelax_first, int check, cudaStream_t st);
+cudaError_t launch_visc(const DevParams &p, int axis, double *U, const ViscScratch &s, Scalars *sc, double dt_host,
+                        int relax, int check, cudaStream_t st);
+}  // namespace dimk
+
+using dimk::DevParams;
+using dimk::Scalars;
+
+namespace {
+
+enum KernelId { K_SWEEP_X, K_SWEEP_Y, K_HEAT, K_VISC_X, K_VISC_Y, K_WAVE, K_RELAX, K_COPY, K_NKERNELS };
+const char *kKernelNames[K_NKERNELS] = {"sweep_x", "sweep_y", "heat", "viscous_x", "viscous_y", "wave_max", "relax",
+                                        "copy"};
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct dim_ctx {
+    dim_params hp;
+    DevParams p;
+    cudaStream_t stream;
+    double *U2;   // 8 planes: out-of-place target of the sweeps
+    double *S;    // 8 scratch planes for the parabolic stages
+    double *Uh;   // 8 planes: device copy of a host state (dim_step_host), lazily allocated
+    Scalars *sc;
+    int device;
+    // profiling
+    int prof;
+    ProfRec *recs;
+    int nrec, caprec;
+};
+
+static bool g_setup_done[64];
+
+
+static bool viscous_on(const dim_params &h) { return h.mu[0] > 0.0 || h.mu[1] > 0.0; }
+static bool heat_on(const dim_params &h) { return h.trelax == DIM_TRELAX_EQUILIBRIUM && (h.k0[0] > 0.0 || h.k0[1] > 0.0); }
+
+static cudaError_t prof_begin(dim_ctx *c, int kid, int *slot)
+{
+    *slot = -1;
+    if (!c->prof) return cudaSuccess;
+    if (c->nrec == c->caprec) {
+        int nc = c->caprec ? 2 * c->caprec : 256;
+        ProfRec *r = (ProfRec *)realloc(c->recs, sizeof(ProfRec) * nc);
+        if (!r) return cudaErrorMemoryAllocation;
+        for (int i = c->caprec; i < nc; i++) {
+            r[i].a = r[i].b = nullptr;
+        }
+        c->recs = r;
+        c->caprec = nc;
+    }
+    ProfRec &r = c->recs[c->nrec];
+    if (!r.a) {
+        cudaError_t e = cudaEventCreate(&r.a);
+        if (e != cudaSuccess) return e;
+        e = cudaEventCreate(&r.b);
+        if (e != cudaSuccess) return e;
+    }
+    r.kid = kid;
+    *slot = c->nrec++;
+    return cudaEventRecord(r.a, c->stream);
+}
+
+static cudaError_t prof_end(dim_ctx *c, int slot)
+{
+    if (slot < 0) return cudaSuccess;
+    return cudaEventRecord(c->recs[slot].b, c->stream);
+}
+
+static cudaError_t reset_accumulators(dim_ctx *c)
+{
+    return cudaMemsetAsync(c->sc, 0, offsetof(Scalars, status), c->stream);
+}
+
+static dimk::HeatScratch heat_scratch(dim_ctx *c)
+{
+    size_t n = (size_t)c->p.n;
+    double *S = c->S;
+    return dimk::HeatScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n};
+}
+
+static dimk::ViscScratch visc_scratch(dim_ctx *c)
+{
+    size_t n = (size_t)c->p.n;
+    double *S = c->S;
+    return dimk::ViscScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n};
+}
+
+#define TRY(x)                                     \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return DIM_ECUDA;   \
+    } while (0)
+
+#define TIMED(c, kid, launch)                      \
+    do {                                           \
+        int slot_;                                 \
+        TRY(prof_begin((c), (kid), &slot_));       \
+        TRY(launch);                               \
+        TRY(prof_end((c), slot_));                 \
+    } while (0)
+
+extern "C" {
+
+const char *dim_strerror(int code)
+{
+    switch (code) {
+    case DIM_OK: return "ok";
+    case DIM_EINVAL: return "invalid argument";
+    case DIM_ECUDA: return "CUDA error";
+    case DIM_ENONPHYS: return "non-physical state (alpha, density or pressure out of range, or NaN)";
+    case DIM_ENOROOT: return "relaxation quadratic without real root";
+    case DIM_ETIMEOUT: return "grid barrier wait timed out";
+    case DIM_ENOTIMPL: return "not implemented";
+    default: return "unknown error";
+    }
+}
+
+int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, double dy, void *cuda_stream)
+{
+    if (!out || !hp) return DIM_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 27) || !(dx > 0.0) || !(dy > 0.0)) return DIM_EINVAL;
+    for (int k = 0; k < 2; k++) {
+        if (!(hp->gamma[k] > 1.0) || !(hp->cv[k] > 0.0) || !(hp->pinf[k] >= 0.0) || !(hp->k0[k] >= 0.0) ||
+            !(hp->mu[k] >= 0.0))
+            return DIM_EINVAL;
+        if (hp->bc[k] != DIM_BC_TRANSMISSIVE && hp->bc[k] != DIM_BC_PERIODIC) return DIM_EINVAL;
+    }
+    if (!(hp->cfl > 0.0) || !(hp->T_ref > 0.0)) return DIM_EINVAL;
+    if (hp->limiter != DIM_LIMITER_NONE && hp->limiter != DIM_LIMITER_MINMOD) return DIM_EINVAL;
+    if (hp->trelax != DIM_TRELAX_OFF && hp->trelax != DIM_TRELAX_EQUILIBRIUM) return DIM_EINVAL;
+    if (hp->n_outer < 1 || hp->n_outer > 8) return DIM_EINVAL;
+    if (hp->p_policy < DIM_P_FORMULA || hp->p_policy > DIM_P_CLAMP) return DIM_EINVAL;
+    if (hp->p_max < 1 || hp->p_max > dimk::PMAX) return DIM_EINVAL;
+    if (hp->p_policy == DIM_P_FIXED && (hp->p_fixed < 1 || hp->p_fixed > dimk::PMAX)) return DIM_EINVAL;
+    if (hp->p_policy == DIM_P_CLAMP && (hp->p_min < 1 || hp->p_min > hp->p_max)) return DIM_EINVAL;
+
+    dim_ctx *c = (dim_ctx *)calloc(1, sizeof(dim_ctx));
+    if (!c) return DIM_ECUDA;
+    c->hp = *hp;
+    DevParams &p = c->p;
+    for (int k = 0; k < 2; k++) {
+        p.g[k] = hp->gamma[k];
+        p.pinf[k] = hp->pinf[k];
+        p.cv[k] = hp->cv[k];
+        p.gm1[k] = hp->gamma[k] - 1.0;
+        p.gpinf[k] = hp->gamma[k] * hp->pinf[k];
+        p.k0[k] = hp->k0[k];
+        p.mu[k] = hp->mu[k];
+        p.bc[k] = hp->bc[k];
+    }
+    p.k_exp = hp->k_exp;
+    p.T_ref = hp->T_ref;
+    p.cfl = hp->cfl;
+    p.dx = dx;
+    p.dy = dy;
+    p.idx2 = 1.0 / (dx * dx);
+    p.idy2 = 1.0 / (dy * dy);
+    p.nx = nx;
+    p.ny = ny;
+    p.n = nx * ny;
+    p.limiter = hp->limiter;
+    p.trelax = hp->trelax;
+    p.n_outer = hp->n_outer;
+    p.p_policy = hp->p_policy;
+    p.p_fixed = hp->p_fixed;
+    p.p_min = hp->p_min;
+    p.p_max = hp->p_max;
+    c->stream = (cudaStream_t)cuda_stream;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { free(c); return DIM_ECUDA; }
+    c->device = dev;
+    if (dev < 64 && !g_setup_done[dev]) {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            dimk::sweep_setup() != cudaSuccess || dimk::parabolic_setup(nsm) != cudaSuccess) {
+            free(c);
+            return DIM_ECUDA;
+        }
+        g_setup_done[dev] = true;
+    }
+    size_t plane = sizeof(double) * (size_t)p.n;
+    if (cudaMalloc(&c->U2, 8 * plane) != cudaSuccess || cudaMalloc(&c->S, 8 * plane) != cudaSuccess ||
+        cudaMalloc(&c->sc, sizeof(Scalars)) != cudaSuccess || cudaMemset(c->sc, 0, sizeof(Scalars)) != cudaSuccess) {
+        dim_destroy(c);
+        return DIM_ECUDA;
+    }
+    *out = c;
+    return DIM_OK;
+}
+
+void dim_destroy(dim_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->U2);
+    cudaFree(c->S);
+    cudaFree(c->Uh);
+    cudaFree(c->sc);
+    for (int i = 0; i < c->caprec; i++) {
+        if (c->recs[i].a) cudaEventDestroy(c->recs[i].a);
+        if (c->recs[i].b) cudaEventDestroy(c->recs[i].b);
+    }
+    free(c->recs);
+    free(c);
+}
+
+int dim_from_primitive(dim_ctx *c, const double *prim, double *U)
+{
+    if (!c || !prim || !U) return DIM_EINVAL;
+    TRY(dimk::launch_from_primitive(c->p, prim, U, c->sc, c->stream));
+    return DIM_OK;
+}
+
+int dim_cfl_dt(dim_ctx *c, const double *U, double *dt)
+{
+    if (!c || !U || !dt) return DIM_EINVAL;
+    TRY(reset_accumulators(c));
+    TIMED(c, K_WAVE, dimk::launch_wave_max(c->p, U, c->sc, c->stream));
+    unsigned long long bits = 0;
+    TRY(cudaMemcpyAsync(&bits, &c->sc->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    double smax;
+    memcpy(&smax, &bits, sizeof(smax));
+    *dt = c->p.cfl / smax;
+    return DIM_OK;
+}
+
+static int status_to_code(unsigned st)
+{
+    if (st & DIM_ST_TIMEOUT) return DIM_ETIMEOUT;
+    if (st & (DIM_ST_NONPHYS | DIM_ST_NAN)) return DIM_ENONPHYS;
+    if (st & DIM_ST_NOROOT) return DIM_ENOROOT;
+    return DIM_OK;
+}
+
+// one split step on U (device); stages in the order of Sec. 3
+static int step_once(dim_ctx *c, double *U)
+{
+    const dim_params &h = c->hp;
+    const DevParams &p = c->p;
+    const bool vis = viscous_on(h), heat = heat_on(h), trx = h.trelax == DIM_TRELAX_EQUILIBRIUM;
+    const bool sx = p.nx > 1, sy = p.ny > 1;
+    // the kernel that ends the step also checks the end-of-step state
+    enum { LAST_SX, LAST_SY, LAST_VX, LAST_VY, LAST_TR, LAST_HEAT } last;
+    if (heat) last = LAST_HEAT;
+    else if (trx) last = LAST_TR;
+    else if (vis) last = sy ? LAST_VY : LAST_VX;
+    else last = sy ? LAST_SY : LAST_SX;
+
+    TRY(reset_accumulators(c));
+    TIMED(c, K_WAVE, dimk::launch_wave_max(p, U, c->sc, c->stream));
+    double *cur = U, *oth = c->U2;
+    if (sx) {
+        TIMED(c, K_SWEEP_X, dimk::launch_sweep(p, 0, cur, oth, 0.0, c->sc, 1, last == LAST_SX, c->stream));
+        double *t = cur; cur = oth; oth = t;
+    }
+    if (sy) {
+        TIMED(c, K_SWEEP_Y, dimk::launch_sweep(p, 1, cur, oth, 0.0, c->sc, 1, last == LAST_SY, c->stream));
+        double *t = cur; cur = oth; oth = t;
+    }
+    if (vis) {
+        if (sx) TIMED(c, K_VISC_X, dimk::launch_visc(p, 0, cur, visc_scratch(c), c->sc, 0.0, !sy, last == LAST_VX, c->stream));
+        if (sy) TIMED(c, K_VISC_Y, dimk::launch_visc(p, 1, cur, visc_scratch(c), c->sc, 0.0, 1, last == LAST_VY, c->stream));
+    }
+    if (heat) {
+        TIMED(c, K_HEAT, dimk::launch_heat(p, cur, heat_scratch(c), c->sc, 0.0, 1, 1, c->stream));
+    } else if (trx) {
+        TIMED(c, K_RELAX, dimk::launch_relax(p, cur, c->sc, DIM_RELAX_TEMPERATURE, 1, c->stream));
+    }
+    if (cur != U) TIMED(c, K_COPY, cudaMemcpyAsync(U, cur, sizeof(double) * 8 * (size_t)p.n, cudaMemcpyDeviceToDevice, c->stream));
+    return DIM_OK;
+}
+
+static int read_back(dim_ctx *c, double *dt_last)
+{
+    unsigned long long bits = 0;
+    unsigned st = 0;
+    TRY(cudaMemcpyAsync(&bits, &c->sc->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaMemcpyAsync(&st, &c->sc->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    if (dt_last) {
+        double smax;
+        memcpy(&smax, &bits, sizeof(smax));
+        *dt_last = c->p.cfl / smax;
+    }
+    return status_to_code(st);
+}
+
+int dim_step(dim_ctx *c, double *U, int nsteps, double *dt_last)
+{
+    if (!c || !U || nsteps < 0) return DIM_EINVAL;
+    for (int s = 0; s < nsteps; s++) {
+        int r = step_once(c, U);
+        if (r != DIM_OK) return r;
+    }
+    if (dt_last && nsteps > 0) return read_back(c, dt_last);
+    return DIM_OK;
+}
+
+int dim_step_host(dim_ctx *c, double *U_host, int nsteps, double *dt_last)
+{
+    if (!c || !U_host || nsteps < 0) return DIM_EINVAL;
+    size_t bytes = sizeof(double) * 8 * (size_t)c->p.n;
+    if (!c->Uh && cudaMalloc(&c->Uh, bytes) != cudaSuccess) return DIM_ECUDA;
+    TRY(cudaMemcpyAsync(c->Uh, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    for (int s = 0; s < nsteps; s++) {
+        int r = step_once(c, c->Uh);
+        if (r != DIM_OK) return r;
+    }
+    TRY(cudaMemcpyAsync(U_host, c->Uh, bytes, cudaMemcpyDeviceToHost, c->stream));
+    double dtl = 0.0;
+    int r = read_back(c, &dtl);
+    if (dt_last) *dt_last = dtl;
+    return r;
+}
+
+int dim_hllc_sweep(dim_ctx *c, double *U, int axis, double dt, int relax)
+{
+    if (!c || !U || (axis != 0 && axis != 1) || !(dt > 0.0)) return DIM_EINVAL;
+    TRY(reset_accumulators(c));
+    TIMED(c, axis == 0 ? K_SWEEP_X : K_SWEEP_Y, dimk::launch_sweep(c->p, axis, U, c->U2, dt, c->sc, relax, 0, c->stream));
+    TIMED(c, K_COPY, cudaMemcpyAsync(U, c->U2, sizeof(double) * 8 * (size_t)c->p.n, cudaMemcpyDeviceToDevice, c->stream));
+    return DIM_OK;
+}
+
+int dim_relax(dim_ctx *c, double *U, int which)
+{
+    if (!c || !U || (which != DIM_RELAX_PRESSURE && which != DIM_RELAX_TEMPERATURE)) return DIM_EINVAL;
+    TIMED(c, K_RELAX, dimk::launch_relax(c->p, U, c->sc, which, 0, c->stream));
+    return DIM_OK;
+}
+
+int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
+{
+    if (!c || !U || !(dt > 0.0)) return DIM_EINVAL;
+    TRY(reset_accumulators(c));
+    int slot = 0;
+    if (kind == DIM_PARABOLIC_HEAT) {
+        TIMED(c, K_HEAT, dimk::launch_heat(c->p, U, heat_scratch(c), c->sc, dt, 0, 0, c->stream));
+        slot = 0;
+    } else if (kind == DIM_PARABOLIC_VISCOUS_X || kind == DIM_PARABOLIC_VISCOUS_Y) {
+        int axis = kind == DIM_PARABOLIC_VISCOUS_X ? 0 : 1;
+        if ((axis == 0 ? c->p.nx : c->p.ny) < 2) {
+            if (P_used) *P_used = 0;
+            return DIM_OK;
+        }
+        TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y,
+              dimk::launch_visc(c->p, axis, U, visc_scratch(c), c->sc, dt, 0, 0, c->stream));
+        slot = 1 + axis;
+    } else {
+        return DIM_EINVAL;
+    }
+    if (P_used) {
+        int P = 0;
+        unsigned st = 0;
+        TRY(cudaMemcpyAsync(&P, &c->sc->P[slot], sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        TRY(cudaMemcpyAsync(&st, &c->sc->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+        TRY(cudaStreamSynchronize(c->stream));
+        *P_used = P;
+        if (st & DIM_ST_TIMEOUT) return DIM_ETIMEOUT;
+    }
+    return DIM_OK;
+}
+
+int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const double *dJ_dUT, double *dJ_dU0,
+             double *dJ_dparams)
+{
+    (void)c; (void)U0; (void)nsteps; (void)ckpt_every; (void)dJ_dUT; (void)dJ_dU0; (void)dJ_dparams;
+    return DIM_ENOTIMPL;
+}
+
+int dim_status(dim_ctx *c, unsigned *flags, int reset)
+{
+    if (!c || !flags) return DIM_EINVAL;
+    TRY(cudaMemcpyAsync(flags, &c->sc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    if (reset) TRY(cudaMemsetAsync(&c->sc->status, 0, sizeof(unsigned), c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    return DIM_OK;
+}
+
+int dim_profile(dim_ctx *c, int enable, int reset)
+{
+    if (!c) return DIM_EINVAL;
+    if (reset) {
+        TRY(cudaStreamSynchronize(c->stream));
+        c->nrec = 0;
+    }
+    c->prof = enable != 0;
+    return DIM_OK;
+}
+
+int dim_kernel_time(dim_ctx *c, const char *name, int *launches, double *ms)
+{
+    if (!c || !name || !launches || !ms) return DIM_EINVAL;
+    int kid = -1;
+    for (int k = 0; k < K_NKERNELS; k++)
+        if (strcmp(name, kKernelNames[k]) == 0) kid = k;
+    if (kid < 0) return DIM_EINVAL;
+    TRY(cudaStreamSynchronize(c->stream));
+    int cnt = 0;
+    double tot = 0.0;
+    for (int i = 0; i < c->nrec; i++) {
+        if (c->recs[i].kid != kid) continue;
+        float t = 0.0f;
+        TRY(cudaEventElapsedTime(&t, c->recs[i].a, c->recs[i].b));
+        tot += t;
+        cnt++;
+    }
+    *launches = cnt;
+    *ms = tot;
+    return DIM_OK;
+}
+
+}  // extern "C"

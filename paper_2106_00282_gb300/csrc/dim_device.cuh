@@ -1,0 +1,303 @@
+// dim_device.cuh -- device building blocks of the split step (sm_103a).
+//
+// Stiffened-gas thermodynamics, the three-step pressure relaxation, the p,T
+// equilibrium used by the temperature relaxation and the conduction
+// projection, the HLLC face solver and a bounded grid-wide barrier for the
+// cooperative (persistent) parabolic kernels.
+//
+// Paper: Zhang, Menshov, Wang & Shen, arXiv:2106.00282 (equations cited at the
+// functions).  Phase 0 is the dense phase, phase 1 the gas; alpha = alpha_2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dim.h"
+
+namespace dimk {
+
+constexpr int NQ = 8;     // conserved planes
+constexpr int PMAX = 64;  // largest Chebyshev parameter count a launch supports
+
+// Parameters as passed by value to every kernel.
+struct DevParams {
+    double g[2], pinf[2], cv[2];
+    double gm1[2];    // gamma_k - 1
+    double gpinf[2];  // gamma_k pinf_k
+    double k0[2], k_exp, T_ref;
+    double mu[2];
+    double cfl;
+    double dx, dy, idx2, idy2;  // spacing and 1/h^2
+    int nx, ny, n;
+    int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
+};
+
+// Device scalars of one context.  The fields before `status` are cleared at
+// the start of every step / stage call; status and the barrier generation
+// persist.
+struct Scalars {
+    unsigned long long smax;     // max (|u|+c)/h of the step (bits of a non-negative double)
+    unsigned long long lam[12];  // Gershgorin lambda_max per LIM solve (heat iterations 0..7, viscous x, y)
+    int P[12];                   // Chebyshev parameter count used: [0] heat, [1] viscous x, [2] viscous y
+    unsigned int bar_count;      // grid barrier: arrivals of the current generation
+    unsigned int status;         // DIM_ST_* bits
+    unsigned int bar_gen;        // grid barrier: generation
+};
+constexpr int LAM_VX = 8, LAM_VY = 9;
+
+// scratch planes of the parabolic stages (n doubles each)
+struct HeatScratch {
+    double *T0, *V, *L, *va, *vb, *Ti, *Ai;
+};
+struct ViscScratch {
+    double *V, *A2, *u0, *w0, *ua, *ub, *wa, *wb;
+};
+
+__device__ __forceinline__ double dmax_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v)
+{
+    // non-negative doubles order like their bit patterns
+    atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ void flag(Scalars *sc, unsigned bits)
+{
+    if (bits) atomicOr(&sc->status, bits);
+}
+
+// ---------------------------------------------------------------------------
+// Stiffened gas (Eqs. eos_stiffened, eos_stiffened2 with q_k = 0)
+// ---------------------------------------------------------------------------
+// p_k = (gamma_k - 1) E_k / alpha_k - gamma_k pinf_k, E_k = alpha_k rho_k e_k
+__device__ __forceinline__ double sg_p(const DevParams &p, int k, double Ek, double ak)
+{
+    return p.gm1[k] * Ek / ak - p.gpinf[k];
+}
+// E_k = alpha_k (p + gamma_k pinf_k) / (gamma_k - 1)
+__device__ __forceinline__ double sg_E(const DevParams &p, int k, double pr, double ak)
+{
+    return ak * (pr + p.gpinf[k]) / p.gm1[k];
+}
+// c_k^2 = gamma_k (p_k + pinf_k) / rho_k  (Eq. AK)
+__device__ __forceinline__ double sg_c2(const DevParams &p, int k, double pr, double rho)
+{
+    return p.g[k] * (pr + p.pinf[k]) / rho;
+}
+
+// mixture sound speed c^2 = Y1 c1^2 + Y2 c2^2 of a cell (Sec. 3.1)
+__device__ __forceinline__ double cell_c(const DevParams &p, double m1, double m2, double E1, double E2, double a2)
+{
+    double a1 = 1.0 - a2;
+    double p1 = sg_p(p, 0, E1, a1), p2 = sg_p(p, 1, E2, a2);
+    double c1 = sg_c2(p, 0, p1, m1 / a1), c2 = sg_c2(p, 1, p2, m2 / a2);
+    return sqrt((m1 * c1 + m2 * c2) / (m1 + m2));
+}
+
+// conductivity lambda_k(T) = k0_k (T / T_ref)^k_exp
+__device__ __forceinline__ double cond(const DevParams &p, int k, double T)
+{
+    double t = T / p.T_ref;
+    double e = p.k_exp;
+    if (e == 0.0) return p.k0[k];
+    if (e == floor(e) && e > 0.0 && e <= 8.0) {
+        double r = t;
+        for (int i = 1; i < (int)e; i++) r = r * t;
+        return p.k0[k] * r;
+    }
+    return p.k0[k] * pow(t, e);
+}
+
+// end-of-step admissibility: alpha in (0,1), m_k > 0, p_k + pinf_k > 0, no NaN
+__device__ __forceinline__ unsigned check_state(const DevParams &p, const double *q)
+{
+    unsigned st = 0;
+    double a2 = q[7], a1 = 1.0 - a2;
+    double p1 = sg_p(p, 0, q[4], a1), p2 = sg_p(p, 1, q[5], a2);
+    if (!(a2 > 0.0 && a2 < 1.0 && q[0] > 0.0 && q[1] > 0.0 && p1 + p.pinf[0] > 0.0 && p2 + p.pinf[1] > 0.0))
+        st |= DIM_ST_NONPHYS;
+#pragma unroll
+    for (int k = 0; k < NQ; k++)
+        if (isnan(q[k])) st |= DIM_ST_NAN;
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// Pressure relaxation, Sec. 3.3 (three steps), on one cell in place.
+// q in the global plane order.  Returns DIM_ST_* bits of inadmissible results.
+// ---------------------------------------------------------------------------
+// Step (1): with p_I the relaxed pressure, dE_k = -p da_k and the EOS give
+// a_k(p) = (A_k + B_k p) / (gamma_k (p + pinf_k)), A_k = (g_k-1) E_k^0,
+// B_k = (g_k-1) a_k^0; a_1(p) + a_2(p) = 1 is a quadratic whose larger root is
+// the unique one with p + pinf_k > 0.  Step (2): p from the mixture energy.
+// Step (3): E_k = E_k(p, a_k).
+__device__ __forceinline__ unsigned prelax(const DevParams &p, double *q)
+{
+    const double g1 = p.g[0], g2 = p.g[1];
+    double a2 = q[7], a1 = 1.0 - a2;
+    double ak1 = p.gm1[0] * q[4], bk1 = p.gm1[0] * a1, ek1 = p.gpinf[0];
+    double ak2 = p.gm1[1] * q[5], bk2 = p.gm1[1] * a2, ek2 = p.gpinf[1];
+    double A = g1 * g2 - bk1 * g2 - bk2 * g1;
+    double B = g1 * ek2 + ek1 * g2 - (ak1 * g2 + bk1 * ek2 + ak2 * g1 + bk2 * ek1);
+    double C = ek1 * ek2 - ak1 * ek2 - ak2 * ek1;
+    double disc = B * B - 4.0 * A * C;
+    unsigned st = 0;
+    if (disc < 0.0) { st |= DIM_ST_NOROOT; disc = 0.0; }
+    double sq = sqrt(disc);
+    double pr = B <= 0.0 ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
+    double a2n = (ak2 + bk2 * pr) / (g2 * pr + ek2);
+    double a1n = 1.0 - a2n;
+    double rho = q[0] + q[1];
+    double rhoe = q[6] - 0.5 * (q[2] * q[2] + q[3] * q[3]) / rho;
+    double p2 = (rhoe - (a1n * p.gpinf[0] / p.gm1[0] + a2n * p.gpinf[1] / p.gm1[1])) /
+                (a1n / p.gm1[0] + a2n / p.gm1[1]);
+    q[4] = sg_E(p, 0, p2, a1n);
+    q[5] = sg_E(p, 1, p2, a2n);
+    q[7] = a2n;
+    if (!(a2n > 0.0 && a2n < 1.0 && q[0] > 0.0 && q[1] > 0.0 && p2 + p.pinf[0] > 0.0 && p2 + p.pinf[1] > 0.0))
+        st |= DIM_ST_NONPHYS;
+    if (isnan(p2) || isnan(a2n)) st |= DIM_ST_NAN;
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// p,T equilibrium at fixed m_k and rho e (Sec. 3.4.1 end state; Sec. 3.4.2
+// projection).  With E_k = C_k T + a_k pinf_k: rho e = C T + pinf_1 - B1 a and
+// p1 = p2:  G1C1 T/(1-a) - G2C2 T/a = B1; eliminating T,
+//   qa a^2 + qb a + qc = 0, qa = B1 (G + C), qb = E G - B1 G2C2 - C B1,
+//   qc = -E G2C2, E = rho e - pinf_1;  admissible root (sqrt(d) - qb)/(2 qa).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned equilibrium(const DevParams &p, double m1, double m2, double rhoe, double &T,
+                                                double &a)
+{
+    double C1 = m1 * p.cv[0], C2 = m2 * p.cv[1], C = C1 + C2;
+    double G1C1 = p.gm1[0] * C1, G2C2 = p.gm1[1] * C2, G = G1C1 + G2C2;
+    double B1 = p.pinf[0] - p.pinf[1];
+    double E = rhoe - p.pinf[0];
+    double qa = B1 * (G + C);
+    double qb = E * G - B1 * G2C2 - C * B1;
+    double qc = -E * G2C2;
+    double disc = qb * qb - 4.0 * qa * qc;
+    unsigned st = 0;
+    if (disc < 0.0) { st |= DIM_ST_NOROOT; disc = 0.0; }
+    double sq = sqrt(disc);
+    a = qb > 0.0 ? (-2.0 * qc) / (qb + sq) : (sq - qb) / (2.0 * qa);
+    T = (E + B1 * a) / C;
+    if (!(a > 0.0 && a < 1.0 && T > 0.0)) st |= DIM_ST_NONPHYS;
+    if (isnan(a) || isnan(T)) st |= DIM_ST_NAN;
+    return st;
+}
+
+// mixture temperature of a cell in thermal equilibrium (energy form of Eq. Taverage)
+__device__ __forceinline__ double mixture_T(const DevParams &p, double m1, double m2, double E1, double E2, double a2)
+{
+    double C = m1 * p.cv[0] + m2 * p.cv[1];
+    return (E1 + E2 - (1.0 - a2) * p.pinf[0] - a2 * p.pinf[1]) / C;
+}
+
+// conduction coefficients at (T, a): V = dT/d(rho e) = 1/(C + B1^2/K),
+// K = T sum_k (p + pinf_k)/a_k = T^2 sum_k G_k C_k / a_k^2, and Lam = sum_k a_k lambda_k(T)
+__device__ __forceinline__ void heat_coeffs(const DevParams &p, double m1, double m2, double T, double a2, double &V,
+                                            double &Lam)
+{
+    double a1 = 1.0 - a2;
+    double C1 = m1 * p.cv[0], C2 = m2 * p.cv[1];
+    double B1 = p.pinf[0] - p.pinf[1];
+    double r1 = p.gm1[0] * C1 * T / (a1 * a1);
+    double r2 = p.gm1[1] * C2 * T / (a2 * a2);
+    double K = T * (r1 + r2);
+    V = 1.0 / (C1 + C2 + B1 * B1 / K);
+    Lam = a1 * cond(p, 0, T) + a2 * cond(p, 1, T);
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev local-iteration parameters (Sec. 3.2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cheb_P(const DevParams &p, double tau, double lam, unsigned &capped)
+{
+    int pf = (int)ceil(3.14159265358979323846 / 4.0 * sqrt(tau * lam + 1.0));
+    capped = 0;
+    if (p.p_policy == DIM_P_FIXED) return p.p_fixed;
+    int P = pf;
+    if (p.p_policy == DIM_P_CLAMP && P < p.p_min) P = p.p_min;
+    if (P > p.p_max) P = p.p_max;
+    if (P < pf) capped = DIM_ST_PCAP;
+    return P;
+}
+
+// b_1..b_{2P-1} = (a_P..a_2, a_P..a_1), a_m = lam (beta_1 - beta_m)/(1 + beta_1),
+// beta_m = cos((2m-1) pi/(2P)) in decreasing order.  One entry per thread of a block.
+__device__ __forceinline__ void cheb_schedule_block(int P, double lam, double *sb)
+{
+    const double pi = 3.14159265358979323846;
+    double beta1 = cos(pi / (2.0 * P));
+    for (int s = threadIdx.x; s < 2 * P - 1; s += blockDim.x) {
+        int m = s < P - 1 ? P - s : 2 * P - 1 - s;  // index of a_m used at position s
+        double bm = cos((2.0 * m - 1.0) * pi / (2.0 * P));
+        sb[s] = lam * (beta1 - bm) / (1.0 + beta1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bounded grid barrier for cooperative launches.  All blocks of the grid are
+// co-resident (cudaLaunchCooperativeKernel), so the wait ends; a wait that
+// exceeds ~2e9 cycles sets DIM_ST_TIMEOUT and returns false, and the caller
+// leaves the kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(Scalars *sc)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire_u32(&sc->bar_gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&sc->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (ld_acquire_u32(&sc->bar_gen) == gen) {
+                __nanosleep(40);
+                if (clock64() - t0 > 2000000000LL) {
+                    atomicOr(&sc->status, DIM_ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// block-wide max of a non-negative double into an accumulator
+__device__ __forceinline__ void block_max_to(unsigned long long *acc, double v)
+{
+    __shared__ double s_w[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) s_w[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        double x = l < nw ? s_w[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (l == 0) atomic_max_pos(acc, x);
+    }
+}
+
+}  // namespace dimk

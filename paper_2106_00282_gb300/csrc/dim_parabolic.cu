@@ -1,0 +1,392 @@
+// dim_parabolic.cu -- parabolic stages by the Chebyshev local-iteration method
+// (Sec. 3.2, Eqs. LIM, LIM_last) as persistent cooperative kernels (sm_103a).
+//
+// The number of Chebyshev parameters P depends on lambda_max, a grid-wide
+// reduction, so it is only known on the device.  One cooperative launch per
+// stage runs: coefficients -> barrier -> lambda_max reduction -> barrier ->
+// schedule b_m (per block, in shared memory) -> 2P-2 predictor sweeps, each
+// followed by a barrier -> the conservative last sweep and the stage's
+// pointwise epilogue.  No host round trip, any P up to PMAX.
+//
+// k_heat   Sec. 3.4.2 / Algorithm 1 (optionally preceded by the temperature
+//          relaxation of Sec. 3.4.1 in the same launch).
+// k_visc   Sec. 3.2 along one axis, optionally followed by the pressure
+//          relaxation of Sec. 3.3.
+#include <cooperative_groups.h>
+
+#include "dim_device.cuh"
+
+namespace dimk {
+
+
+// cell (i, j) of index c and its neighbours with the boundary rule; returns -1
+// for a transmissive wall (no flux through that face)
+struct Nb {
+    int xm, xp, ym, yp;
+};
+
+__device__ __forceinline__ Nb neighbours(const DevParams &p, int c)
+{
+    Nb r;
+    int j = c / p.nx, i = c - j * p.nx;
+    r.xm = r.xp = r.ym = r.yp = -1;
+    if (p.nx > 1) {
+        if (i > 0) r.xm = c - 1;
+        else if (p.bc[0] == DIM_BC_PERIODIC) r.xm = c + p.nx - 1;
+        if (i < p.nx - 1) r.xp = c + 1;
+        else if (p.bc[0] == DIM_BC_PERIODIC) r.xp = c - (p.nx - 1);
+    }
+    if (p.ny > 1) {
+        if (j > 0) r.ym = c - p.nx;
+        else if (p.bc[1] == DIM_BC_PERIODIC) r.ym = c + (p.ny - 1) * p.nx;
+        if (j < p.ny - 1) r.yp = c + p.nx;
+        else if (p.bc[1] == DIM_BC_PERIODIC) r.yp = c - (p.ny - 1) * p.nx;
+    }
+    return r;
+}
+
+// (L_h v)_c = Fx_{+} - Fx_{-} + Fy_{+} - Fy_{-}, F = Lam_f (v_R - v_L) / h^2,
+// Lam_f = mean of the two cells (Eq. qk_dis in flux-difference form)
+__device__ __forceinline__ double lap(const DevParams &p, const Nb &nb, int c, const double *__restrict__ v,
+                                      const double *__restrict__ L)
+{
+    double r = 0.0;
+    double vc = v[c], Lc = L[c];
+    if (p.nx > 1) {
+        double fl = nb.xm >= 0 ? 0.5 * (L[nb.xm] + Lc) * (vc - v[nb.xm]) * p.idx2 : 0.0;
+        double fr = nb.xp >= 0 ? 0.5 * (Lc + L[nb.xp]) * (v[nb.xp] - vc) * p.idx2 : 0.0;
+        r += fr - fl;
+    }
+    if (p.ny > 1) {
+        double fl = nb.ym >= 0 ? 0.5 * (L[nb.ym] + Lc) * (vc - v[nb.ym]) * p.idy2 : 0.0;
+        double fr = nb.yp >= 0 ? 0.5 * (Lc + L[nb.yp]) * (v[nb.yp] - vc) * p.idy2 : 0.0;
+        r += fr - fl;
+    }
+    return r;
+}
+
+// Gershgorin row bound 2 V_c sum_f Lam_f / h_f^2 of A = -V L_h
+__device__ __forceinline__ double gersh(const DevParams &p, const Nb &nb, int c, const double *__restrict__ V,
+                                        const double *__restrict__ L)
+{
+    double Lc = L[c];
+    double s = 0.0;
+    if (p.nx > 1) {
+        double fl = nb.xm >= 0 ? 0.5 * (L[nb.xm] + Lc) : 0.0;
+        double fr = nb.xp >= 0 ? 0.5 * (Lc + L[nb.xp]) : 0.0;
+        s += (fl + fr) * p.idx2;
+    }
+    if (p.ny > 1) {
+        double fl = nb.ym >= 0 ? 0.5 * (L[nb.ym] + Lc) : 0.0;
+        double fr = nb.yp >= 0 ? 0.5 * (Lc + L[nb.yp]) : 0.0;
+        s += (fl + fr) * p.idy2;
+    }
+    return 2.0 * V[c] * s;
+}
+
+__device__ __forceinline__ double read_acc(const unsigned long long *a)
+{
+    unsigned long long v = *(volatile const unsigned long long *)a;
+    return dmax_bits(v);
+}
+
+// ---------------------------------------------------------------------------
+// heat conduction (Algorithm 1 with the LIM)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_heat(const DevParams p, double *__restrict__ U, HeatScratch s,
+                                              Scalars *sc, double dt_host, int trelax_first, int check)
+{
+    __shared__ double s_b[2 * PMAX];
+    const int n = p.n;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const double tau = dt_host > 0.0 ? dt_host : p.cfl / dmax_bits(sc->smax);
+    const int nout = p.n_outer < 1 ? 1 : (p.n_outer > 8 ? 8 : p.n_outer);
+    unsigned st = 0;
+
+    // A. (temperature relaxation,) temperature and frozen coefficients
+    for (int c = t0; c < n; c += nt) {
+        double m1 = U[c], m2 = U[n + c], E1 = U[4 * n + c], E2 = U[5 * n + c], a2 = U[7 * n + c];
+        double T;
+        if (trelax_first) {
+            unsigned r = equilibrium(p, m1, m2, E1 + E2, T, a2);
+            if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+            st |= r & DIM_ST_NAN;
+            U[4 * n + c] = m1 * p.cv[0] * T + (1.0 - a2) * p.pinf[0];
+            U[5 * n + c] = m2 * p.cv[1] * T + a2 * p.pinf[1];
+            U[7 * n + c] = a2;
+            // temperature of the relaxed energies, as a later heat stage would read it
+            T = mixture_T(p, m1, m2, U[4 * n + c], U[5 * n + c], a2);
+        } else {
+            T = mixture_T(p, m1, m2, E1, E2, a2);
+        }
+        s.T0[c] = T;
+        double V, L;
+        heat_coeffs(p, m1, m2, T, a2, V, L);
+        s.V[c] = V;
+        s.L[c] = L;
+    }
+
+    for (int it = 0; it < nout; it++) {
+        if (!grid_barrier(sc)) return;
+        // B. lambda_max (Gershgorin) of this iteration's frozen operator
+        double lm = 0.0;
+        for (int c = t0; c < n; c += nt) lm = fmax(lm, gersh(p, neighbours(p, c), c, s.V, s.L));
+        block_max_to(&sc->lam[it], lm);
+        if (!grid_barrier(sc)) return;
+        double lam = read_acc(&sc->lam[it]);
+        unsigned capped;
+        const int P = cheb_P(p, tau, lam, capped);
+        cheb_schedule_block(P, lam, s_b);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicMax(&sc->P[0], P);
+            if (capped) st |= capped;
+        }
+        __syncthreads();
+        // C. the 2P-2 predictor sweeps from v^(0) = T^n
+        const double *vin = s.T0;
+        for (int m = 1; m <= 2 * P - 2; m++) {
+            double *vout = (m & 1) ? s.va : s.vb;
+            const double bm = s_b[m - 1];
+            const double den = 1.0 + tau * bm;
+            for (int c = t0; c < n; c += nt) {
+                double Lv = lap(p, neighbours(p, c), c, vin, s.L);
+                vout[c] = (s.T0[c] + tau * bm * vin[c] + tau * s.V[c] * Lv) / den;
+            }
+            if (!grid_barrier(sc)) return;
+            vin = vout;
+        }
+        // D. last (explicit, b = 0) sweep in conservative form on the energy and
+        //    the projection onto the p,T-equilibrium manifold
+        if (it == nout - 1) {
+            for (int c = t0; c < n; c += nt) {
+                double q = lap(p, neighbours(p, c), c, vin, s.L);
+                double m1 = U[c], m2 = U[n + c];
+                double rhoe = U[4 * n + c] + U[5 * n + c] + tau * q;
+                double T, a2;
+                unsigned r = equilibrium(p, m1, m2, rhoe, T, a2);
+                double Q[NQ];
+                Q[0] = m1;
+                Q[1] = m2;
+                Q[2] = U[2 * n + c];
+                Q[3] = U[3 * n + c];
+                Q[4] = m1 * p.cv[0] * T + (1.0 - a2) * p.pinf[0];
+                Q[5] = m2 * p.cv[1] * T + a2 * p.pinf[1];
+                Q[6] = U[6 * n + c] + tau * q;
+                Q[7] = a2;
+                U[4 * n + c] = Q[4];
+                U[5 * n + c] = Q[5];
+                U[6 * n + c] = Q[6];
+                U[7 * n + c] = Q[7];
+                if (check) st |= check_state(p, Q) | (r & DIM_ST_NAN);
+                else if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+            }
+        } else {
+            for (int c = t0; c < n; c += nt) {
+                double q = lap(p, neighbours(p, c), c, vin, s.L);
+                double T, a2;
+                unsigned r = equilibrium(p, U[c], U[n + c], U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
+                if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+                s.Ti[c] = T;
+                s.Ai[c] = a2;
+            }
+            if (!grid_barrier(sc)) return;
+            for (int c = t0; c < n; c += nt) {
+                double V, L;
+                heat_coeffs(p, U[c], U[n + c], s.Ti[c], s.Ai[c], V, L);
+                s.V[c] = V;
+                s.L[c] = L;
+            }
+        }
+    }
+    flag(sc, st);
+}
+
+// ---------------------------------------------------------------------------
+// viscous step along one axis (Sec. 3.2)
+// ---------------------------------------------------------------------------
+// rho du_n/dt = d(4/3 mu du_n/dh)/dh, rho du_t/dt = d(mu du_t/dh)/dh by the LIM
+// with V = 1/rho; conservative last sweep on rho u; rho E and E_k from the
+// face fluxes with two-cell face means and u_hat_i in place of u_i.
+template <int AXIS>
+__device__ __forceinline__ void visc_nb(const DevParams &p, int c, int &cm, int &cp)
+{
+    Nb nb = neighbours(p, c);
+    cm = AXIS == 0 ? nb.xm : nb.ym;
+    cp = AXIS == 0 ? nb.xp : nb.yp;
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_visc(const DevParams p, double *__restrict__ U, ViscScratch s, Scalars *sc,
+                                              double dt_host, int relax, int check)
+{
+    __shared__ double s_b[2 * PMAX];
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    constexpr int SLOT = AXIS == 0 ? LAM_VX : LAM_VY;
+    const int n = p.n;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const double tau = dt_host > 0.0 ? dt_host : p.cfl / dmax_bits(sc->smax);
+    const double ih2 = AXIS == 0 ? p.idx2 : p.idy2;
+    const double ih = AXIS == 0 ? 1.0 / p.dx : 1.0 / p.dy;
+    unsigned st = 0;
+
+    // A. velocities, V = 1/rho, alpha_2 snapshot (read by the face means)
+    for (int c = t0; c < n; c += nt) {
+        double rho = U[c] + U[n + c];
+        s.V[c] = 1.0 / rho;
+        s.A2[c] = U[7 * n + c];
+        s.u0[c] = U[QN * n + c] / rho;
+        s.w0[c] = U[QT * n + c] / rho;
+    }
+    if (!grid_barrier(sc)) return;
+    // mixture viscosity of a cell from the alpha snapshot
+    auto mu_of = [&](int c) {
+        double a2 = s.A2[c];
+        return (1.0 - a2) * p.mu[0] + a2 * p.mu[1];
+    };
+    // B. lambda_max with the normal coefficient 4/3 mu (bounds the tangential one too)
+    double lm = 0.0;
+    for (int c = t0; c < n; c += nt) {
+        int cm, cp;
+        visc_nb<AXIS>(p, c, cm, cp);
+        double lc = 4.0 / 3.0 * mu_of(c);
+        double fl = cm >= 0 ? 0.5 * (4.0 / 3.0 * mu_of(cm) + lc) : 0.0;
+        double fr = cp >= 0 ? 0.5 * (lc + 4.0 / 3.0 * mu_of(cp)) : 0.0;
+        lm = fmax(lm, 2.0 * s.V[c] * ((fl + fr) * ih2));
+    }
+    block_max_to(&sc->lam[SLOT], lm);
+    if (!grid_barrier(sc)) return;
+    double lam = read_acc(&sc->lam[SLOT]);
+    unsigned capped;
+    const int P = cheb_P(p, tau, lam, capped);
+    cheb_schedule_block(P, lam, s_b);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicMax(&sc->P[1 + AXIS], P);
+        if (capped) st |= capped;
+    }
+    __syncthreads();
+    // C. predictor sweeps on u_n (4/3 mu) and u_t (mu)
+    const double *uin = s.u0, *win = s.w0;
+    for (int m = 1; m <= 2 * P - 2; m++) {
+        double *uo = (m & 1) ? s.ua : s.ub;
+        double *wo = (m & 1) ? s.wa : s.wb;
+        const double bm = s_b[m - 1];
+        const double den = 1.0 + tau * bm;
+        for (int c = t0; c < n; c += nt) {
+            int cm, cp;
+            visc_nb<AXIS>(p, c, cm, cp);
+            double mc = mu_of(c);
+            double mm = cm >= 0 ? 0.5 * (mu_of(cm) + mc) : 0.0;
+            double mp = cp >= 0 ? 0.5 * (mc + mu_of(cp)) : 0.0;
+            double lnm = cm >= 0 ? 0.5 * (4.0 / 3.0 * mu_of(cm) + 4.0 / 3.0 * mc) : 0.0;
+            double lnp = cp >= 0 ? 0.5 * (4.0 / 3.0 * mc + 4.0 / 3.0 * mu_of(cp)) : 0.0;
+            double uc = uin[c], wc = win[c];
+            double Lu = (cp >= 0 ? lnp * (uin[cp] - uc) * ih2 : 0.0) - (cm >= 0 ? lnm * (uc - uin[cm]) * ih2 : 0.0);
+            double Lw = (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.0) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.0);
+            uo[c] = (s.u0[c] + tau * bm * uc + tau * s.V[c] * Lu) / den;
+            wo[c] = (s.w0[c] + tau * bm * wc + tau * s.V[c] * Lw) / den;
+        }
+        if (!grid_barrier(sc)) return;
+        uin = uo;
+        win = wo;
+    }
+    // D. conservative last sweep and energies
+    for (int c = t0; c < n; c += nt) {
+        int cm, cp;
+        visc_nb<AXIS>(p, c, cm, cp);
+        double mc = mu_of(c);
+        double Fn[2], Ft[2], W[2], aF1[2], aF2[2];
+        for (int sd = 0; sd < 2; sd++) {
+            int cl = sd == 0 ? cm : c, cr = sd == 0 ? c : cp;
+            if ((sd == 0 ? cm : cp) < 0) {
+                Fn[sd] = Ft[sd] = W[sd] = 0.0;
+                aF1[sd] = aF2[sd] = 0.0;
+                continue;
+            }
+            double ml = sd == 0 ? mu_of(cm) : mc, mr = sd == 0 ? mc : mu_of(cp);
+            double lnf = 0.5 * (4.0 / 3.0 * ml + 4.0 / 3.0 * mr);
+            double lmf = 0.5 * (ml + mr);
+            Fn[sd] = lnf * (uin[cr] - uin[cl]) * ih;
+            Ft[sd] = lmf * (win[cr] - win[cl]) * ih;
+            double ubar = 0.5 * (uin[cl] + uin[cr]);
+            double wbar = 0.5 * (win[cl] + win[cr]);
+            W[sd] = ubar * Fn[sd] + wbar * Ft[sd];
+            double a2l = s.A2[cl], a2r = s.A2[cr];
+            aF2[sd] = 0.5 * (a2l + a2r);
+            aF1[sd] = 0.5 * ((1.0 - a2l) + (1.0 - a2r));
+        }
+        double uh = uin[c], wh = win[c];
+        double q[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
+        q[QN] = q[QN] + tau * (Fn[1] - Fn[0]) * ih;
+        q[QT] = q[QT] + tau * (Ft[1] - Ft[0]) * ih;
+        q[6] = q[6] + tau * (W[1] - W[0]) * ih;
+        q[4] = q[4] + tau * (aF1[1] * W[1] - aF1[0] * W[0]) * ih -
+               tau * (uh * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + wh * (aF1[1] * Ft[1] - aF1[0] * Ft[0])) * ih;
+        q[5] = q[5] + tau * (aF2[1] * W[1] - aF2[0] * W[0]) * ih -
+               tau * (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) * ih;
+        if (relax) {
+            unsigned r = prelax(p, q);
+            if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+            st |= r & DIM_ST_NAN;
+        }
+        if (check) st |= check_state(p, q);
+        U[QN * n + c] = q[QN];
+        U[QT * n + c] = q[QT];
+        U[4 * n + c] = q[4];
+        U[5 * n + c] = q[5];
+        U[6 * n + c] = q[6];
+        U[7 * n + c] = q[7];
+    }
+    flag(sc, st);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int g_heat_blocks = 0, g_visc_blocks[2] = {0, 0};
+
+cudaError_t parabolic_setup(int nsm)
+{
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heat, 256, 0);
+    if (e != cudaSuccess) return e;
+    g_heat_blocks = b * nsm;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_visc<0>, 256, 0);
+    if (e != cudaSuccess) return e;
+    g_visc_blocks[0] = b * nsm;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_visc<1>, 256, 0);
+    if (e != cudaSuccess) return e;
+    g_visc_blocks[1] = b * nsm;
+    return cudaSuccess;
+}
+
+static int coop_grid(int maxb, int n)
+{
+    int need = (n + 255) / 256;
+    return need < maxb ? need : maxb;
+}
+
+cudaError_t launch_heat(const DevParams &p, double *U, const HeatScratch &s, Scalars *sc, double dt_host,
+                        int trelax_first, int check, cudaStream_t st)
+{
+    DevParams pp = p;
+    HeatScratch ss = s;
+    void *args[] = {(void *)&pp, (void *)&U, (void *)&ss, (void *)&sc, (void *)&dt_host, (void *)&trelax_first,
+                    (void *)&check};
+    return cudaLaunchCooperativeKernel((const void *)k_heat, dim3(coop_grid(g_heat_blocks, p.n)), dim3(256), args, 0,
+                                       st);
+}
+
+cudaError_t launch_visc(const DevParams &p, int axis, double *U, const ViscScratch &s, Scalars *sc, double dt_host,
+                        int relax, int check, cudaStream_t st)
+{
+    DevParams pp = p;
+    ViscScratch ss = s;
+    void *args[] = {(void *)&pp, (void *)&U, (void *)&ss, (void *)&sc, (void *)&dt_host, (void *)&relax,
+                    (void *)&check};
+    const void *f = axis == 0 ? (const void *)k_visc<0> : (const void *)k_visc<1>;
+    return cudaLaunchCooperativeKernel(f, dim3(coop_grid(g_visc_blocks[axis], p.n)), dim3(256), args, 0, st);
+}
+
+}  // namespace dimk

@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every entry point include/dim.h
+declares; argument validation needs no GPU (no compute call is made here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dim_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_00282_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def test_header_symbols_exported(lib):
+    from paper_2106_00282_gb300 import _lib
+
+    names = _declared()
+    assert "dim_step" in names and "dim_cheb_parabolic" in names
+    assert sorted(_lib.SYMBOLS) == names
+    for n in names:
+        assert getattr(lib, n) is not None, n
+
+
+def test_strerror(lib):
+    assert lib.dim_strerror(0) == b"ok"
+    assert b"non-physical" in lib.dim_strerror(-3)
+
+
+def test_init_rejects_bad_arguments(lib):
+    """Validation happens before any CUDA call."""
+    from paper_2106_00282_gb300 import _lib, inputs
+
+    good = inputs.shock_tube().params
+    ctx = C.c_void_p()
+    cases = [
+        (good, 0, 1, 1e-3, 1e-3),
+        (good, 10, 1, -1.0, 1e-3),
+        (good.replace(gamma=(1.0, 1.4)), 10, 1, 1e-3, 1e-3),
+        (good.replace(cfl=0.0), 10, 1, 1e-3, 1e-3),
+        (good.replace(limiter=7), 10, 1, 1e-3, 1e-3),
+        (good.replace(p_max=65), 10, 1, 1e-3, 1e-3),
+        (good.replace(p_policy=1, p_fixed=0), 10, 1, 1e-3, 1e-3),
+        (good.replace(n_outer=0), 10, 1, 1e-3, 1e-3),
+        (good.replace(bc=(0, 5)), 10, 1, 1e-3, 1e-3),
+    ]
+    for p, nx, ny, dx, dy in cases:
+        s = _lib.make_params(p)
+        assert lib.dim_init(C.byref(ctx), C.byref(s), nx, ny, dx, dy, None) == _lib.DIM_EINVAL
+    assert lib.dim_step(None, None, 1, None) == _lib.DIM_EINVAL
+    assert lib.dim_grad(None, None, 1, 1, None, None, None) == _lib.DIM_ENOTIMPL

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by
+element on the same seeded inputs.  Tolerance: relative L1 per conserved
+field <= 1e-11 (the FP64 target), stage by stage and after 100 full steps;
+edge cases (1D both ways, ragged tiles, tiny grids, periodic walls, first
+order, no relaxation, Algorithm-1 outer iterations, fixed and capped P)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2106_00282_gb300 import build
+
+    build.build()
+    return torch
+
+
+def _solver(torch, wl, params=None):
+    from paper_2106_00282_gb300.api import Solver
+
+    return Solver(params or wl.params, wl.nx, wl.ny, wl.dx, wl.dy)
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy()
+
+
+def rel_l1(a, b):
+    """per-field relative L1 distance, shape (8,)"""
+    num = np.abs(a - b).reshape(8, -1).sum(axis=1)
+    den = np.abs(b).reshape(8, -1).sum(axis=1)
+    return num / np.maximum(den, 1e-300)
+
+
+def assert_parity(a, b, tol=TOL, what=""):
+    e = rel_l1(a, b)
+    assert np.all(e <= tol), f"{what}: rel L1 per field {e}"
+    assert not np.isnan(a).any()
+
+
+def _init_both(torch, O, wl, params=None):
+    p = params or wl.params
+    s = _solver(torch, wl, p)
+    U = s.from_primitive(_dev(torch, wl.prim))
+    Uo = O.from_primitive(p, wl.prim)
+    return s, U, Uo
+
+
+def test_from_primitive_and_dt(torch_cuda, O, I):
+    wl = I.impact(200, 90)
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    assert_parity(_host(U), Uo, 1e-15, "from_primitive")
+    dt = s.cfl_dt(U)
+    assert abs(dt - O.dt(wl.params, Uo, wl.dx, wl.dy)) <= 1e-14 * dt
+
+
+@pytest.mark.parametrize("name", ["impact", "shock_tube", "shock_tube_y", "mixture"])
+@pytest.mark.parametrize("relax", [False, True])
+def test_hllc_sweep(torch_cuda, O, I, name, relax):
+    wl = {"impact": lambda: I.impact(203, 77), "shock_tube": lambda: I.shock_tube(n=333),
+          "shock_tube_y": lambda: I.shock_tube(n=333, axis=1), "mixture": lambda: I.mixture_shock(n=257)}[name]()
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    # a few steps first so that the sweep sees a developed flow
+    s.step(U, 3)
+    Uo = O.step(wl.params, Uo, wl.dx, wl.dy, 3)[0]
+    assert_parity(_host(U), Uo, TOL, "3 steps")
+    Uo = _host(U)
+    dt = O.dt(wl.params, Uo, wl.dx, wl.dy)
+    for axis in (0, 1):
+        if (wl.nx if axis == 0 else wl.ny) < 2:
+            continue
+        s.hllc_sweep(U, axis, dt, relax)
+        Uo, st = O.sweep(wl.params, Uo, wl.dx, wl.dy, axis, dt)
+        if relax:
+            Uo, st = O.prelax(wl.params, Uo)
+        assert_parity(_host(U), Uo, 1e-13, f"sweep axis {axis}")
+
+
+def test_relaxations(torch_cuda, O, I):
+    from test_oracle_relax import _nonequilibrium_state
+    from paper_2106_00282_gb300 import _lib
+
+    for params in (I.impact(8, 8).params, I.shock_tube().params):
+        U0 = _nonequilibrium_state(I, params, 5000, 21, dT=0.3, dp=0.3, dE=1e-3)
+        wl = I.Workload("r", 5000, 1, 1.0, 1.0, params, None)
+        s = _solver(torch_cuda, wl)
+        for which, fn in ((_lib.RELAX_PRESSURE, O.prelax), (_lib.RELAX_TEMPERATURE, O.trelax)):
+            U = _dev(torch_cuda, U0)
+            s.relax(U, which)
+            Uo, st = fn(params, U0)
+            assert_parity(_host(U), Uo, 1e-12, f"relax {which}")
+
+
+@pytest.mark.parametrize("case", ["disc", "mixture", "periodic", "outer2", "fixedP"])
+def test_heat_stage(torch_cuda, O, I, case):
+    from paper_2106_00282_gb300 import _lib
+
+    if case == "disc":
+        wl = I.conduction_disc(n=131, p_min=4, p_max=12)
+    elif case == "mixture":
+        wl = I.mixture_shock(n=301)
+    elif case == "periodic":
+        wl = I.conduction_disc(n=64, p_min=3, p_max=9)
+        wl.params = wl.params.replace(bc=(1, 1))
+    elif case == "outer2":
+        wl = I.conduction_disc(n=72, p_min=5, p_max=12)
+        wl.params = wl.params.replace(n_outer=2)
+    else:
+        wl = I.shock_tube(n=517)
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    tau = {"disc": 2e-5, "mixture": 1e-6, "periodic": 4e-5, "outer2": 2e-5, "fixedP": 2e-6}[case]
+    P = s.cheb_parabolic(U, _lib.PARABOLIC_HEAT, tau)
+    Uo, st, Po = O.heat(wl.params, Uo, wl.dx, wl.dy, tau)
+    assert P == Po
+    assert_parity(_host(U), Uo, 1e-12, f"heat {case} P={P}")
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_viscous_stage(torch_cuda, O, I, axis):
+    from paper_2106_00282_gb300 import _lib
+
+    wl = I.impact(150, 70)
+    wl.params = wl.params.replace(mu=(50.0, 2.0))
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    s.step(U, 4)
+    Uo = O.step(wl.params, Uo, wl.dx, wl.dy, 4)[0]
+    Uo = _host(U)
+    tau = 2e-7
+    P = s.cheb_parabolic(U, _lib.PARABOLIC_VISCOUS_X if axis == 0 else _lib.PARABOLIC_VISCOUS_Y, tau)
+    Uo, st, Po = O.viscous(wl.params, Uo, wl.dx, wl.dy, axis, tau)
+    assert P == Po
+    assert_parity(_host(U), Uo, 1e-12, f"viscous {axis}")
+
+
+CASES = {
+    # the benchmark workloads at reduced size, 100 steps
+    "shock_tube_1000": lambda I: I.shock_tube(n=1000),
+    "impact_160x80": lambda I: I.impact(160, 80),
+    "conduction_96": lambda I: I.conduction_disc(n=96),
+    "mixture_shock": lambda I: I.mixture_shock(n=400),
+    # edge cases
+    "shock_tube_column": lambda I: I.shock_tube(n=300, axis=1),
+    "ragged_131x37": lambda I: I.impact(131, 37),
+    "tiny_7x5": lambda I: I.impact(7, 5),
+    "pvt_periodic": lambda I: I.pvt_translation(n=150, k=(0.6, 0.026)),
+    "first_order": lambda I: I.shock_tube(n=400, limiter=0),
+    "no_relaxation": lambda I: I.shock_tube(n=400, k=(0, 0), trelax=0),
+    "viscous_shock": lambda I: I.shock_tube(n=400, k=(1e6, 1e6), mu=(500.0, 1.0), p_policy=0),
+    "capped_P": lambda I: I.shock_tube(n=300, k=(1e7, 1e7), p_policy=0),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_step_parity_100(torch_cuda, O, I, case):
+    wl = CASES[case](I)
+    params = wl.params
+    if case == "capped_P":
+        params = params.replace(p_max=6)
+    s, U, Uo = _init_both(torch_cuda, O, wl, params)
+    nst = 100
+    dt = s.step(U, nst)
+    Uo, st, dto, ph = O.step(params, Uo, wl.dx, wl.dy, nst)
+    assert st & 3 == 0
+    assert abs(dt - dto) <= 1e-9 * dto
+    assert_parity(_host(U), Uo, TOL, case)
+    from paper_2106_00282_gb300 import _lib
+
+    sts = s.status()
+    assert sts & (_lib.ST_NONPHYS | _lib.ST_NAN | _lib.ST_TIMEOUT) == 0
+    if case == "capped_P":
+        assert sts & _lib.ST_PCAP
+
+
+def test_single_cell(torch_cuda, O, I):
+    """nx = ny = 1: no sweep, only the pointwise relaxations and a flux-free heat stage."""
+    wl = I.impact(1, 1)
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    s.step(U, 3)
+    Uo = O.step(wl.params, Uo, wl.dx, wl.dy, 3)[0]
+    assert_parity(_host(U), Uo, TOL, "1x1")
+
+
+def test_host_entry_point(torch_cuda, O, I):
+    """dim_step_host (host buffers, copies inside) equals the device path."""
+    wl = I.impact(120, 60)
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    Uh = _host(U).copy()
+    Ut = torch_cuda.from_numpy(Uh).pin_memory()
+    s.step_host(Ut, 5)
+    s.step(U, 5)
+    assert np.array_equal(Ut.numpy(), _host(U))
+
+
+def test_nonphysical_input_is_reported(torch_cuda, O, I):
+    """A corrupted state (alpha_2 > 1 in one cell, made on the host) is reported
+    as DIM_ENONPHYS after the step; the context stays usable."""
+    from paper_2106_00282_gb300 import _lib
+
+    wl = I.shock_tube(n=200)
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    bad = _host(U).copy()
+    bad[7, 0, 50] = 1.5
+    Ub = _dev(torch_cuda, bad)
+    with pytest.raises(_lib.DimError) as e:
+        s.step(Ub, 1)
+    assert e.value.code == _lib.DIM_ENONPHYS
+    s.status(reset=True)
+    s.step(U, 2)
+    assert s.status() & _lib.ST_NONPHYS == 0
+
+
+@pytest.mark.parametrize("which", ["impact", "conduction"])
+def test_full_size_parity(torch_cuda, O, I, which):
+    """At the benchmark sizes (1024 x 512 impact; 2048^2 conduction disc), in the
+    launch configuration the benchmark times, against the oracle over the whole
+    grid after the first steps."""
+    wl = I.impact() if which == "impact" else I.conduction_disc()
+    nst = 2 if which == "impact" else 1
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    s.step(U, nst)
+    Uo, st, dto, ph = O.step(wl.params, Uo, wl.dx, wl.dy, nst)
+    assert_parity(_host(U), Uo, TOL, which)
