@@ -502,7 +502,18 @@ typedef struct {
     double dx, dy;
     int bc[2];
     double *lx, *ly;
+    double idx2, idy2; /* the 1/h^2 factors of Eq. (qk_dis), formed once per grid */
 } orc_op;
+
+static void op_init(orc_op *o, int nx, int ny, double dx, double dy, const int *bc)
+{
+    o->nx = nx; o->ny = ny; o->dx = dx; o->dy = dy;
+    o->bc[0] = bc[0]; o->bc[1] = bc[1];
+    o->idx2 = 1.0 / (dx * dx);
+    o->idy2 = 1.0 / (dy * dy);
+    o->lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
+    o->ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+}
 
 static void op_apply(const orc_op *o, const double *v, double *out)
 {
@@ -512,14 +523,14 @@ static void op_apply(const orc_op *o, const double *v, double *out)
             double r = 0.0;
             if (nx > 1) {
                 int il = i == 0 ? nx - 1 : i - 1, ir = i == nx - 1 ? 0 : i + 1;
-                double fl = o->lx[j * (nx + 1) + i] * (v[j * nx + i] - v[j * nx + il]) / (o->dx * o->dx);
-                double fr = o->lx[j * (nx + 1) + i + 1] * (v[j * nx + ir] - v[j * nx + i]) / (o->dx * o->dx);
+                double fl = o->lx[j * (nx + 1) + i] * (v[j * nx + i] - v[j * nx + il]) * o->idx2;
+                double fr = o->lx[j * (nx + 1) + i + 1] * (v[j * nx + ir] - v[j * nx + i]) * o->idx2;
                 r += fr - fl;
             }
             if (ny > 1) {
                 int jl = j == 0 ? ny - 1 : j - 1, jr = j == ny - 1 ? 0 : j + 1;
-                double fl = o->ly[j * nx + i] * (v[j * nx + i] - v[jl * nx + i]) / (o->dy * o->dy);
-                double fr = o->ly[(j + 1) * nx + i] * (v[jr * nx + i] - v[j * nx + i]) / (o->dy * o->dy);
+                double fl = o->ly[j * nx + i] * (v[j * nx + i] - v[jl * nx + i]) * o->idy2;
+                double fr = o->ly[(j + 1) * nx + i] * (v[jr * nx + i] - v[j * nx + i]) * o->idy2;
                 r += fr - fl;
             }
             out[j * nx + i] = r;
@@ -559,8 +570,8 @@ static double op_lam_max(const orc_op *o, const double *V)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             double s = 0.0;
-            if (nx > 1) s += (o->lx[j * (nx + 1) + i] + o->lx[j * (nx + 1) + i + 1]) / (o->dx * o->dx);
-            if (ny > 1) s += (o->ly[j * nx + i] + o->ly[(j + 1) * nx + i]) / (o->dy * o->dy);
+            if (nx > 1) s += (o->lx[j * (nx + 1) + i] + o->lx[j * (nx + 1) + i + 1]) * o->idx2;
+            if (ny > 1) s += (o->ly[j * nx + i] + o->ly[(j + 1) * nx + i]) * o->idy2;
             double r = 2.0 * V[j * nx + i] * s;
             if (r > lm) lm = r;
         }
@@ -599,9 +610,8 @@ int orc_lim_solve(const orc_params *P, int nx, int ny, double dx, double dy, dou
                   const double *lam, const double *V, const double *v0, double *v1, double *lam_max_out)
 {
     int n = nx * ny;
-    orc_op o = {nx, ny, dx, dy, {P->bc[0], P->bc[1]}, NULL, NULL};
-    o.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
-    o.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+    orc_op o;
+    op_init(&o, nx, ny, dx, dy, P->bc);
     op_faces(&o, lam);
     double lm = op_lam_max(&o, V);
     int Pn = orc_cheb_P(P, tau, lm);
@@ -642,9 +652,8 @@ unsigned orc_heat(const orc_params *P, int nx, int ny, double dx, double dy, dou
     double *lam = (double *)malloc(sizeof(double) * n);
     double *uh = (double *)malloc(sizeof(double) * n);
     double *q = (double *)malloc(sizeof(double) * n);
-    orc_op o = {nx, ny, dx, dy, {P->bc[0], P->bc[1]}, NULL, NULL};
-    o.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
-    o.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+    orc_op o;
+    op_init(&o, nx, ny, dx, dy, P->bc);
     for (int c = 0; c < n; c++) {
         T0[c] = cell_T(P, U, n, c);
         re0[c] = U[4 * n + c] + U[5 * n + c];
@@ -729,12 +738,10 @@ unsigned orc_viscous(const orc_params *P, int nx, int ny, double dx, double dy, 
         un0[c] = U[qn * n + c] / rho;
         ut0[c] = U[qt * n + c] / rho;
     }
-    orc_op o = {nx, ny, dx, dy, {P->bc[0], P->bc[1]}, NULL, NULL};
-    o.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
-    o.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
-    orc_op ot = o;
-    ot.lx = (double *)malloc(sizeof(double) * (nx + 1) * ny);
-    ot.ly = (double *)malloc(sizeof(double) * nx * (ny + 1));
+    orc_op o, ot;
+    op_init(&o, nx, ny, dx, dy, P->bc);
+    op_init(&ot, nx, ny, dx, dy, P->bc);
+    double ih = 1.0 / h; /* the 1/dx factor of the face fluxes of Sec. 3.2, formed once */
     op_faces(&o, ln);
     op_faces(&ot, mu);
     /* restrict both operators to the sweep axis */
@@ -777,8 +784,8 @@ unsigned orc_viscous(const orc_params *P, int nx, int ny, double dx, double dy, 
                 int jl = fp == 0 ? ny - 1 : fp - 1, jr = fp == ny ? 0 : fp;
                 cl = jl * nx + i; cr = jr * nx + i;
             }
-            Fn[s] = lnf * (unh[cr] - unh[cl]) / h;
-            Ft[s] = lmf * (uth[cr] - uth[cl]) / h;
+            Fn[s] = lnf * (unh[cr] - unh[cl]) * ih;
+            Ft[s] = lmf * (uth[cr] - uth[cl]) * ih;
             double ubar = 0.5 * (unh[cl] + unh[cr]);
             double wbar = 0.5 * (uth[cl] + uth[cr]);
             W[s] = ubar * Fn[s] + wbar * Ft[s];
@@ -786,13 +793,13 @@ unsigned orc_viscous(const orc_params *P, int nx, int ny, double dx, double dy, 
             aF2[s] = 0.5 * (a2l + a2r);
             aF1[s] = 0.5 * ((1.0 - a2l) + (1.0 - a2r));
         }
-        newU[qn * n + c] = U[qn * n + c] + tau * (Fn[1] - Fn[0]) / h;
-        newU[qt * n + c] = U[qt * n + c] + tau * (Ft[1] - Ft[0]) / h;
-        newU[6 * n + c] = U[6 * n + c] + tau * (W[1] - W[0]) / h;
-        newU[4 * n + c] = U[4 * n + c] + tau * (aF1[1] * W[1] - aF1[0] * W[0]) / h -
-                          tau * (unh[c] * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + uth[c] * (aF1[1] * Ft[1] - aF1[0] * Ft[0])) / h;
-        newU[5 * n + c] = U[5 * n + c] + tau * (aF2[1] * W[1] - aF2[0] * W[0]) / h -
-                          tau * (unh[c] * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + uth[c] * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) / h;
+        newU[qn * n + c] = U[qn * n + c] + tau * (Fn[1] - Fn[0]) * ih;
+        newU[qt * n + c] = U[qt * n + c] + tau * (Ft[1] - Ft[0]) * ih;
+        newU[6 * n + c] = U[6 * n + c] + tau * (W[1] - W[0]) * ih;
+        newU[4 * n + c] = U[4 * n + c] + tau * (aF1[1] * W[1] - aF1[0] * W[0]) * ih -
+                          tau * (unh[c] * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + uth[c] * (aF1[1] * Ft[1] - aF1[0] * Ft[0])) * ih;
+        newU[5 * n + c] = U[5 * n + c] + tau * (aF2[1] * W[1] - aF2[0] * W[0]) * ih -
+                          tau * (unh[c] * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + uth[c] * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) * ih;
     }
     memcpy(U, newU, sizeof(double) * NQ * n);
     if (P_used) *P_used = Pn;
