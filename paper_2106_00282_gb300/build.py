@@ -21,7 +21,11 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    # --fmad=false: the FP64 kernels round every operation as written (no FMA
+    # contraction), which keeps them bit-compatible with a plain IEEE-754
+    # evaluation of the same formulas
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
+                   "-I", os.path.join(ROOT, "include")]
 
 
 def _stale(out, deps):

@@ -51,6 +51,7 @@ struct dim_ctx {
     double *U2;   // 8 planes: out-of-place target of the sweeps
     double *S;    // 8 scratch planes for the parabolic stages
     double *Uh;   // 8 planes: device copy of a host state (dim_step_host), lazily allocated
+    double *beta; // Chebyshev roots table (PMAX x PMAX)
     Scalars *sc;
     int device;
     // profiling
@@ -213,9 +214,22 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
     }
     size_t plane = sizeof(double) * (size_t)p.n;
     if (cudaMalloc(&c->U2, 8 * plane) != cudaSuccess || cudaMalloc(&c->S, 8 * plane) != cudaSuccess ||
-        cudaMalloc(&c->sc, sizeof(Scalars)) != cudaSuccess || cudaMemset(c->sc, 0, sizeof(Scalars)) != cudaSuccess) {
+        cudaMalloc(&c->sc, sizeof(Scalars)) != cudaSuccess || cudaMemset(c->sc, 0, sizeof(Scalars)) != cudaSuccess ||
+        cudaMalloc(&c->beta, sizeof(double) * dimk::PMAX * dimk::PMAX) != cudaSuccess) {
         dim_destroy(c);
         return DIM_ECUDA;
+    }
+    {
+        // roots of the Chebyshev polynomials T_P, P = 1..PMAX, in decreasing order
+        const double pi = 3.14159265358979323846;
+        double *tab = (double *)calloc((size_t)dimk::PMAX * dimk::PMAX, sizeof(double));
+        if (!tab) { dim_destroy(c); return DIM_ECUDA; }
+        for (int P = 1; P <= dimk::PMAX; P++)
+            for (int m = 1; m <= P; m++) tab[(P - 1) * dimk::PMAX + (m - 1)] = cos((2.0 * m - 1.0) * pi / (2.0 * P));
+        cudaError_t e = cudaMemcpy(c->beta, tab, sizeof(double) * dimk::PMAX * dimk::PMAX, cudaMemcpyHostToDevice);
+        free(tab);
+        if (e != cudaSuccess) { dim_destroy(c); return DIM_ECUDA; }
+        p.beta = c->beta;
     }
     *out = c;
     return DIM_OK;
@@ -229,6 +243,7 @@ void dim_destroy(dim_ctx *c)
     cudaFree(c->S);
     cudaFree(c->Uh);
     cudaFree(c->sc);
+    cudaFree(c->beta);
     for (int i = 0; i < c->caprec; i++) {
         if (c->recs[i].a) cudaEventDestroy(c->recs[i].a);
         if (c->recs[i].b) cudaEventDestroy(c->recs[i].b);

@@ -29,6 +29,9 @@ struct DevParams {
     double dx, dy, idx2, idy2;  // spacing and 1/h^2
     int nx, ny, n;
     int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
+    // roots of T_P: beta[(P-1)*PMAX + m-1] = cos((2m-1) pi / (2P)), m = 1..P,
+    // tabulated on the host (libm) once per context
+    const double *beta;
 };
 
 // Device scalars of one context.  The fields before `status` are cleared at
@@ -148,7 +151,7 @@ __device__ __forceinline__ unsigned prelax(const DevParams &p, double *q)
     double a1n = 1.0 - a2n;
     double rho = q[0] + q[1];
     double rhoe = q[6] - 0.5 * (q[2] * q[2] + q[3] * q[3]) / rho;
-    double p2 = (rhoe - (a1n * p.gpinf[0] / p.gm1[0] + a2n * p.gpinf[1] / p.gm1[1])) /
+    double p2 = (rhoe - (a1n * p.g[0] * p.pinf[0] / p.gm1[0] + a2n * p.g[1] * p.pinf[1] / p.gm1[1])) /
                 (a1n / p.gm1[0] + a2n / p.gm1[1]);
     q[4] = sg_E(p, 0, p2, a1n);
     q[5] = sg_E(p, 1, p2, a2n);
@@ -226,14 +229,13 @@ __device__ __forceinline__ int cheb_P(const DevParams &p, double tau, double lam
 
 // b_1..b_{2P-1} = (a_P..a_2, a_P..a_1), a_m = lam (beta_1 - beta_m)/(1 + beta_1),
 // beta_m = cos((2m-1) pi/(2P)) in decreasing order.  One entry per thread of a block.
-__device__ __forceinline__ void cheb_schedule_block(int P, double lam, double *sb)
+__device__ __forceinline__ void cheb_schedule_block(const DevParams &p, int P, double lam, double *sb)
 {
-    const double pi = 3.14159265358979323846;
-    double beta1 = cos(pi / (2.0 * P));
+    const double *beta = p.beta + (P - 1) * PMAX;
+    double beta1 = beta[0];
     for (int s = threadIdx.x; s < 2 * P - 1; s += blockDim.x) {
         int m = s < P - 1 ? P - s : 2 * P - 1 - s;  // index of a_m used at position s
-        double bm = cos((2.0 * m - 1.0) * pi / (2.0 * P));
-        sb[s] = lam * (beta1 - bm) / (1.0 + beta1);
+        sb[s] = lam * (beta1 - beta[m - 1]) / (1.0 + beta1);
     }
 }
 

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *__restr
         double lam = read_acc(&sc->lam[it]);
         unsigned capped;
         const int P = cheb_P(p, tau, lam, capped);
-        cheb_schedule_block(P, lam, s_b);
+        cheb_schedule_block(p, P, lam, s_b);
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             atomicMax(&sc->P[0], P);
             if (capped) st |= capped;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *__restr
     double lam = read_acc(&sc->lam[SLOT]);
     unsigned capped;
     const int P = cheb_P(p, tau, lam, capped);
-    cheb_schedule_block(P, lam, s_b);
+    cheb_schedule_block(p, P, lam, s_b);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         atomicMax(&sc->P[1 + AXIS], P);
         if (capped) st |= capped;

@@ -45,6 +45,7 @@ def rel_l1(a, b):
 
 def assert_parity(a, b, tol=TOL, what=""):
     e = rel_l1(a, b)
+    print(f"[parity] {what}: max rel L1 {e.max():.3e}, bit-identical cells {np.mean(a == b):.6f}")
     assert np.all(e <= tol), f"{what}: rel L1 per field {e}"
     assert not np.isnan(a).any()
 
