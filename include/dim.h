@@ -87,7 +87,8 @@ typedef struct dim_ctx dim_ctx; /* opaque: parameters, grid, stream, scratch */
 /* Create a context for an nx x ny grid of spacing (dx, dy) and allocate its
  * scratch.  A 1D problem is ny = 1 (or nx = 1); an axis of extent 1 is inactive.
  * cuda_stream is a cudaStream_t (NULL: legacy default stream).
- * Errors: DIM_EINVAL for non-positive sizes/spacings, gamma_k <= 1, Cv_k <= 0,
+ * Errors: DIM_EINVAL for non-positive sizes/spacings, a 1 x 1 grid (no axis,
+ * hence no CFL time scale), gamma_k <= 1, Cv_k <= 0,
  * cfl <= 0, unknown flags, p_max outside [1, 64]; DIM_ECUDA on allocation
  * failure.  The paper's parameters: Sec. 2 (EOS), Sec. 3 (scheme). */
 int dim_init(dim_ctx **out, const dim_params *p, int nx, int ny, double dx, double dy, void *cuda_stream);

@@ -152,6 +152,7 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
     if (!out || !hp) return DIM_EINVAL;
     *out = nullptr;
     if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 27) || !(dx > 0.0) || !(dy > 0.0)) return DIM_EINVAL;
+    if (nx == 1 && ny == 1) return DIM_EINVAL; /* no active axis: no CFL time scale */
     for (int k = 0; k < 2; k++) {
         if (!(hp->gamma[k] > 1.0) || !(hp->cv[k] > 0.0) || !(hp->pinf[k] >= 0.0) || !(hp->k0[k] >= 0.0) ||
             !(hp->mu[k] >= 0.0))

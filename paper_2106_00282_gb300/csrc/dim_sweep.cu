@@ -272,23 +272,27 @@ __global__ void k_from_primitive(const DevParams p, const double *__restrict__ p
     flag(sc, st);
 }
 
-// max over cells of (|u_axis| + c) / h_axis, active axes only
+// max over cells of (|u_axis| + c) / h_axis, active axes only; also checks that
+// the state entering the step is admissible
 __global__ void k_wave_max(const DevParams p, const double *__restrict__ U, Scalars *sc)
 {
     const int n = p.n;
     double m = 0.0;
     unsigned st = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        double m1 = U[c], m2 = U[n + c];
-        double rho = m1 + m2;
-        double cs = cell_c(p, m1, m2, U[4 * n + c], U[5 * n + c], U[7 * n + c]);
+        double q[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
+        st |= check_state(p, q);
+        double rho = q[0] + q[1];
+        double cs = cell_c(p, q[0], q[1], q[4], q[5], q[7]);
         if (p.nx > 1) {
-            double s = (fabs(U[2 * n + c] / rho) + cs) / p.dx;
+            double s = (fabs(q[2] / rho) + cs) / p.dx;
             if (s > m) m = s;
             if (isnan(s)) st |= DIM_ST_NAN;
         }
         if (p.ny > 1) {
-            double s = (fabs(U[3 * n + c] / rho) + cs) / p.dy;
+            double s = (fabs(q[3] / rho) + cs) / p.dy;
             if (s > m) m = s;
             if (isnan(s)) st |= DIM_ST_NAN;
         }

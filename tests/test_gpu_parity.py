@@ -164,32 +164,41 @@ CASES = {
 
 @pytest.mark.parametrize("case", list(CASES))
 def test_step_parity_100(torch_cuda, O, I, case):
-    wl = CASES[case](I)
-    params = wl.params
-    if case == "capped_P":
-        params = params.replace(p_max=6)
-    s, U, Uo = _init_both(torch_cuda, O, wl, params)
-    nst = 100
-    dt = s.step(U, nst)
-    Uo, st, dto, ph = O.step(params, Uo, wl.dx, wl.dy, nst)
-    assert st & 3 == 0
-    assert abs(dt - dto) <= 1e-9 * dto
-    assert_parity(_host(U), Uo, TOL, case)
+    """100 steps (10 for the deliberately under-resolved capped-P case); the
+    status words agree too: the no-relaxation model ends its first step with a
+    transiently negative gas pressure at the interface (the pressure
+    relaxation of the next step repairs it), which both sides report."""
     from paper_2106_00282_gb300 import _lib
 
-    sts = s.status()
-    assert sts & (_lib.ST_NONPHYS | _lib.ST_NAN | _lib.ST_TIMEOUT) == 0
+    wl = CASES[case](I)
+    params = wl.params
+    nst = 100
     if case == "capped_P":
-        assert sts & _lib.ST_PCAP
+        params = params.replace(p_max=6)
+        nst = 10
+    s, U, Uo = _init_both(torch_cuda, O, wl, params)
+    s.step(U, nst, sync=False)
+    sts = s.status()
+    Uo, st, dto, ph = O.step(params, Uo, wl.dx, wl.dy, nst)
+    assert_parity(_host(U), Uo, TOL, case)
+    assert (sts & (_lib.ST_NONPHYS | _lib.ST_NAN)) == (st & 3), (sts, st)
+    assert sts & _lib.ST_TIMEOUT == 0
+    if case not in ("no_relaxation", "capped_P"):
+        assert st & 3 == 0
+    if case == "capped_P":
+        assert sts & _lib.ST_PCAP and st & 32
 
 
-def test_single_cell(torch_cuda, O, I):
-    """nx = ny = 1: no sweep, only the pointwise relaxations and a flux-free heat stage."""
-    wl = I.impact(1, 1)
-    s, U, Uo = _init_both(torch_cuda, O, wl)
-    s.step(U, 3)
-    Uo = O.step(wl.params, Uo, wl.dx, wl.dy, 3)[0]
-    assert_parity(_host(U), Uo, TOL, "1x1")
+def test_two_cells(torch_cuda, O, I):
+    """The smallest grids with an active axis: 2 x 1 and 1 x 2."""
+    for nx, ny in ((2, 1), (1, 2)):
+        wl = I.impact(nx, ny)
+        wl.prim[0].flat[0] = 1e-6
+        wl.prim[3].flat[0] = 100.0
+        s, U, Uo = _init_both(torch_cuda, O, wl)
+        s.step(U, 3)
+        Uo = O.step(wl.params, Uo, wl.dx, wl.dy, 3)[0]
+        assert_parity(_host(U), Uo, TOL, f"{nx}x{ny}")
 
 
 def test_host_entry_point(torch_cuda, O, I):
@@ -203,22 +212,28 @@ def test_host_entry_point(torch_cuda, O, I):
     assert np.array_equal(Ut.numpy(), _host(U))
 
 
-def test_nonphysical_input_is_reported(torch_cuda, O, I):
-    """A corrupted state (alpha_2 > 1 in one cell, made on the host) is reported
-    as DIM_ENONPHYS after the step; the context stays usable."""
+@pytest.mark.parametrize("fault", ["alpha_above_one", "negative_mass", "nan_energy"])
+def test_nonphysical_input_is_reported(torch_cuda, O, I, fault):
+    """A corrupted state (made on the host: alpha_2 > 1, m_1 < 0 or a NaN in one
+    cell) is reported as DIM_ENONPHYS by the step; the context stays usable."""
     from paper_2106_00282_gb300 import _lib
 
     wl = I.shock_tube(n=200)
     s, U, Uo = _init_both(torch_cuda, O, wl)
     bad = _host(U).copy()
-    bad[7, 0, 50] = 1.5
+    if fault == "alpha_above_one":
+        bad[7, 0, 50] = 1.5
+    elif fault == "negative_mass":
+        bad[0, 0, 120] = -1.0
+    else:
+        bad[6, 0, 10] = float("nan")
     Ub = _dev(torch_cuda, bad)
     with pytest.raises(_lib.DimError) as e:
         s.step(Ub, 1)
     assert e.value.code == _lib.DIM_ENONPHYS
     s.status(reset=True)
     s.step(U, 2)
-    assert s.status() & _lib.ST_NONPHYS == 0
+    assert s.status() & (_lib.ST_NONPHYS | _lib.ST_NAN) == 0
 
 
 @pytest.mark.parametrize("which", ["impact", "conduction"])
