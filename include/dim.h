@@ -37,6 +37,7 @@ extern "C" {
 #define DIM_ENOROOT (-4)  /* a relaxation quadratic had no real root */
 #define DIM_ETIMEOUT (-5) /* a bounded grid-wide wait inside a kernel gave up */
 #define DIM_ENOTIMPL (-6) /* entry point not implemented in this build */
+#define DIM_ETOOLARGE (-7) /* grid larger than the fixed scratch of dim_hllc_sweep_noalloc */
 
 /* device status word bits (dim_status) */
 #define DIM_ST_NONPHYS 1u   /* end-of-step state inadmissible */
@@ -145,6 +146,33 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used);
  * implemented in this build: returns DIM_ENOTIMPL. */
 int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const double *dJ_dUT, double *dJ_dU0,
              double *dJ_dparams);
+
+/* The sweep of dim_hllc_sweep without a context and without any allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library allocate device memory -- applications whose own pool
+ * allocator owns all device memory, programs with a device-memory budget fixed
+ * at load time, and loops that cannot afford the device-wide synchronization of
+ * cudaMalloc/cudaFree.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Its scratch (an out-of-place copy of the state and the status
+ * scalars) is a fixed array compiled into the library, DIM_NOALLOC_MAX_CELLS
+ * cells x 8 doubles + 512 B (4 MiB), held by every GPU that loads the library
+ * until the process exits.
+ *  - p, nx, ny, dx, dy: as for dim_init (validated the same way); U: device
+ *    state as everywhere (8 planes, caller-owned), updated in place; axis 0 = x,
+ *    1 = y; dt > 0; relax != 0 applies the Sec. 3.3 pressure relaxation after
+ *    the sweep; cuda_stream: a cudaStream_t (NULL: legacy default stream).
+ *  - Returns DIM_ETOOLARGE if nx * ny > DIM_NOALLOC_MAX_CELLS, DIM_EINVAL for
+ *    invalid arguments, DIM_ECUDA if a CUDA call fails.  Asynchronous.
+ *  - The first call on a device sets that device up (looks up the array's
+ *    device address, sets the kernels' shared-memory limit); make that first
+ *    call before any stream capture.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents (the status scalars are cleared at every call): calls that
+ *    overlap on the GPU (different streams, or different host threads) race and
+ *    give wrong results; serialise them. */
+#define DIM_NOALLOC_MAX_CELLS 65536
+int dim_hllc_sweep_noalloc(const dim_params *p, int nx, int ny, double dx, double dy, double *U, int axis, double dt,
+                           int relax, void *cuda_stream);
 
 /* Read (and clear if reset != 0) the device status word (DIM_ST_* bits);
  * synchronizes. */

@@ -14,6 +14,8 @@ LIB_PATH = os.path.join(HERE, "libdim.so")
 
 # return codes and status bits (include/dim.h)
 DIM_OK, DIM_EINVAL, DIM_ECUDA, DIM_ENONPHYS, DIM_ENOROOT, DIM_ETIMEOUT, DIM_ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
+DIM_ETOOLARGE = -7
+NOALLOC_MAX_CELLS = 65536
 ST_NONPHYS, ST_NAN, ST_NOROOT, ST_TRANSIENT, ST_PCAP, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
 RELAX_PRESSURE, RELAX_TEMPERATURE = 0, 1
 PARABOLIC_HEAT, PARABOLIC_VISCOUS_X, PARABOLIC_VISCOUS_Y = 0, 1, 2
@@ -21,7 +23,7 @@ PARABOLIC_HEAT, PARABOLIC_VISCOUS_X, PARABOLIC_VISCOUS_Y = 0, 1, 2
 # every entry point the header declares
 SYMBOLS = ["dim_init", "dim_destroy", "dim_from_primitive", "dim_cfl_dt", "dim_step", "dim_step_host",
            "dim_hllc_sweep", "dim_relax", "dim_cheb_parabolic", "dim_grad", "dim_status", "dim_profile",
-           "dim_kernel_time", "dim_strerror"]
+           "dim_kernel_time", "dim_strerror", "dim_hllc_sweep_noalloc"]
 
 
 class DimParams(C.Structure):
@@ -83,6 +85,7 @@ def load(path: str = LIB_PATH):
     L.dim_status.argtypes = [vp, C.POINTER(u), i]
     L.dim_profile.argtypes = [vp, i, i]
     L.dim_kernel_time.argtypes = [vp, C.c_char_p, C.POINTER(i), pd]
+    L.dim_hllc_sweep_noalloc.argtypes = [C.POINTER(DimParams), i, i, d, d, vp, i, d, i, vp]
     L.dim_strerror.argtypes = [i]
     L.dim_strerror.restype = C.c_char_p
     for name in SYMBOLS:

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdim.so")
-SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu"]
+SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu"]
 HEADERS = ["dim_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -143,14 +143,19 @@ const char *dim_strerror(int code)
     case DIM_ENOROOT: return "relaxation quadratic without real root";
     case DIM_ETIMEOUT: return "grid barrier wait timed out";
     case DIM_ENOTIMPL: return "not implemented";
+    case DIM_ETOOLARGE: return "grid larger than the fixed scratch of the no-allocation entry point";
     default: return "unknown error";
     }
 }
 
-int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, double dy, void *cuda_stream)
+}  // extern "C"
+
+// Validate a parameter set and a grid and fill the kernels' parameter block.
+// No CUDA call, no allocation.  Shared by dim_init and the no-allocation entry
+// point.
+int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, DevParams *out)
 {
-    if (!out || !hp) return DIM_EINVAL;
-    *out = nullptr;
+    if (!hp || !out) return DIM_EINVAL;
     if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 27) || !(dx > 0.0) || !(dy > 0.0)) return DIM_EINVAL;
     if (nx == 1 && ny == 1) return DIM_EINVAL; /* no active axis: no CFL time scale */
     for (int k = 0; k < 2; k++) {
@@ -167,11 +172,8 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
     if (hp->p_max < 1 || hp->p_max > dimk::PMAX) return DIM_EINVAL;
     if (hp->p_policy == DIM_P_FIXED && (hp->p_fixed < 1 || hp->p_fixed > dimk::PMAX)) return DIM_EINVAL;
     if (hp->p_policy == DIM_P_CLAMP && (hp->p_min < 1 || hp->p_min > hp->p_max)) return DIM_EINVAL;
-
-    dim_ctx *c = (dim_ctx *)calloc(1, sizeof(dim_ctx));
-    if (!c) return DIM_ECUDA;
-    c->hp = *hp;
-    DevParams &p = c->p;
+    DevParams p;
+    memset(&p, 0, sizeof(p));
     for (int k = 0; k < 2; k++) {
         p.g[k] = hp->gamma[k];
         p.pinf[k] = hp->pinf[k];
@@ -199,6 +201,25 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
     p.p_fixed = hp->p_fixed;
     p.p_min = hp->p_min;
     p.p_max = hp->p_max;
+    p.beta = nullptr;
+    *out = p;
+    return DIM_OK;
+}
+
+extern "C" {
+
+int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, double dy, void *cuda_stream)
+{
+    if (!out || !hp) return DIM_EINVAL;
+    *out = nullptr;
+    DevParams pv;
+    int r = dim_host_params(hp, nx, ny, dx, dy, &pv);
+    if (r != DIM_OK) return r;
+    dim_ctx *c = (dim_ctx *)calloc(1, sizeof(dim_ctx));
+    if (!c) return DIM_ECUDA;
+    c->hp = *hp;
+    DevParams &p = c->p;
+    p = pv;
     c->stream = (cudaStream_t)cuda_stream;
 
     int dev = 0;
