@@ -74,10 +74,16 @@ static double phase_p(const orc_params *P, int k, double Ek, double ak)
     return (P->gamma[k] - 1.0) * Ek / ak - P->gamma[k] * P->pinf[k];
 }
 
+/* the material constant 1/(gamma_k - 1) of Eq. (eos_stiffened) */
+static double inv_gm1(const orc_params *P, int k)
+{
+    return 1.0 / (P->gamma[k] - 1.0);
+}
+
 /* phase energy per mixture volume from (p, a_k): E_k = a_k (p + g pinf)/(g-1) */
 static double phase_E(const orc_params *P, int k, double p, double ak)
 {
-    return ak * (p + P->gamma[k] * P->pinf[k]) / (P->gamma[k] - 1.0);
+    return ak * (p + P->gamma[k] * P->pinf[k]) * inv_gm1(P, k);
 }
 
 /* squared phase sound speed c_k^2 = g_k (p_k + pinf_k) / rho_k  (Eq. AK) */
@@ -89,7 +95,7 @@ static double phase_c2(const orc_params *P, int k, double p, double rho)
 /* conductivity law lambda_k(T) = k0_k (T / T_ref)^k_exp */
 static double lambda_k(const orc_params *P, int k, double T)
 {
-    double t = T / P->T_ref;
+    double t = T * (1.0 / P->T_ref);
     double e = P->k_exp;
     if (e == 0.0) return P->k0[k];
     if (e == floor(e) && e > 0.0 && e <= 8.0) {
@@ -155,11 +161,11 @@ double orc_dt(const orc_params *P, int nx, int ny, double dx, double dy, const d
         double rho = U[0 * n + c] + U[1 * n + c];
         double cs = cell_sound_speed(P, U, n, c);
         if (nx > 1) {
-            double s = (fabs(U[2 * n + c] / rho) + cs) / dx;
+            double s = (fabs(U[2 * n + c] / rho) + cs) * (1.0 / dx);
             if (s > smax) smax = s;
         }
         if (ny > 1) {
-            double s = (fabs(U[3 * n + c] / rho) + cs) / dy;
+            double s = (fabs(U[3 * n + c] / rho) + cs) * (1.0 / dy);
             if (s > smax) smax = s;
         }
     }
@@ -369,8 +375,8 @@ static unsigned prelax_cell(const orc_params *P, double *U, int n, int c)
     double rho = m1 + m2;
     double mu = U[2 * n + c], mv = U[3 * n + c];
     double rhoe = U[6 * n + c] - 0.5 * (mu * mu + mv * mv) / rho;
-    double p2 = (rhoe - (a1n * g1 * pi1 / (g1 - 1.0) + a2n * g2 * pi2 / (g2 - 1.0))) /
-                (a1n / (g1 - 1.0) + a2n / (g2 - 1.0));
+    double i1 = inv_gm1(P, 0), i2 = inv_gm1(P, 1);
+    double p2 = (rhoe - (a1n * g1 * pi1 * i1 + a2n * g2 * pi2 * i2)) / (a1n * i1 + a2n * i2);
     /* step (3) */
     U[4 * n + c] = phase_E(P, 0, p2, a1n);
     U[5 * n + c] = phase_E(P, 1, p2, a2n);
