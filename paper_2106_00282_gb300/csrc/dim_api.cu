@@ -179,6 +179,7 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
         p.pinf[k] = hp->pinf[k];
         p.cv[k] = hp->cv[k];
         p.gm1[k] = hp->gamma[k] - 1.0;
+        p.inv_gm1[k] = 1.0 / (hp->gamma[k] - 1.0);
         p.gpinf[k] = hp->gamma[k] * hp->pinf[k];
         p.k0[k] = hp->k0[k];
         p.mu[k] = hp->mu[k];
@@ -186,9 +187,16 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
     }
     p.k_exp = hp->k_exp;
     p.T_ref = hp->T_ref;
+    p.inv_Tref = 1.0 / hp->T_ref;
+    {
+        double e = hp->k_exp;
+        p.k_pow = e == 0.0 ? 0 : ((e == floor(e) && e > 0.0 && e <= 8.0) ? (int)e : -1);
+    }
     p.cfl = hp->cfl;
     p.dx = dx;
     p.dy = dy;
+    p.idx = 1.0 / dx;
+    p.idy = 1.0 / dy;
     p.idx2 = 1.0 / (dx * dx);
     p.idy2 = 1.0 / (dy * dy);
     p.nx = nx;

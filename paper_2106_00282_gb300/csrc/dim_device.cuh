@@ -9,6 +9,7 @@
 // functions).  Phase 0 is the dense phase, phase 1 the gas; alpha = alpha_2.
 #pragma once
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 
 #include "../../include/dim.h"
@@ -21,12 +22,14 @@ constexpr int PMAX = 64;  // largest Chebyshev parameter count a launch supports
 // Parameters as passed by value to every kernel.
 struct DevParams {
     double g[2], pinf[2], cv[2];
-    double gm1[2];    // gamma_k - 1
-    double gpinf[2];  // gamma_k pinf_k
-    double k0[2], k_exp, T_ref;
+    double gm1[2];      // gamma_k - 1
+    double inv_gm1[2];  // 1 / (gamma_k - 1)
+    double gpinf[2];    // gamma_k pinf_k
+    double k0[2], k_exp, T_ref, inv_Tref;
+    int k_pow;          // conductivity exponent: 0 constant, 1..8 integer power, -1 general
     double mu[2];
     double cfl;
-    double dx, dy, idx2, idy2;  // spacing and 1/h^2
+    double dx, dy, idx, idy, idx2, idy2;  // spacing, 1/h and 1/h^2
     int nx, ny, n;
     int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
     // roots of T_P: beta[(P-1)*PMAX + m-1] = cos((2m-1) pi / (2P)), m = 1..P,
@@ -69,6 +72,46 @@ __device__ __forceinline__ void flag(Scalars *sc, unsigned bits)
 }
 
 // ---------------------------------------------------------------------------
+// IEEE-754 ordering decided on the integer pipe.  On GB300 an FP64 compare or
+// min/max issues on the same narrow FP64 pipe as the arithmetic (one warp
+// instruction per 64 cycles per scheduler); these take the same decisions as
+// the IEEE comparisons (NaN compares false, -0 == +0) from the bit patterns.
+// ---------------------------------------------------------------------------
+constexpr long long kAbsMask = 0x7FFFFFFFFFFFFFFFLL, kInfBits = 0x7FF0000000000000LL;
+__device__ __forceinline__ long long bits_of(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool nan_i(double x) { return (bits_of(x) & kAbsMask) > kInfBits; }
+__device__ __forceinline__ bool gt0_i(double x)  // x > 0
+{
+    long long b = bits_of(x);
+    return b > 0 && b <= kInfBits;
+}
+__device__ __forceinline__ bool ge0_i(double x)  // x >= 0
+{
+    long long b = bits_of(x);
+    return (b >= 0 && b <= kInfBits) || b == LLONG_MIN;
+}
+__device__ __forceinline__ bool lt0_i(double x)  // x < 0
+{
+    long long b = bits_of(x), m = b & kAbsMask;
+    return b < 0 && m != 0 && m <= kInfBits;
+}
+__device__ __forceinline__ bool le0_i(double x)  // x <= 0
+{
+    long long b = bits_of(x);
+    return (b < 0 && (b & kAbsMask) <= kInfBits) || b == 0;
+}
+// key monotone in the value, -0 and +0 both 0
+__device__ __forceinline__ long long okey(double x)
+{
+    long long b = bits_of(x);
+    return b >= 0 ? b : (LLONG_MIN - b);
+}
+__device__ __forceinline__ bool lt_i(double x, double y)  // x < y
+{
+    return !nan_i(x) && !nan_i(y) && okey(x) < okey(y);
+}
+
+// ---------------------------------------------------------------------------
 // Stiffened gas (Eqs. eos_stiffened, eos_stiffened2 with q_k = 0)
 // ---------------------------------------------------------------------------
 // p_k = (gamma_k - 1) E_k / alpha_k - gamma_k pinf_k, E_k = alpha_k rho_k e_k
@@ -79,7 +122,7 @@ __device__ __forceinline__ double sg_p(const DevParams &p, int k, double Ek, dou
 // E_k = alpha_k (p + gamma_k pinf_k) / (gamma_k - 1)
 __device__ __forceinline__ double sg_E(const DevParams &p, int k, double pr, double ak)
 {
-    return ak * (pr + p.gpinf[k]) / p.gm1[k];
+    return ak * (pr + p.gpinf[k]) * p.inv_gm1[k];
 }
 // c_k^2 = gamma_k (p_k + pinf_k) / rho_k  (Eq. AK)
 __device__ __forceinline__ double sg_c2(const DevParams &p, int k, double pr, double rho)
@@ -99,15 +142,14 @@ __device__ __forceinline__ double cell_c(const DevParams &p, double m1, double m
 // conductivity lambda_k(T) = k0_k (T / T_ref)^k_exp
 __device__ __forceinline__ double cond(const DevParams &p, int k, double T)
 {
-    double t = T / p.T_ref;
-    double e = p.k_exp;
-    if (e == 0.0) return p.k0[k];
-    if (e == floor(e) && e > 0.0 && e <= 8.0) {
+    if (p.k_pow == 0) return p.k0[k];
+    double t = T * p.inv_Tref;
+    if (p.k_pow > 0) {
         double r = t;
-        for (int i = 1; i < (int)e; i++) r = r * t;
+        for (int i = 1; i < p.k_pow; i++) r = r * t;
         return p.k0[k] * r;
     }
-    return p.k0[k] * pow(t, e);
+    return p.k0[k] * pow(t, p.k_exp);
 }
 
 // end-of-step admissibility: alpha in (0,1), m_k > 0, p_k + pinf_k > 0, no NaN
@@ -116,11 +158,11 @@ __device__ __forceinline__ unsigned check_state(const DevParams &p, const double
     unsigned st = 0;
     double a2 = q[7], a1 = 1.0 - a2;
     double p1 = sg_p(p, 0, q[4], a1), p2 = sg_p(p, 1, q[5], a2);
-    if (!(a2 > 0.0 && a2 < 1.0 && q[0] > 0.0 && q[1] > 0.0 && p1 + p.pinf[0] > 0.0 && p2 + p.pinf[1] > 0.0))
+    if (!(gt0_i(a2) && lt_i(a2, 1.0) && gt0_i(q[0]) && gt0_i(q[1]) && gt0_i(p1 + p.pinf[0]) && gt0_i(p2 + p.pinf[1])))
         st |= DIM_ST_NONPHYS;
 #pragma unroll
     for (int k = 0; k < NQ; k++)
-        if (isnan(q[k])) st |= DIM_ST_NAN;
+        if (nan_i(q[k])) st |= DIM_ST_NAN;
     return st;
 }
 
@@ -144,21 +186,22 @@ __device__ __forceinline__ unsigned prelax(const DevParams &p, double *q)
     double C = ek1 * ek2 - ak1 * ek2 - ak2 * ek1;
     double disc = B * B - 4.0 * A * C;
     unsigned st = 0;
-    if (disc < 0.0) { st |= DIM_ST_NOROOT; disc = 0.0; }
+    if (lt0_i(disc)) { st |= DIM_ST_NOROOT; disc = 0.0; }
     double sq = sqrt(disc);
-    double pr = B <= 0.0 ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
+    double pr = le0_i(B) ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
     double a2n = (ak2 + bk2 * pr) / (g2 * pr + ek2);
     double a1n = 1.0 - a2n;
     double rho = q[0] + q[1];
     double rhoe = q[6] - 0.5 * (q[2] * q[2] + q[3] * q[3]) / rho;
-    double p2 = (rhoe - (a1n * p.g[0] * p.pinf[0] / p.gm1[0] + a2n * p.g[1] * p.pinf[1] / p.gm1[1])) /
-                (a1n / p.gm1[0] + a2n / p.gm1[1]);
+    double p2 = (rhoe - (a1n * p.g[0] * p.pinf[0] * p.inv_gm1[0] + a2n * p.g[1] * p.pinf[1] * p.inv_gm1[1])) /
+                (a1n * p.inv_gm1[0] + a2n * p.inv_gm1[1]);
     q[4] = sg_E(p, 0, p2, a1n);
     q[5] = sg_E(p, 1, p2, a2n);
     q[7] = a2n;
-    if (!(a2n > 0.0 && a2n < 1.0 && q[0] > 0.0 && q[1] > 0.0 && p2 + p.pinf[0] > 0.0 && p2 + p.pinf[1] > 0.0))
+    if (!(gt0_i(a2n) && lt_i(a2n, 1.0) && gt0_i(q[0]) && gt0_i(q[1]) && gt0_i(p2 + p.pinf[0]) &&
+          gt0_i(p2 + p.pinf[1])))
         st |= DIM_ST_NONPHYS;
-    if (isnan(p2) || isnan(a2n)) st |= DIM_ST_NAN;
+    if (nan_i(p2) || nan_i(a2n)) st |= DIM_ST_NAN;
     return st;
 }
 
@@ -181,12 +224,12 @@ __device__ __forceinline__ unsigned equilibrium(const DevParams &p, double m1, d
     double qc = -E * G2C2;
     double disc = qb * qb - 4.0 * qa * qc;
     unsigned st = 0;
-    if (disc < 0.0) { st |= DIM_ST_NOROOT; disc = 0.0; }
+    if (lt0_i(disc)) { st |= DIM_ST_NOROOT; disc = 0.0; }
     double sq = sqrt(disc);
-    a = qb > 0.0 ? (-2.0 * qc) / (qb + sq) : (sq - qb) / (2.0 * qa);
+    a = gt0_i(qb) ? (-2.0 * qc) / (qb + sq) : (sq - qb) / (2.0 * qa);
     T = (E + B1 * a) / C;
-    if (!(a > 0.0 && a < 1.0 && T > 0.0)) st |= DIM_ST_NONPHYS;
-    if (isnan(a) || isnan(T)) st |= DIM_ST_NAN;
+    if (!(gt0_i(a) && lt_i(a, 1.0) && gt0_i(T))) st |= DIM_ST_NONPHYS;
+    if (nan_i(a) || nan_i(T)) st |= DIM_ST_NAN;
     return st;
 }
 

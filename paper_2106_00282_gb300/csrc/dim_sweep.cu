@@ -30,11 +30,15 @@ __device__ __forceinline__ void prims(const DevParams &p, const double *q, doubl
     w[6] = sg_p(p, 1, q[5], a2);
 }
 
+// minmod(a, b): the smaller-magnitude argument when both have the same sign and
+// neither is zero, else 0 -- decided on the integer pipe (same result as the
+// IEEE comparisons, NaN gives 0)
 __device__ __forceinline__ double minmod(double a, double b)
 {
-    if (a > 0.0 && b > 0.0) return a < b ? a : b;
-    if (a < 0.0 && b < 0.0) return a > b ? a : b;
-    return 0.0;
+    long long ia = bits_of(a), ib = bits_of(b);
+    long long ma = ia & kAbsMask, mb = ib & kAbsMask;
+    bool same = (ia ^ ib) >= 0 && ma != 0 && mb != 0 && ma <= kInfBits && mb <= kInfBits;
+    return same ? (ma < mb ? a : b) : 0.0;
 }
 
 struct Face {
@@ -75,14 +79,15 @@ __device__ __forceinline__ void hllc(const Face &L, const Face &R, double *F)
     double Ss = (R.p - L.p + L.rho * L.un * (SL - L.un) - R.rho * R.un * (SR - R.un)) /
                 (L.rho * (SL - L.un) - R.rho * (SR - R.un));
     double q[NQ], us, ps;
-    if (0.0 <= SL) {
+    const bool starL = ge0_i(Ss);
+    if (ge0_i(SL)) {
 #pragma unroll
         for (int k = 0; k < NQ; k++) q[k] = L.q[k];
         us = L.un;
         ps = L.p;
-    } else if (0.0 <= SR) {
-        const Face &K = (0.0 <= Ss) ? L : R;
-        double SK = (0.0 <= Ss) ? SL : SR;
+    } else if (ge0_i(SR)) {
+        const Face &K = starL ? L : R;
+        double SK = starL ? SL : SR;
         double chi = (SK - K.un) / (SK - Ss);
         q[0] = chi * K.q[0];
         q[1] = chi * K.q[1];
@@ -266,7 +271,7 @@ __global__ void k_from_primitive(const DevParams p, const double *__restrict__ p
         U[5 * n + c] = E2;
         U[6 * n + c] = E1 + E2 + 0.5 * rho * (u * u + v * v);
         U[7 * n + c] = a2;
-        if (!(a2 > 0.0 && a2 < 1.0 && T > 0.0 && pr + p.pinf[0] > 0.0 && pr + p.pinf[1] > 0.0))
+        if (!(gt0_i(a2) && lt_i(a2, 1.0) && gt0_i(T) && gt0_i(pr + p.pinf[0]) && gt0_i(pr + p.pinf[1])))
             st |= DIM_ST_NONPHYS;
     }
     flag(sc, st);
@@ -287,14 +292,14 @@ __global__ void k_wave_max(const DevParams p, const double *__restrict__ U, Scal
         double rho = q[0] + q[1];
         double cs = cell_c(p, q[0], q[1], q[4], q[5], q[7]);
         if (p.nx > 1) {
-            double s = (fabs(q[2] / rho) + cs) / p.dx;
-            if (s > m) m = s;
-            if (isnan(s)) st |= DIM_ST_NAN;
+            double s = (fabs(q[2] / rho) + cs) * p.idx;
+            if (lt_i(m, s)) m = s;
+            if (nan_i(s)) st |= DIM_ST_NAN;
         }
         if (p.ny > 1) {
-            double s = (fabs(q[3] / rho) + cs) / p.dy;
-            if (s > m) m = s;
-            if (isnan(s)) st |= DIM_ST_NAN;
+            double s = (fabs(q[3] / rho) + cs) * p.idy;
+            if (lt_i(m, s)) m = s;
+            if (nan_i(s)) st |= DIM_ST_NAN;
         }
     }
     block_max_to(&sc->smax, m);
