@@ -86,10 +86,17 @@ static double phase_E(const orc_params *P, int k, double p, double ak)
     return ak * (p + P->gamma[k] * P->pinf[k]) * inv_gm1(P, k);
 }
 
-/* squared phase sound speed c_k^2 = g_k (p_k + pinf_k) / rho_k  (Eq. AK) */
-static double phase_c2(const orc_params *P, int k, double p, double rho)
+/* A_k = rho_k c_k^2 = gamma_k (p_k + pinf_k)  (Eq. AK) */
+static double phase_A(const orc_params *P, int k, double p)
 {
-    return P->gamma[k] * (p + P->pinf[k]) / rho;
+    return P->gamma[k] * (p + P->pinf[k]);
+}
+
+/* mixture sound speed c^2 = Y1 c1^2 + Y2 c2^2 (Sec. 3.1); with Y_k = a_k rho_k / rho
+ * and rho_k c_k^2 = A_k (Eq. AK) this is c^2 = (a1 A1 + a2 A2) / rho */
+static double mixture_c(const orc_params *P, double a1, double p1, double a2, double p2, double rho)
+{
+    return sqrt((a1 * phase_A(P, 0, p1) + a2 * phase_A(P, 1, p2)) / rho);
 }
 
 /* conductivity law lambda_k(T) = k0_k (T / T_ref)^k_exp */
@@ -147,10 +154,7 @@ static double cell_sound_speed(const orc_params *P, const double *U, int n, int 
     double rho = m1 + m2;
     double p1 = phase_p(P, 0, U[4 * n + c], a1);
     double p2 = phase_p(P, 1, U[5 * n + c], a2);
-    double c1 = phase_c2(P, 0, p1, m1 / a1);
-    double c2 = phase_c2(P, 1, p2, m2 / a2);
-    /* c^2 = Y1 c1^2 + Y2 c2^2 with Y_k = m_k / rho */
-    return sqrt((m1 * c1 + m2 * c2) / rho);
+    return mixture_c(P, a1, p1, a2, p2, rho);
 }
 
 double orc_dt(const orc_params *P, int nx, int ny, double dx, double dy, const double *U)
@@ -210,11 +214,10 @@ static void face_from_w(const orc_params *P, const double *w, face_state *s)
     double m1 = w[1], m2 = w[2], un = w[3], ut = w[4], p1 = w[5], p2 = w[6];
     double rho = m1 + m2;
     double E1 = phase_E(P, 0, p1, a1), E2 = phase_E(P, 1, p2, a2);
-    double c1 = phase_c2(P, 0, p1, m1 / a1), c2 = phase_c2(P, 1, p2, m2 / a2);
     s->a2 = a2; s->m1 = m1; s->m2 = m2; s->un = un; s->ut = ut;
     s->rho = rho;
     s->p = a1 * p1 + a2 * p2;
-    s->c = sqrt((m1 * c1 + m2 * c2) / rho);
+    s->c = mixture_c(P, a1, p1, a2, p2, rho);
     s->q[0] = m1; s->q[1] = m2;
     s->q[2] = rho * un; s->q[3] = rho * ut;
     s->q[4] = E1; s->q[5] = E2;
