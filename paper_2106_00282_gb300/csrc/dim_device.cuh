@@ -124,19 +124,20 @@ __device__ __forceinline__ double sg_E(const DevParams &p, int k, double pr, dou
 {
     return ak * (pr + p.gpinf[k]) * p.inv_gm1[k];
 }
-// c_k^2 = gamma_k (p_k + pinf_k) / rho_k  (Eq. AK)
-__device__ __forceinline__ double sg_c2(const DevParams &p, int k, double pr, double rho)
+// A_k = rho_k c_k^2 = gamma_k (p_k + pinf_k)  (Eq. AK)
+__device__ __forceinline__ double sg_A(const DevParams &p, int k, double pr) { return p.g[k] * (pr + p.pinf[k]); }
+
+// mixture sound speed c^2 = Y1 c1^2 + Y2 c2^2 (Sec. 3.1) = (a1 A1 + a2 A2) / rho
+__device__ __forceinline__ double mix_c(const DevParams &p, double a1, double p1, double a2, double p2, double rho)
 {
-    return p.g[k] * (pr + p.pinf[k]) / rho;
+    return sqrt((a1 * sg_A(p, 0, p1) + a2 * sg_A(p, 1, p2)) / rho);
 }
 
-// mixture sound speed c^2 = Y1 c1^2 + Y2 c2^2 of a cell (Sec. 3.1)
 __device__ __forceinline__ double cell_c(const DevParams &p, double m1, double m2, double E1, double E2, double a2)
 {
     double a1 = 1.0 - a2;
     double p1 = sg_p(p, 0, E1, a1), p2 = sg_p(p, 1, E2, a2);
-    double c1 = sg_c2(p, 0, p1, m1 / a1), c2 = sg_c2(p, 1, p2, m2 / a2);
-    return sqrt((m1 * c1 + m2 * c2) / (m1 + m2));
+    return mix_c(p, a1, p1, a2, p2, m1 + m2);
 }
 
 // conductivity lambda_k(T) = k0_k (T / T_ref)^k_exp
@@ -152,13 +153,15 @@ __device__ __forceinline__ double cond(const DevParams &p, int k, double T)
     return p.k0[k] * pow(t, p.k_exp);
 }
 
-// end-of-step admissibility: alpha in (0,1), m_k > 0, p_k + pinf_k > 0, no NaN
+// end-of-step admissibility: alpha in (0,1), m_k > 0, p_k + pinf_k > 0, no NaN.
+// With alpha_k > 0, p_k + pinf_k = (gamma_k - 1)(E_k - alpha_k pinf_k)/alpha_k > 0
+// is tested as E_k > alpha_k pinf_k (no division).
 __device__ __forceinline__ unsigned check_state(const DevParams &p, const double *q)
 {
     unsigned st = 0;
     double a2 = q[7], a1 = 1.0 - a2;
-    double p1 = sg_p(p, 0, q[4], a1), p2 = sg_p(p, 1, q[5], a2);
-    if (!(gt0_i(a2) && lt_i(a2, 1.0) && gt0_i(q[0]) && gt0_i(q[1]) && gt0_i(p1 + p.pinf[0]) && gt0_i(p2 + p.pinf[1])))
+    if (!(gt0_i(a2) && lt_i(a2, 1.0) && gt0_i(q[0]) && gt0_i(q[1]) && lt_i(a1 * p.pinf[0], q[4]) &&
+          lt_i(a2 * p.pinf[1], q[5])))
         st |= DIM_ST_NONPHYS;
 #pragma unroll
     for (int k = 0; k < NQ; k++)

@@ -52,13 +52,12 @@ __device__ __forceinline__ void face_state(const DevParams &p, const double *w, 
     double m1 = w[1], m2 = w[2], un = w[3], ut = w[4], p1 = w[5], p2 = w[6];
     double rho = m1 + m2;
     double E1 = sg_E(p, 0, p1, a1), E2 = sg_E(p, 1, p2, a2);
-    double c1 = sg_c2(p, 0, p1, m1 / a1), c2 = sg_c2(p, 1, p2, m2 / a2);
     s.a2 = a2;
     s.un = un;
     s.ut = ut;
     s.rho = rho;
     s.p = a1 * p1 + a2 * p2;
-    s.c = sqrt((m1 * c1 + m2 * c2) / rho);
+    s.c = mix_c(p, a1, p1, a2, p2, rho);
     s.q[0] = m1;
     s.q[1] = m2;
     s.q[2] = rho * un;
