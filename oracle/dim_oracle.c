@@ -484,6 +484,14 @@ static unsigned cheb_capped(const orc_params *P, double tau, double lam_max, int
     return (P->p_policy != 1 && Pn < cheb_P_formula(tau, lam_max)) ? ORC_PCAP : 0u;
 }
 
+/* P of the viscous solve: the formula (capped at p_max); the fixed / clamped
+ * stage counts of a configuration are those of the heat-conduction solve */
+static int cheb_P_viscous(const orc_params *P, double tau, double lam_max)
+{
+    int pf = cheb_P_formula(tau, lam_max);
+    return pf > P->p_max ? P->p_max : pf;
+}
+
 /* b_1..b_{2P-1} = (a_P .. a_2, a_P .. a_1), a_m = lam (beta_1 - beta_m)/(1 + beta_1),
  * beta_m = cos((2m-1) pi / (2P)) the roots of T_P.  The roots are taken in their
  * natural (decreasing) order so that beta_1 is the largest and every a_m >= 0
@@ -604,9 +612,10 @@ static void lim_predict(const orc_op *o, int Pn, const double *b, double tau, co
     memcpy(cur, v0, sizeof(double) * n);
     for (int m = 1; m <= 2 * Pn - 2; m++) {
         double bm = b[m - 1];
+        double rden = 1.0 / (1.0 + tau * bm); /* the prefactor of Eq. (LIM), once per sweep */
         op_apply(o, cur, Lv);
         for (int c = 0; c < n; c++)
-            nxt[c] = (v0[c] + tau * bm * cur[c] + tau * V[c] * Lv[c]) / (1.0 + tau * bm);
+            nxt[c] = (v0[c] + tau * bm * cur[c] + tau * V[c] * Lv[c]) * rden;
         double *t = cur; cur = nxt; nxt = t;
     }
     memcpy(uhat, cur, sizeof(double) * n);
@@ -762,8 +771,8 @@ unsigned orc_viscous(const orc_params *P, int nx, int ny, double dx, double dy, 
         memset(ot.lx, 0, sizeof(double) * (nx + 1) * ny);
     }
     double lm = op_lam_max(&o, V);
-    int Pn = orc_cheb_P(P, tau, lm);
-    unsigned st = cheb_capped(P, tau, lm, Pn);
+    int Pn = cheb_P_viscous(P, tau, lm);
+    unsigned st = Pn < cheb_P_formula(tau, lm) ? ORC_PCAP : 0u;
     double *b = (double *)malloc(sizeof(double) * (2 * Pn - 1));
     orc_cheb_schedule(Pn, lm, b);
     lim_predict(&o, Pn, b, tau, V, un0, unh);

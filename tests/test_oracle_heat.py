@@ -143,7 +143,7 @@ def test_lim_matches_dense_polynomial(O, I):
         v = v0.reshape(-1).copy()
         u0 = v.copy()
         for m in range(2 * Pn - 1):
-            v = (u0 + tau * b[m] * v + tau * (A @ v)) / (1 + tau * b[m])
+            v = (u0 + tau * b[m] * v + tau * (A @ v)) * (1 / (1 + tau * b[m]))
         assert np.max(np.abs(v - v1.reshape(-1))) < 1e-12
 
 
