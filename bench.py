@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--workload", default="impact")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk variant")
     return ap.parse_args()
 
 
@@ -127,7 +128,7 @@ def flops_per_cell(kernel: str, wl) -> float:
     return flops.per_cell(kernel, wl.params)
 
 
-def run_ours(args, rank, world, dev):
+def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
     import torch
 
     from paper_2106_00282_gb300 import build as cuda_build, inputs as I
@@ -138,6 +139,7 @@ def run_ours(args, rank, world, dev):
     if world > 1:
         torch.distributed.barrier()
     wl = I.bench_workload(args.workload)
+    wl.params = wl.params.replace(precision=precision)
     ncell = wl.nx * wl.ny
     s = Solver(wl.params, wl.nx, wl.ny, wl.dx, wl.dy)
     U0 = s.from_primitive(torch.from_numpy(wl.prim).to(dev))
@@ -209,7 +211,7 @@ def run_ours(args, rank, world, dev):
 
     # end to end: host buffers through dim_step_host (copies inside the timed region)
     e2e = None
-    if not args.no_e2e:
+    if with_e2e and not args.no_e2e:
         Uh = U0.cpu().pin_memory()
         Ke = max(3, min(K, 30))
         s.step_host(Uh, 1)
@@ -260,6 +262,7 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
     r = run_ours(args, rank, world, dev)
+    r32 = None if args.no_fp32 else run_ours(args, rank, world, dev, precision=1, with_e2e=False)
     if rank == 0:
         wl = r["wl"]
         cpu = None
@@ -276,6 +279,15 @@ def main():
                 "config": dict(workload_desc(wl), parallelism=f"replicas{world}" if world > 1 else "single"),
                 "hbm_roofline_frac_alg": r["hbm_frac"], "roofline": r["roofline"], "cpu_baseline": cpu,
                 "e2e": r["e2e"], "clocks": r["clocks"], "gpu_launches": r["launches"]}
+        if r32 is not None:
+            line["fp32_bulk"] = {
+                "value": r32["value"], "unit": UNIT, "ms_per_step": r32["ms_per_step"],
+                "speedup_vs_fp64": r32["value"] / r["value"], "clocks": r32["clocks"],
+                "kernels_us": {k: round(v["avg_us"], 1) for k, v in r32["roofline"]["kernels"].items()},
+                "precision": "FP32 flux/stencil arithmetic; FP64 state accumulation, phase pressures, "
+                             "volume-fraction transport, relaxation root solves, Chebyshev parameters",
+                "accuracy": "relative L1 per conserved field vs the FP64 oracle <= 2e-5 after 100 steps "
+                            "(tests/test_gpu_fp32.py)"}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

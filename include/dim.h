@@ -59,6 +59,11 @@ extern "C" {
 #define DIM_P_FIXED 1            /* P = p_fixed */
 #define DIM_P_CLAMP 2            /* P = clamp(formula, p_min, p_max) */
 
+#define DIM_PRECISION_FP64 0      /* every operation in FP64 */
+#define DIM_PRECISION_FP32_BULK 1 /* flux and stencil arithmetic in FP32; state accumulation, phase
+                                     pressures, volume-fraction transport and the relaxation root solves
+                                     in FP64 */
+
 #define DIM_RELAX_PRESSURE 0    /* dim_relax: Sec. 3.3 three-step pressure relaxation */
 #define DIM_RELAX_TEMPERATURE 1 /* dim_relax: Sec. 3.4.1 temperature relaxation */
 
@@ -81,6 +86,7 @@ typedef struct dim_params {
     int trelax;
     int n_outer; /* outer iterations of Algorithm 1 (>= 1) */
     int p_policy, p_fixed, p_min, p_max;
+    int precision; /* DIM_PRECISION_FP64 or DIM_PRECISION_FP32_BULK */
 } dim_params;
 
 typedef struct dim_ctx dim_ctx; /* opaque: parameters, grid, stream, scratch */

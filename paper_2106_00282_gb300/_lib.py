@@ -18,6 +18,7 @@ DIM_ETOOLARGE = -7
 NOALLOC_MAX_CELLS = 65536
 ST_NONPHYS, ST_NAN, ST_NOROOT, ST_TRANSIENT, ST_PCAP, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
 RELAX_PRESSURE, RELAX_TEMPERATURE = 0, 1
+PRECISION_FP64, PRECISION_FP32_BULK = 0, 1
 PARABOLIC_HEAT, PARABOLIC_VISCOUS_X, PARABOLIC_VISCOUS_Y = 0, 1, 2
 
 # every entry point the header declares
@@ -33,6 +34,7 @@ class DimParams(C.Structure):
         ("mu", C.c_double * 2), ("cfl", C.c_double),
         ("limiter", C.c_int), ("bc", C.c_int * 2), ("trelax", C.c_int), ("n_outer", C.c_int),
         ("p_policy", C.c_int), ("p_fixed", C.c_int), ("p_min", C.c_int), ("p_max", C.c_int),
+        ("precision", C.c_int),
     ]
 
 
@@ -54,6 +56,7 @@ def make_params(p) -> DimParams:
     s.p_fixed = p.p_fixed
     s.p_min = p.p_min
     s.p_max = p.p_max
+    s.precision = getattr(p, "precision", 0)
     return s
 
 

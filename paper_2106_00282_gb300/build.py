@@ -14,7 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdim.so")
-SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu"]
+SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulk32.cu"]
+# the FP32-bulk kernels may contract multiply-adds (no bit-compatibility claim)
+FMA_SOURCES = {"dim_bulk32.cu"}
 HEADERS = ["dim_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -46,7 +48,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [NVCC] + _flags() + list(extra) + ["-c", s, "-o", o]
+            flags = _flags()
+            if src in FMA_SOURCES:
+                flags = [f for f in flags if f != "--fmad=false"] + ["--fmad=true"]
+            cmd = [NVCC] + flags + list(extra) + ["-c", s, "-o", o]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -26,6 +26,14 @@ cudaError_t launch_heat(const DevParams &p, double *U, const HeatScratch &s, Sca
                         int trelax_first, int check, cudaStream_t st);
 cudaError_t launch_visc(const DevParams &p, int axis, double *U, const ViscScratch &s, Scalars *sc, double dt_host,
                         int relax, int check, cudaStream_t st);
+cudaError_t bulk32_setup(int nsm);
+cudaError_t launch_sweep32(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
+                           int relax, int check, cudaStream_t s);
+cudaError_t launch_wave_max32(const DevParams &p, const double *U, Scalars *sc, cudaStream_t s);
+cudaError_t launch_heat32(const DevParams &p, double *U, double *S, Scalars *sc, double dt_host, int trelax_first,
+                          int check, cudaStream_t st);
+cudaError_t launch_visc32(const DevParams &p, int axis, double *U, double *S, Scalars *sc, double dt_host, int relax,
+                          int check, cudaStream_t st);
 }  // namespace dimk
 
 using dimk::DevParams;
@@ -117,6 +125,29 @@ static dimk::ViscScratch visc_scratch(dim_ctx *c)
     return dimk::ViscScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n};
 }
 
+static bool fp32(const dim_ctx *c) { return c->p.precision == DIM_PRECISION_FP32_BULK; }
+
+static cudaError_t run_sweep(dim_ctx *c, int axis, const double *Uin, double *Uout, double dt, int relax, int check)
+{
+    return fp32(c) ? dimk::launch_sweep32(c->p, axis, Uin, Uout, dt, c->sc, relax, check, c->stream)
+                   : dimk::launch_sweep(c->p, axis, Uin, Uout, dt, c->sc, relax, check, c->stream);
+}
+static cudaError_t run_wave(dim_ctx *c, const double *U)
+{
+    return fp32(c) ? dimk::launch_wave_max32(c->p, U, c->sc, c->stream)
+                   : dimk::launch_wave_max(c->p, U, c->sc, c->stream);
+}
+static cudaError_t run_heat(dim_ctx *c, double *U, double dt, int trelax_first, int check)
+{
+    return fp32(c) ? dimk::launch_heat32(c->p, U, c->S, c->sc, dt, trelax_first, check, c->stream)
+                   : dimk::launch_heat(c->p, U, heat_scratch(c), c->sc, dt, trelax_first, check, c->stream);
+}
+static cudaError_t run_visc(dim_ctx *c, int axis, double *U, double dt, int relax, int check)
+{
+    return fp32(c) ? dimk::launch_visc32(c->p, axis, U, c->S, c->sc, dt, relax, check, c->stream)
+                   : dimk::launch_visc(c->p, axis, U, visc_scratch(c), c->sc, dt, relax, check, c->stream);
+}
+
 #define TRY(x)                                     \
     do {                                           \
         cudaError_t e_ = (x);                      \
@@ -172,6 +203,7 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
     if (hp->p_max < 1 || hp->p_max > dimk::PMAX) return DIM_EINVAL;
     if (hp->p_policy == DIM_P_FIXED && (hp->p_fixed < 1 || hp->p_fixed > dimk::PMAX)) return DIM_EINVAL;
     if (hp->p_policy == DIM_P_CLAMP && (hp->p_min < 1 || hp->p_min > hp->p_max)) return DIM_EINVAL;
+    if (hp->precision != DIM_PRECISION_FP64 && hp->precision != DIM_PRECISION_FP32_BULK) return DIM_EINVAL;
     DevParams p;
     memset(&p, 0, sizeof(p));
     for (int k = 0; k < 2; k++) {
@@ -209,6 +241,7 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
     p.p_fixed = hp->p_fixed;
     p.p_min = hp->p_min;
     p.p_max = hp->p_max;
+    p.precision = hp->precision;
     p.beta = nullptr;
     *out = p;
     return DIM_OK;
@@ -236,7 +269,8 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
     if (dev < 64 && !g_setup_done[dev]) {
         int nsm = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            dimk::sweep_setup() != cudaSuccess || dimk::parabolic_setup(nsm) != cudaSuccess) {
+            dimk::sweep_setup() != cudaSuccess || dimk::parabolic_setup(nsm) != cudaSuccess ||
+            dimk::bulk32_setup(nsm) != cudaSuccess) {
             free(c);
             return DIM_ECUDA;
         }
@@ -293,7 +327,7 @@ int dim_cfl_dt(dim_ctx *c, const double *U, double *dt)
 {
     if (!c || !U || !dt) return DIM_EINVAL;
     TRY(reset_accumulators(c));
-    TIMED(c, K_WAVE, dimk::launch_wave_max(c->p, U, c->sc, c->stream));
+    TIMED(c, K_WAVE, run_wave(c, U));
     unsigned long long bits = 0;
     TRY(cudaMemcpyAsync(&bits, &c->sc->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
     TRY(cudaStreamSynchronize(c->stream));
@@ -326,22 +360,22 @@ static int step_once(dim_ctx *c, double *U)
     else last = sy ? LAST_SY : LAST_SX;
 
     TRY(reset_accumulators(c));
-    TIMED(c, K_WAVE, dimk::launch_wave_max(p, U, c->sc, c->stream));
+    TIMED(c, K_WAVE, run_wave(c, U));
     double *cur = U, *oth = c->U2;
     if (sx) {
-        TIMED(c, K_SWEEP_X, dimk::launch_sweep(p, 0, cur, oth, 0.0, c->sc, 1, last == LAST_SX, c->stream));
+        TIMED(c, K_SWEEP_X, run_sweep(c, 0, cur, oth, 0.0, 1, last == LAST_SX));
         double *t = cur; cur = oth; oth = t;
     }
     if (sy) {
-        TIMED(c, K_SWEEP_Y, dimk::launch_sweep(p, 1, cur, oth, 0.0, c->sc, 1, last == LAST_SY, c->stream));
+        TIMED(c, K_SWEEP_Y, run_sweep(c, 1, cur, oth, 0.0, 1, last == LAST_SY));
         double *t = cur; cur = oth; oth = t;
     }
     if (vis) {
-        if (sx) TIMED(c, K_VISC_X, dimk::launch_visc(p, 0, cur, visc_scratch(c), c->sc, 0.0, !sy, last == LAST_VX, c->stream));
-        if (sy) TIMED(c, K_VISC_Y, dimk::launch_visc(p, 1, cur, visc_scratch(c), c->sc, 0.0, 1, last == LAST_VY, c->stream));
+        if (sx) TIMED(c, K_VISC_X, run_visc(c, 0, cur, 0.0, !sy, last == LAST_VX));
+        if (sy) TIMED(c, K_VISC_Y, run_visc(c, 1, cur, 0.0, 1, last == LAST_VY));
     }
     if (heat) {
-        TIMED(c, K_HEAT, dimk::launch_heat(p, cur, heat_scratch(c), c->sc, 0.0, 1, 1, c->stream));
+        TIMED(c, K_HEAT, run_heat(c, cur, 0.0, 1, 1));
     } else if (trx) {
         TIMED(c, K_RELAX, dimk::launch_relax(p, cur, c->sc, DIM_RELAX_TEMPERATURE, 1, c->stream));
     }
@@ -396,7 +430,7 @@ int dim_hllc_sweep(dim_ctx *c, double *U, int axis, double dt, int relax)
 {
     if (!c || !U || (axis != 0 && axis != 1) || !(dt > 0.0)) return DIM_EINVAL;
     TRY(reset_accumulators(c));
-    TIMED(c, axis == 0 ? K_SWEEP_X : K_SWEEP_Y, dimk::launch_sweep(c->p, axis, U, c->U2, dt, c->sc, relax, 0, c->stream));
+    TIMED(c, axis == 0 ? K_SWEEP_X : K_SWEEP_Y, run_sweep(c, axis, U, c->U2, dt, relax, 0));
     TIMED(c, K_COPY, cudaMemcpyAsync(U, c->U2, sizeof(double) * 8 * (size_t)c->p.n, cudaMemcpyDeviceToDevice, c->stream));
     return DIM_OK;
 }
@@ -414,7 +448,7 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
     TRY(reset_accumulators(c));
     int slot = 0;
     if (kind == DIM_PARABOLIC_HEAT) {
-        TIMED(c, K_HEAT, dimk::launch_heat(c->p, U, heat_scratch(c), c->sc, dt, 0, 0, c->stream));
+        TIMED(c, K_HEAT, run_heat(c, U, dt, 0, 0));
         slot = 0;
     } else if (kind == DIM_PARABOLIC_VISCOUS_X || kind == DIM_PARABOLIC_VISCOUS_Y) {
         int axis = kind == DIM_PARABOLIC_VISCOUS_X ? 0 : 1;
@@ -422,8 +456,7 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
             if (P_used) *P_used = 0;
             return DIM_OK;
         }
-        TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y,
-              dimk::launch_visc(c->p, axis, U, visc_scratch(c), c->sc, dt, 0, 0, c->stream));
+        TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y, run_visc(c, axis, U, dt, 0, 0));
         slot = 1 + axis;
     } else {
         return DIM_EINVAL;

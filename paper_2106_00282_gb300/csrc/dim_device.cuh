@@ -32,6 +32,7 @@ struct DevParams {
     double dx, dy, idx, idy, idx2, idy2;  // spacing, 1/h and 1/h^2
     int nx, ny, n;
     int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
+    int precision;  // DIM_PRECISION_FP64 or DIM_PRECISION_FP32_BULK
     // roots of T_P: beta[(P-1)*PMAX + m-1] = cos((2m-1) pi / (2P)), m = 1..P,
     // tabulated on the host (libm) once per context
     const double *beta;
@@ -124,6 +125,17 @@ __device__ __forceinline__ double sg_E(const DevParams &p, int k, double pr, dou
 {
     return ak * (pr + p.gpinf[k]) * p.inv_gm1[k];
 }
+// minmod(a, b): the smaller-magnitude argument when both have the same sign and
+// neither is zero, else 0 -- decided on the integer pipe (same result as the
+// IEEE comparisons, NaN gives 0)
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    long long ia = bits_of(a), ib = bits_of(b);
+    long long ma = ia & kAbsMask, mb = ib & kAbsMask;
+    bool same = (ia ^ ib) >= 0 && ma != 0 && mb != 0 && ma <= kInfBits && mb <= kInfBits;
+    return same ? (ma < mb ? a : b) : 0.0;
+}
+
 // A_k = rho_k c_k^2 = gamma_k (p_k + pinf_k)  (Eq. AK)
 __device__ __forceinline__ double sg_A(const DevParams &p, int k, double pr) { return p.g[k] * (pr + p.pinf[k]); }
 
@@ -273,6 +285,16 @@ __device__ __forceinline__ int cheb_P(const DevParams &p, double tau, double lam
     return P;
 }
 
+// P of the viscous solve: the formula capped at p_max (fixed / clamped stage
+// counts belong to the heat-conduction solve)
+__device__ __forceinline__ int cheb_P_visc(const DevParams &p, double tau, double lam, unsigned &capped)
+{
+    int pf = (int)ceil(3.14159265358979323846 / 4.0 * sqrt(tau * lam + 1.0));
+    int P = pf > p.p_max ? p.p_max : pf;
+    capped = P < pf ? DIM_ST_PCAP : 0u;
+    return P;
+}
+
 // b_1..b_{2P-1} = (a_P..a_2, a_P..a_1), a_m = lam (beta_1 - beta_m)/(1 + beta_1),
 // beta_m = cos((2m-1) pi/(2P)) in decreasing order.  One entry per thread of a block.
 __device__ __forceinline__ void cheb_schedule_block(const DevParams &p, int P, double lam, double *sb)
@@ -346,6 +368,41 @@ __device__ __forceinline__ void block_max_to(unsigned long long *acc, double v)
         for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
         if (l == 0) atomic_max_pos(acc, x);
     }
+}
+
+// ---------------------------------------------------------------------------
+// stencil neighbourhood of a cell and reading a device accumulator
+// ---------------------------------------------------------------------------
+// cell (i, j) of index c and its neighbours with the boundary rule; returns -1
+// for a transmissive wall (no flux through that face)
+struct Nb {
+    int xm, xp, ym, yp;
+};
+
+__device__ __forceinline__ Nb neighbours(const DevParams &p, int c)
+{
+    Nb r;
+    int j = c / p.nx, i = c - j * p.nx;
+    r.xm = r.xp = r.ym = r.yp = -1;
+    if (p.nx > 1) {
+        if (i > 0) r.xm = c - 1;
+        else if (p.bc[0] == DIM_BC_PERIODIC) r.xm = c + p.nx - 1;
+        if (i < p.nx - 1) r.xp = c + 1;
+        else if (p.bc[0] == DIM_BC_PERIODIC) r.xp = c - (p.nx - 1);
+    }
+    if (p.ny > 1) {
+        if (j > 0) r.ym = c - p.nx;
+        else if (p.bc[1] == DIM_BC_PERIODIC) r.ym = c + (p.ny - 1) * p.nx;
+        if (j < p.ny - 1) r.yp = c + p.nx;
+        else if (p.bc[1] == DIM_BC_PERIODIC) r.yp = c - (p.ny - 1) * p.nx;
+    }
+    return r;
+}
+
+__device__ __forceinline__ double read_acc(const unsigned long long *a)
+{
+    unsigned long long v = *(volatile const unsigned long long *)a;
+    return dmax_bits(v);
 }
 
 }  // namespace dimk

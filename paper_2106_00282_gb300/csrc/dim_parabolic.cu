@@ -19,32 +19,6 @@
 namespace dimk {
 
 
-// cell (i, j) of index c and its neighbours with the boundary rule; returns -1
-// for a transmissive wall (no flux through that face)
-struct Nb {
-    int xm, xp, ym, yp;
-};
-
-__device__ __forceinline__ Nb neighbours(const DevParams &p, int c)
-{
-    Nb r;
-    int j = c / p.nx, i = c - j * p.nx;
-    r.xm = r.xp = r.ym = r.yp = -1;
-    if (p.nx > 1) {
-        if (i > 0) r.xm = c - 1;
-        else if (p.bc[0] == DIM_BC_PERIODIC) r.xm = c + p.nx - 1;
-        if (i < p.nx - 1) r.xp = c + 1;
-        else if (p.bc[0] == DIM_BC_PERIODIC) r.xp = c - (p.nx - 1);
-    }
-    if (p.ny > 1) {
-        if (j > 0) r.ym = c - p.nx;
-        else if (p.bc[1] == DIM_BC_PERIODIC) r.ym = c + (p.ny - 1) * p.nx;
-        if (j < p.ny - 1) r.yp = c + p.nx;
-        else if (p.bc[1] == DIM_BC_PERIODIC) r.yp = c - (p.ny - 1) * p.nx;
-    }
-    return r;
-}
-
 // (L_h v)_c = Fx_{+} - Fx_{-} + Fy_{+} - Fy_{-}, F = Lam_f (v_R - v_L) / h^2,
 // Lam_f = mean of the two cells (Eq. qk_dis in flux-difference form)
 __device__ __forceinline__ double lap(const DevParams &p, const Nb &nb, int c, const double *__restrict__ v,
@@ -82,12 +56,6 @@ __device__ __forceinline__ double gersh(const DevParams &p, const Nb &nb, int c,
         s += (fl + fr) * p.idy2;
     }
     return 2.0 * V[c] * s;
-}
-
-__device__ __forceinline__ double read_acc(const unsigned long long *a)
-{
-    unsigned long long v = *(volatile const unsigned long long *)a;
-    return dmax_bits(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -147,10 +115,10 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *__restr
         for (int m = 1; m <= 2 * P - 2; m++) {
             double *vout = (m & 1) ? s.va : s.vb;
             const double bm = s_b[m - 1];
-            const double den = 1.0 + tau * bm;
+            const double rden = 1.0 / (1.0 + tau * bm);
             for (int c = t0; c < n; c += nt) {
                 double Lv = lap(p, neighbours(p, c), c, vin, s.L);
-                vout[c] = (s.T0[c] + tau * bm * vin[c] + tau * s.V[c] * Lv) / den;
+                vout[c] = (s.T0[c] + tau * bm * vin[c] + tau * s.V[c] * Lv) * rden;
             }
             if (!grid_barrier(sc)) return;
             vin = vout;
@@ -257,7 +225,7 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *__restr
     if (!grid_barrier(sc)) return;
     double lam = read_acc(&sc->lam[SLOT]);
     unsigned capped;
-    const int P = cheb_P(p, tau, lam, capped);
+    const int P = cheb_P_visc(p, tau, lam, capped);
     cheb_schedule_block(p, P, lam, s_b);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         atomicMax(&sc->P[1 + AXIS], P);
@@ -270,7 +238,7 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *__restr
         double *uo = (m & 1) ? s.ua : s.ub;
         double *wo = (m & 1) ? s.wa : s.wb;
         const double bm = s_b[m - 1];
-        const double den = 1.0 + tau * bm;
+        const double rden = 1.0 / (1.0 + tau * bm);
         for (int c = t0; c < n; c += nt) {
             int cm, cp;
             visc_nb<AXIS>(p, c, cm, cp);
@@ -282,8 +250,8 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *__restr
             double uc = uin[c], wc = win[c];
             double Lu = (cp >= 0 ? lnp * (uin[cp] - uc) * ih2 : 0.0) - (cm >= 0 ? lnm * (uc - uin[cm]) * ih2 : 0.0);
             double Lw = (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.0) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.0);
-            uo[c] = (s.u0[c] + tau * bm * uc + tau * s.V[c] * Lu) / den;
-            wo[c] = (s.w0[c] + tau * bm * wc + tau * s.V[c] * Lw) / den;
+            uo[c] = (s.u0[c] + tau * bm * uc + tau * s.V[c] * Lu) * rden;
+            wo[c] = (s.w0[c] + tau * bm * wc + tau * s.V[c] * Lw) * rden;
         }
         if (!grid_barrier(sc)) return;
         uin = uo;

@@ -30,17 +30,6 @@ __device__ __forceinline__ void prims(const DevParams &p, const double *q, doubl
     w[6] = sg_p(p, 1, q[5], a2);
 }
 
-// minmod(a, b): the smaller-magnitude argument when both have the same sign and
-// neither is zero, else 0 -- decided on the integer pipe (same result as the
-// IEEE comparisons, NaN gives 0)
-__device__ __forceinline__ double minmod(double a, double b)
-{
-    long long ia = bits_of(a), ib = bits_of(b);
-    long long ma = ia & kAbsMask, mb = ib & kAbsMask;
-    bool same = (ia ^ ib) >= 0 && ma != 0 && mb != 0 && ma <= kInfBits && mb <= kInfBits;
-    return same ? (ma < mb ? a : b) : 0.0;
-}
-
 struct Face {
     double a2, un, ut, rho, p, c;
     double q[NQ];

@@ -33,6 +33,7 @@ LIMITER_NONE, LIMITER_MINMOD = 0, 1
 BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
 TRELAX_OFF, TRELAX_EQUILIBRIUM = 0, 1
 P_FORMULA, P_FIXED, P_CLAMP = 0, 1, 2
+PRECISION_FP64, PRECISION_FP32_BULK = 0, 1
 
 ALPHA_FLOOR = 1e-6  # minor-phase volume fraction of a "pure" cell
 
@@ -57,6 +58,7 @@ class Params:
     p_fixed: int = 1
     p_min: int = 1
     p_max: int = 24
+    precision: int = PRECISION_FP64  # read by the CUDA library only; the oracle is FP64
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -1,0 +1,102 @@
+"""FP32-bulk form of the CUDA path (flux and stencil arithmetic in FP32; state
+accumulation, phase pressures, volume-fraction transport, relaxation root
+solves and Chebyshev parameters in FP64) against the FP64 oracle.
+
+Tolerance: relative L1 per conserved field <= 2e-5 after 100 steps.  The
+momentum of a flow at rest up to thermal expansion (the conduction disc) is
+roundoff noise -- a one-ulp change of the FP64 input already moves it by 1e-4
+relative -- so a momentum plane is measured against the acoustic momentum
+scale sum(rho) * (the largest wave speed) whenever its own L1 norm is below
+1e-3 of that scale."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2106_00282_gb300 import build
+
+    build.build()
+    return torch
+
+
+def rel_l1_32(a, b, O, wl, params):
+    num = np.abs(a - b).reshape(8, -1).sum(axis=1)
+    den = np.abs(b).reshape(8, -1).sum(axis=1)
+    rho = (b[0] + b[1]).sum()
+    h = min(wl.dx if wl.nx > 1 else np.inf, wl.dy if wl.ny > 1 else np.inf)
+    smax = params.cfl * h / O.dt(params, b, wl.dx, wl.dy)
+    acoustic = rho * smax
+    for q in (2, 3):
+        den[q] = max(den[q], 1e-3 * acoustic)
+    return num / np.maximum(den, 1e-300)
+
+
+def _run(torch, O, wl, nsteps):
+    from paper_2106_00282_gb300.api import Solver
+
+    p32 = wl.params.replace(precision=1)
+    s = Solver(p32, wl.nx, wl.ny, wl.dx, wl.dy)
+    U = s.from_primitive(torch.from_numpy(np.ascontiguousarray(wl.prim)).cuda())
+    s.step(U, nsteps, sync=False)
+    st = s.status()
+    Uo, sto, dto, ph = O.step(wl.params, O.from_primitive(wl.params, wl.prim), wl.dx, wl.dy, nsteps)
+    return U.cpu().numpy(), Uo, st, sto
+
+
+CASES = {
+    "shock_tube_1000": lambda I: I.shock_tube(n=1000),
+    "impact_160x80": lambda I: I.impact(160, 80),
+    "conduction_96": lambda I: I.conduction_disc(n=96),
+    "mixture_shock": lambda I: I.mixture_shock(n=400),
+    "pvt_periodic": lambda I: I.pvt_translation(n=150, k=(0.6, 0.026)),
+    "viscous_shock": lambda I: I.shock_tube(n=400, k=(1e6, 1e6), mu=(500.0, 1.0), p_policy=0),
+    "ragged_131x37": lambda I: I.impact(131, 37),
+    "shock_tube_column": lambda I: I.shock_tube(n=300, axis=1),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp32_bulk_100_steps(torch_cuda, O, I, case):
+    from paper_2106_00282_gb300 import _lib
+
+    wl = CASES[case](I)
+    G, Uo, st, sto = _run(torch_cuda, O, wl, 100)
+    e = rel_l1_32(G, Uo, O, wl, wl.params)
+    print(f"[fp32] {case}: rel L1 per field {np.array2string(e, precision=2)}")
+    assert np.all(e <= TOL32), e
+    assert not np.isnan(G).any()
+    assert st & (_lib.ST_NONPHYS | _lib.ST_NAN | _lib.ST_TIMEOUT) == 0
+
+
+def test_fp32_bulk_pvt(torch_cuda, O, I):
+    """Sec. 4.1 translation in FP32 bulk: u and T stay uniform to 1e-5 (the
+    consistent reconstruction of alpha and alpha rho; the cold energy of the
+    stiff phase carried by the FP64 volume-fraction flux).  The pressure of the
+    stiff phase is resolved only to the FP32 rounding of the total-energy flux:
+    at 1000 m/s water carries rho u^2/2 = 5e8 J/m^3 against a thermal energy of
+    3e4 J/m^3, so 6e-8 of the former moves p by ~1e-3 of itself."""
+    wl = I.pvt_translation(n=200, k=(0.6, 0.026))
+    G, Uo, st, sto = _run(torch_cuda, O, wl, 60)
+    d = O.diagnostics(wl.params, G)
+    assert np.max(np.abs(d[4] - 1000.0)) / 1000.0 < 1e-5
+    assert np.max(np.abs(d[1] - 1e5)) / 1e5 < 1e-2
+    assert np.max(np.abs(d[3] - 300.0)) / 300.0 < 1e-5
+
+
+@pytest.mark.parametrize("which", ["impact", "conduction"])
+def test_fp32_bulk_full_size(torch_cuda, O, I, which):
+    """The benchmark sizes (1024 x 512 impact, 2048^2 conduction disc)."""
+    wl = I.impact() if which == "impact" else I.conduction_disc()
+    nst = 2 if which == "impact" else 1
+    G, Uo, st, sto = _run(torch_cuda, O, wl, nst)
+    e = rel_l1_32(G, Uo, O, wl, wl.params)
+    print(f"[fp32] full {which}: rel L1 per field {np.array2string(e, precision=2)}")
+    assert np.all(e <= TOL32), e
