@@ -180,6 +180,37 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
 int dim_hllc_sweep_noalloc(const dim_params *p, int nx, int ny, double dx, double dy, double *U, int axis, double dt,
                            int relax, void *cuda_stream);
 
+/* ---- Batches: many independent grids advanced together (FP32 bulk) ----
+ * A batch of ninst independent problems with the same phase parameters and
+ * flags p (p->precision must be DIM_PRECISION_FP32_BULK) on grids nx[i] x ny[i]
+ * (both >= 2) of spacing dx[i], dy[i].  Each instance has its own CFL time
+ * step, lambda_max and Chebyshev parameter count (Sec. 3 per instance).  The
+ * states are packed: instance i occupies 8 planes of nx[i]*ny[i] doubles at
+ * U + 8 * offsets[i] (offsets from dim_batch_layout), the layout of dim_step
+ * within that window.  One split step of every instance is one persistent
+ * cooperative kernel launch; dim_batch_step captures it once into a CUDA graph
+ * (per state pointer and launch configuration) and replays it.  Calls are
+ * ordered on cuda_stream (the graph runs on a library stream joined to it with
+ * events).  The paper's method per instance; batching has no counterpart in
+ * the paper. */
+typedef struct dim_batch dim_batch;
+int dim_batch_init(dim_batch **out, const dim_params *p, int ninst, const int *nx, const int *ny, const double *dx,
+                   const double *dy, void *cuda_stream);
+void dim_batch_destroy(dim_batch *b);
+/* offsets[0..ninst]: cell offset of each instance; offsets[ninst] = total cells */
+int dim_batch_layout(const dim_batch *b, long long *offsets);
+/* prim: 5 planes per instance (alpha_2, p, T, u, v) at prim + 5 * offsets[i] */
+int dim_batch_from_primitive(dim_batch *b, const double *prim, double *U);
+/* nsteps split steps of every instance, in place, asynchronous */
+int dim_batch_step(dim_batch *b, double *U, int nsteps);
+/* time every compiled tile-shape variant and block count on a copy of U and
+ * keep the fastest; config (may be NULL) receives {variant, blocks, x-sweep
+ * tile cells, x-sweep tile lines, y-sweep tile cells, y-sweep tile lines};
+ * allocates a temporary copy of the state; synchronizes */
+int dim_batch_autotune(dim_batch *b, const double *U, int *config);
+/* per-instance status words (flags may be NULL) and their OR; synchronizes */
+int dim_batch_status(dim_batch *b, unsigned *flags, unsigned *any);
+
 /* Read (and clear if reset != 0) the device status word (DIM_ST_* bits);
  * synchronizes. */
 int dim_status(dim_ctx *c, unsigned *flags, int reset);

@@ -24,7 +24,9 @@ PARABOLIC_HEAT, PARABOLIC_VISCOUS_X, PARABOLIC_VISCOUS_Y = 0, 1, 2
 # every entry point the header declares
 SYMBOLS = ["dim_init", "dim_destroy", "dim_from_primitive", "dim_cfl_dt", "dim_step", "dim_step_host",
            "dim_hllc_sweep", "dim_relax", "dim_cheb_parabolic", "dim_grad", "dim_status", "dim_profile",
-           "dim_kernel_time", "dim_strerror", "dim_hllc_sweep_noalloc"]
+           "dim_kernel_time", "dim_strerror", "dim_hllc_sweep_noalloc", "dim_batch_init", "dim_batch_destroy",
+           "dim_batch_layout", "dim_batch_from_primitive", "dim_batch_step", "dim_batch_autotune",
+           "dim_batch_status"]
 
 
 class DimParams(C.Structure):
@@ -92,8 +94,9 @@ def load(path: str = LIB_PATH):
     L.dim_strerror.argtypes = [i]
     L.dim_strerror.restype = C.c_char_p
     for name in SYMBOLS:
-        if name not in ("dim_destroy", "dim_strerror"):
+        if name not in ("dim_destroy", "dim_strerror") and not name.startswith("dim_batch"):
             getattr(L, name).restype = i
+    declare_batch(L)
     _lib = L
     return L
 
@@ -109,3 +112,19 @@ def check(code: int, where: str) -> int:
     if code != DIM_OK:
         raise DimError(code, where)
     return code
+
+
+def declare_batch(L):
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.dim_batch_init.argtypes = [C.POINTER(vp), C.POINTER(DimParams), i, C.POINTER(i), C.POINTER(i),
+                                 C.POINTER(d), C.POINTER(d), vp]
+    L.dim_batch_destroy.argtypes = [vp]
+    L.dim_batch_destroy.restype = None
+    L.dim_batch_layout.argtypes = [vp, C.POINTER(C.c_longlong)]
+    L.dim_batch_from_primitive.argtypes = [vp, vp, vp]
+    L.dim_batch_step.argtypes = [vp, vp, i]
+    L.dim_batch_autotune.argtypes = [vp, vp, C.POINTER(i)]
+    L.dim_batch_status.argtypes = [vp, C.POINTER(C.c_uint), C.POINTER(C.c_uint)]
+    for n in ("dim_batch_init", "dim_batch_layout", "dim_batch_from_primitive", "dim_batch_step",
+              "dim_batch_autotune", "dim_batch_status"):
+        getattr(L, n).restype = i

@@ -110,3 +110,74 @@ class Solver:
         ms = C.c_double(0.0)
         check(self.L.dim_kernel_time(self._ctx, name.encode(), C.byref(n), C.byref(ms)), "dim_kernel_time")
         return n.value, ms.value
+
+
+class Batch:
+    """Many independent grids (same parameters, FP32 bulk) advanced together:
+    one persistent launch per step, replayed from a CUDA graph (a dim_batch)."""
+
+    def __init__(self, params, grids, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdim needs a CUDA device")
+        self.L = _lib.load()
+        self.params = params
+        self.grids = list(grids)
+        n = len(self.grids)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._p = _lib.make_params(params)
+        nx = (C.c_int * n)(*[g[0] for g in self.grids])
+        ny = (C.c_int * n)(*[g[1] for g in self.grids])
+        dx = (C.c_double * n)(*[g[2] for g in self.grids])
+        dy = (C.c_double * n)(*[g[3] for g in self.grids])
+        self._b = C.c_void_p()
+        check(self.L.dim_batch_init(C.byref(self._b), C.byref(self._p), n, nx, ny, dx, dy,
+                                    C.c_void_p(self.stream.cuda_stream)), "dim_batch_init")
+        off = (C.c_longlong * (n + 1))()
+        check(self.L.dim_batch_layout(self._b, off), "dim_batch_layout")
+        self.offsets = list(off)
+        self.ncell = self.offsets[-1]
+
+    def close(self):
+        if self._b:
+            self.L.dim_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack_primitive(self, prims) -> torch.Tensor:
+        """Primitive arrays (5, ny, nx) per instance -> one packed device buffer."""
+        buf = torch.empty(5 * self.ncell, dtype=torch.float64)
+        for i, pr in enumerate(prims):
+            o, n = self.offsets[i], self.offsets[i + 1] - self.offsets[i]
+            buf[5 * o:5 * o + 5 * n] = torch.from_numpy(pr.reshape(-1))
+        return buf.cuda()
+
+    def from_primitive(self, prim_packed: torch.Tensor) -> torch.Tensor:
+        U = torch.empty(8 * self.ncell, dtype=torch.float64, device=prim_packed.device)
+        check(self.L.dim_batch_from_primitive(self._b, _dev_ptr(prim_packed), _dev_ptr(U)), "dim_batch_from_primitive")
+        return U
+
+    def state(self, U: torch.Tensor, i: int) -> torch.Tensor:
+        """View of instance i as (8, ny, nx)."""
+        nx, ny = self.grids[i][0], self.grids[i][1]
+        o = self.offsets[i]
+        return U[8 * o:8 * o + 8 * nx * ny].view(8, ny, nx)
+
+    def step(self, U: torch.Tensor, nsteps: int = 1):
+        check(self.L.dim_batch_step(self._b, _dev_ptr(U), nsteps), "dim_batch_step")
+
+    def autotune(self, U: torch.Tensor):
+        cfg = (C.c_int * 6)()
+        check(self.L.dim_batch_autotune(self._b, _dev_ptr(U), cfg), "dim_batch_autotune")
+        return list(cfg)
+
+    def status(self):
+        n = len(self.grids)
+        flags = (C.c_uint * n)()
+        anyf = C.c_uint(0)
+        check(self.L.dim_batch_status(self._b, flags, C.byref(anyf)), "dim_batch_status")
+        return list(flags), anyf.value

@@ -14,10 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdim.so")
-SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulk32.cu"]
+SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulk32.cu", "dim_batch.cu"]
 # the FP32-bulk kernels may contract multiply-adds (no bit-compatibility claim)
-FMA_SOURCES = {"dim_bulk32.cu"}
-HEADERS = ["dim_device.cuh"]
+FMA_SOURCES = {"dim_bulk32.cu", "dim_batch.cu"}
+HEADERS = ["dim_device.cuh", "dim_bulk32.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -21,8 +21,7 @@ namespace dimk {
 
 // (L_h v)_c = Fx_{+} - Fx_{-} + Fy_{+} - Fy_{-}, F = Lam_f (v_R - v_L) / h^2,
 // Lam_f = mean of the two cells (Eq. qk_dis in flux-difference form)
-__device__ __forceinline__ double lap(const DevParams &p, const Nb &nb, int c, const double *__restrict__ v,
-                                      const double *__restrict__ L)
+__device__ __forceinline__ double lap(const DevParams &p, const Nb &nb, int c, const double *v, const double *L)
 {
     double r = 0.0;
     double vc = v[c], Lc = L[c];
@@ -40,8 +39,7 @@ __device__ __forceinline__ double lap(const DevParams &p, const Nb &nb, int c, c
 }
 
 // Gershgorin row bound 2 V_c sum_f Lam_f / h_f^2 of A = -V L_h
-__device__ __forceinline__ double gersh(const DevParams &p, const Nb &nb, int c, const double *__restrict__ V,
-                                        const double *__restrict__ L)
+__device__ __forceinline__ double gersh(const DevParams &p, const Nb &nb, int c, const double *V, const double *L)
 {
     double Lc = L[c];
     double s = 0.0;
@@ -61,7 +59,7 @@ __device__ __forceinline__ double gersh(const DevParams &p, const Nb &nb, int c,
 // ---------------------------------------------------------------------------
 // heat conduction (Algorithm 1 with the LIM)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_heat(const DevParams p, double *__restrict__ U, HeatScratch s,
+__global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, HeatScratch s,
                                               Scalars *sc, double dt_host, int trelax_first, int check)
 {
     __shared__ double s_b[2 * PMAX];
@@ -184,7 +182,7 @@ __device__ __forceinline__ void visc_nb(const DevParams &p, int c, int &cm, int 
 }
 
 template <int AXIS>
-__global__ void __launch_bounds__(256) k_visc(const DevParams p, double *__restrict__ U, ViscScratch s, Scalars *sc,
+__global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, ViscScratch s, Scalars *sc,
                                               double dt_host, int relax, int check)
 {
     __shared__ double s_b[2 * PMAX];

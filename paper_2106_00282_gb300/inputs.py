@@ -240,3 +240,55 @@ def bench_workload(name: str = "impact") -> Workload:
     if name == "shock_tube":
         return shock_tube()
     raise ValueError(name)
+
+
+# ---------------------------------------------------------------------------
+# batches of independent problems
+# ---------------------------------------------------------------------------
+def batch_instance(nx: int, ny: int, rng: np.random.Generator, kind: str | None = None) -> np.ndarray:
+    """Primitive fields (5, ny, nx) of one water/air problem on a unit-height
+    domain of square cells (width nx/ny): a 'riemann' setup (water at
+    ratio * 1e5 Pa left of x = W/2, air at 1e5 Pa right) or a 'bubble' setup
+    (an air bubble of radius R in water at 1e5 Pa, hit by water at ratio * 1e5
+    Pa from x < W/4); ratio log-uniform in [10, 1e4], R uniform in [0.05, 0.3],
+    everything at 300 K and at rest."""
+    kind = kind or ("riemann" if rng.random() < 0.5 else "bubble")
+    ratio = math.exp(rng.uniform(math.log(10.0), math.log(1e4)))
+    R = rng.uniform(0.05, 0.3)
+    h = 1.0 / ny
+    W = nx * h
+    x = (np.arange(nx) + 0.5)[None, :] * h
+    y = (np.arange(ny) + 0.5)[:, None] * h
+    pr = _prim(ny, nx)
+    pr[2] = 300.0
+    if kind == "riemann":
+        left = (x < 0.5 * W) & (y >= 0.0 * y)
+        pr[0] = np.where(left, ALPHA_FLOOR, 1.0 - ALPHA_FLOOR)
+        pr[1] = np.where(left, 1e5 * ratio, 1e5)
+    else:
+        bubble = (x - 0.5 * W) ** 2 + (y - 0.5) ** 2 < R * R
+        pr[0] = np.where(bubble, 1.0 - ALPHA_FLOOR, ALPHA_FLOOR)
+        pr[1] = np.where((x < 0.25 * W) & (y >= 0.0 * y), 1e5 * ratio, 1e5)
+    return pr
+
+
+def batch_params() -> Params:
+    """Water/air, heat conduction with the conduction-disc law, no viscosity,
+    FP32 bulk, P by formula."""
+    return Params(gamma=(WATER["gamma"], AIR["gamma"]), pinf=(WATER["pinf"], AIR["pinf"]),
+                  cv=(WATER["cv"], AIR["cv"]), k0=(0.6, 0.026), k_exp=2.0, T_ref=300.0, mu=(0.0, 0.0),
+                  cfl=0.5, p_policy=P_FORMULA, precision=PRECISION_FP32_BULK)
+
+
+def batch(ninst: int = 256, seed: int = 4, sizes=(128, 256, 512, 1024)):
+    """ninst instances with nx, ny drawn independently and uniformly from
+    `sizes`; returns (params, list of (nx, ny, dx, dy), list of primitive arrays)."""
+    rng = np.random.default_rng(seed)
+    grids, prims = [], []
+    for _ in range(ninst):
+        nx = int(rng.choice(sizes))
+        ny = int(rng.choice(sizes))
+        h = 1.0 / ny
+        grids.append((nx, ny, h, h))
+        prims.append(batch_instance(nx, ny, rng))
+    return batch_params(), grids, prims
