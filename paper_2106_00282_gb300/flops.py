@@ -8,12 +8,12 @@ tile is not algorithmic work and is not counted.
 hyperbolic sweep (one axis), per cell:
   primitives (alpha_1, rho, u_n, u_t, p_1, p_2)                          10
   minmod slopes (2 differences x 7) + face values (2 sides x 7 x 2)       42
-  face states, 2 sides x (E_k, rho_k, c_k^2, p, c, rho u, rho E)          66
+  face states, 2 sides x (E_k, p, c^2 = (a1 A1 + a2 A2)/rho, rho u, rho E) 58
   HLLC: S_L, S_R, S*, star state, flux                                    53
   Godunov update with the R term                                          37
   pressure relaxation (quadratic, alpha, p from rho E, E_k)               65
-                                                                  total  273
-CFL wave-speed maximum, per cell                                          28
+                                                                  total  265
+CFL wave-speed maximum, per cell                                          24
 heat stage (temperature relaxation fused), per cell:
   equilibrium 28 + energies 10 + temperature 10 + coefficients 28 = 76 (A)
   Gershgorin bound 13 (B); per predictor sweep 19 (C, 2P - 2 of them);
@@ -25,8 +25,8 @@ viscous stage (one axis), per cell:
 """
 from __future__ import annotations
 
-SWEEP = 273
-WAVE = 28
+SWEEP = 265
+WAVE = 24
 HEAT_BASE, HEAT_SWEEP = 152, 19
 VISC_BASE, VISC_SWEEP, PRELAX = 83, 24, 65
 
