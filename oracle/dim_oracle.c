@@ -56,12 +56,15 @@ typedef struct {
     double k0[2], k_exp, T_ref; /* lambda_k(T) = k0_k (T/T_ref)^k_exp */
     double mu[2];
     double cfl;
-    int limiter;  /* 0: first order (no reconstruction), 1: minmod MUSCL */
+    int limiter;  /* 0: first order, 1: minmod MUSCL, 2: Overbee on alpha_2 and alpha_k rho_k with minmod
+                   * on u and p_k, 3: Overbee on alpha_2 only (the inconsistent combination of Sec. 4.1) */
     int bc[2];    /* per axis: 0 transmissive, 1 periodic */
     int trelax;   /* 0: off (no T relaxation, no conduction), 1: equilibrium */
     int n_outer;  /* outer iterations of Algorithm 1 */
     int p_policy; /* 0: P by formula, 1: fixed p_fixed, 2: clamp(formula, p_min, p_max) */
     int p_fixed, p_min, p_max;
+    int precision; /* unused: the oracle is FP64 */
+    double src[2]; /* external heat source intensities I_k, I_k = alpha_k I_k (Eq. I) */
 } orc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -202,6 +205,14 @@ static double minmod(double a, double b)
     return 0.0;
 }
 
+/* Overbee slope: the limiter phi(r) = max(0, min(2r, 2)) (the upper boundary of
+ * the TVD region; the paper cites the limiter without printing it), i.e. twice
+ * the minmod slope -- homogeneous of degree 1 like minmod (Sec. 3.6) */
+static double overbee(double a, double b)
+{
+    return 2.0 * minmod(a, b);
+}
+
 typedef struct {
     double a2, m1, m2, un, ut, rho, p, c;
     double q[NQ]; /* conserved face state, line-local order */
@@ -281,10 +292,15 @@ static void line_update(const orc_params *P, int n, double dtdx, const double *e
     for (int e = 0; e < ne; e++) line_prims(P, ext + NQ * e, W + 7 * e);
     /* MUSCL slopes: sigma_e = minmod(W_e - W_{e-1}, W_{e+1} - W_e) on every
      * component of W, the same limiter for alpha_2 and m_k (Sec. 3.6) */
-    if (P->limiter == 1)
+    /* limiter 2: Overbee on alpha_2, m1, m2 (components 0-2), minmod on the rest;
+     * limiter 3: Overbee on alpha_2 only */
+    if (P->limiter >= 1)
         for (int e = 1; e <= n + 2; e++)
-            for (int k = 0; k < 7; k++)
-                S[7 * e + k] = minmod(W[7 * e + k] - W[7 * (e - 1) + k], W[7 * (e + 1) + k] - W[7 * e + k]);
+            for (int k = 0; k < 7; k++) {
+                double dm = W[7 * e + k] - W[7 * (e - 1) + k], dp = W[7 * (e + 1) + k] - W[7 * e + k];
+                int ob = (P->limiter == 2 && k <= 2) || (P->limiter == 3 && k == 0);
+                S[7 * e + k] = ob ? overbee(dm, dp) : minmod(dm, dp);
+            }
     /* face f (f = 0..n) lies between extended cells f+1 and f+2 */
     for (int f = 0; f <= n; f++) {
         double wl[7], wr[7];
@@ -603,7 +619,7 @@ static double op_lam_max(const orc_op *o, const double *V)
  * explicit sweep (b_{2P-1} = 0, Eq. LIM_last) is applied by the caller in
  * conservative form. */
 static void lim_predict(const orc_op *o, int Pn, const double *b, double tau, const double *V,
-                        const double *v0, double *uhat)
+                        const double *v0, const double *f, double *uhat)
 {
     int n = o->nx * o->ny;
     double *cur = (double *)malloc(sizeof(double) * n);
@@ -615,7 +631,7 @@ static void lim_predict(const orc_op *o, int Pn, const double *b, double tau, co
         double rden = 1.0 / (1.0 + tau * bm); /* the prefactor of Eq. (LIM), once per sweep */
         op_apply(o, cur, Lv);
         for (int c = 0; c < n; c++)
-            nxt[c] = (v0[c] + tau * bm * cur[c] + tau * V[c] * Lv[c]) * rden;
+            nxt[c] = (v0[c] + tau * bm * cur[c] + tau * V[c] * Lv[c] + (f ? tau * f[c] : 0.0)) * rden;
         double *t = cur; cur = nxt; nxt = t;
     }
     memcpy(uhat, cur, sizeof(double) * n);
@@ -637,7 +653,7 @@ int orc_lim_solve(const orc_params *P, int nx, int ny, double dx, double dy, dou
     orc_cheb_schedule(Pn, lm, b);
     double *uh = (double *)malloc(sizeof(double) * n);
     double *Lu = (double *)malloc(sizeof(double) * n);
-    lim_predict(&o, Pn, b, tau, V, v0, uh);
+    lim_predict(&o, Pn, b, tau, V, v0, NULL, uh);
     op_apply(&o, uh, Lu);
     for (int c = 0; c < n; c++) v1[c] = v0[c] + tau * V[c] * Lu[c];
     if (lam_max_out) *lam_max_out = lm;
@@ -670,6 +686,8 @@ unsigned orc_heat(const orc_params *P, int nx, int ny, double dx, double dy, dou
     double *lam = (double *)malloc(sizeof(double) * n);
     double *uh = (double *)malloc(sizeof(double) * n);
     double *q = (double *)malloc(sizeof(double) * n);
+    double *Ia = (double *)malloc(sizeof(double) * n); /* I1 + I2 = a1 I1 + a2 I2 (Eq. I) */
+    double *f = (double *)malloc(sizeof(double) * n);  /* V (I1 + I2): the f of Eq. (LIM) */
     orc_op o;
     op_init(&o, nx, ny, dx, dy, P->bc);
     for (int c = 0; c < n; c++) {
@@ -692,6 +710,8 @@ unsigned orc_heat(const orc_params *P, int nx, int ny, double dx, double dy, dou
             double K = T * (r1 + r2);
             V[c] = 1.0 / (C1 + C2 + B1 * B1 / K);
             lam[c] = a1 * lambda_k(P, 0, T) + a2 * lambda_k(P, 1, T);
+            Ia[c] = a1 * P->src[0] + a2 * P->src[1];
+            f[c] = V[c] * Ia[c];
         }
         op_faces(&o, lam);
         double lm = op_lam_max(&o, V);
@@ -700,9 +720,11 @@ unsigned orc_heat(const orc_params *P, int nx, int ny, double dx, double dy, dou
         if (Pn > pmax_used) pmax_used = Pn;
         double *b = (double *)malloc(sizeof(double) * (2 * Pn - 1));
         orc_cheb_schedule(Pn, lm, b);
-        lim_predict(&o, Pn, b, tau, V, T0, uh);
+        lim_predict(&o, Pn, b, tau, V, T0, f, uh);
         free(b);
         op_apply(&o, uh, q);
+        /* the last sweep in conservative form: rho e gains tau (L_h u_hat + I1 + I2) */
+        for (int c = 0; c < n; c++) q[c] = q[c] + Ia[c];
         for (int c = 0; c < n; c++) {
             double T, a2;
             st |= equilibrium(P, U[0 * n + c], U[1 * n + c], re0[c] + tau * q[c], &T, &a2);
@@ -718,7 +740,7 @@ unsigned orc_heat(const orc_params *P, int nx, int ny, double dx, double dy, dou
         U[7 * n + c] = a2;
     }
     if (P_used) *P_used = pmax_used;
-    free(T0); free(re0); free(rE0); free(Ti); free(ai); free(V); free(lam); free(uh); free(q);
+    free(T0); free(re0); free(rE0); free(Ti); free(ai); free(V); free(lam); free(uh); free(q); free(Ia); free(f);
     free(o.lx); free(o.ly);
     return st;
 }
@@ -775,8 +797,8 @@ unsigned orc_viscous(const orc_params *P, int nx, int ny, double dx, double dy, 
     unsigned st = Pn < cheb_P_formula(tau, lm) ? ORC_PCAP : 0u;
     double *b = (double *)malloc(sizeof(double) * (2 * Pn - 1));
     orc_cheb_schedule(Pn, lm, b);
-    lim_predict(&o, Pn, b, tau, V, un0, unh);
-    lim_predict(&ot, Pn, b, tau, V, ut0, uth);
+    lim_predict(&o, Pn, b, tau, V, un0, NULL, unh);
+    lim_predict(&ot, Pn, b, tau, V, ut0, NULL, uth);
     free(b);
     /* conservative last sweep and energy updates, line by line */
     double *newU = (double *)malloc(sizeof(double) * NQ * n);
@@ -832,7 +854,10 @@ unsigned orc_viscous(const orc_params *P, int nx, int ny, double dx, double dy, 
 /* relaxation, heat conduction (Sec. 3 opening, Sec. 2.4).                    */
 /* ------------------------------------------------------------------------- */
 static int viscous_on(const orc_params *P) { return P->mu[0] > 0.0 || P->mu[1] > 0.0; }
-static int heat_on(const orc_params *P) { return P->trelax == 1 && (P->k0[0] > 0.0 || P->k0[1] > 0.0); }
+static int heat_on(const orc_params *P)
+{
+    return P->trelax == 1 && (P->k0[0] > 0.0 || P->k0[1] > 0.0 || P->src[0] > 0.0 || P->src[1] > 0.0);
+}
 
 /* end-of-step admissibility: alpha_2 in (0,1), m_k > 0, p_k + pinf_k > 0 */
 static unsigned final_check(const orc_params *P, int n, const double *U)

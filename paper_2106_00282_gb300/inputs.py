@@ -29,7 +29,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # flag values shared by both consumers' parameter structs
-LIMITER_NONE, LIMITER_MINMOD = 0, 1
+LIMITER_NONE, LIMITER_MINMOD, LIMITER_OVERBEE = 0, 1, 2
+LIMITER_OVERBEE_ALPHA_ONLY = 3  # the inconsistent combination (oracle only)
 BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
 TRELAX_OFF, TRELAX_EQUILIBRIUM = 0, 1
 P_FORMULA, P_FIXED, P_CLAMP = 0, 1, 2
@@ -59,6 +60,7 @@ class Params:
     p_min: int = 1
     p_max: int = 24
     precision: int = PRECISION_FP64  # read by the CUDA library only; the oracle is FP64
+    src: tuple = (0.0, 0.0)          # external heat source intensities I_k (W/m^3 of phase k)
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
