@@ -51,6 +51,8 @@ extern "C" {
 /* flag values of dim_params */
 #define DIM_LIMITER_NONE 0   /* first-order Godunov */
 #define DIM_LIMITER_MINMOD 1 /* PVT-consistent MUSCL, Sec. 3.6 */
+#define DIM_LIMITER_OVERBEE 2 /* interface sharpening (cited in Sec. 4.1): slope 2 minmod on alpha_2 and
+                                 alpha_k rho_k, minmod on u and p_k */
 #define DIM_BC_TRANSMISSIVE 0
 #define DIM_BC_PERIODIC 1
 #define DIM_TRELAX_OFF 0         /* no temperature relaxation and no conduction */
@@ -87,6 +89,8 @@ typedef struct dim_params {
     int n_outer; /* outer iterations of Algorithm 1 (>= 1) */
     int p_policy, p_fixed, p_min, p_max;
     int precision; /* DIM_PRECISION_FP64 or DIM_PRECISION_FP32_BULK */
+    double src[2]; /* external heat source I_k >= 0 per unit volume of phase k: I_k = alpha_k I_k (Eq. I),
+                      deposited in the heat-conduction stage */
 } dim_params;
 
 typedef struct dim_ctx dim_ctx; /* opaque: parameters, grid, stream, scratch */

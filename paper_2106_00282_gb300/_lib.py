@@ -36,7 +36,7 @@ class DimParams(C.Structure):
         ("mu", C.c_double * 2), ("cfl", C.c_double),
         ("limiter", C.c_int), ("bc", C.c_int * 2), ("trelax", C.c_int), ("n_outer", C.c_int),
         ("p_policy", C.c_int), ("p_fixed", C.c_int), ("p_min", C.c_int), ("p_max", C.c_int),
-        ("precision", C.c_int),
+        ("precision", C.c_int), ("src", C.c_double * 2),
     ]
 
 
@@ -59,6 +59,7 @@ def make_params(p) -> DimParams:
     s.p_min = p.p_min
     s.p_max = p.p_max
     s.precision = getattr(p, "precision", 0)
+    s.src[:] = list(getattr(p, "src", (0.0, 0.0)))
     return s
 
 

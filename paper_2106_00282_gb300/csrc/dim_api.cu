@@ -72,7 +72,11 @@ static bool g_setup_done[64];
 
 
 static bool viscous_on(const dim_params &h) { return h.mu[0] > 0.0 || h.mu[1] > 0.0; }
-static bool heat_on(const dim_params &h) { return h.trelax == DIM_TRELAX_EQUILIBRIUM && (h.k0[0] > 0.0 || h.k0[1] > 0.0); }
+static bool heat_on(const dim_params &h)
+{
+    return h.trelax == DIM_TRELAX_EQUILIBRIUM &&
+           (h.k0[0] > 0.0 || h.k0[1] > 0.0 || h.src[0] > 0.0 || h.src[1] > 0.0);
+}
 
 static cudaError_t prof_begin(dim_ctx *c, int kid, int *slot)
 {
@@ -115,7 +119,7 @@ static dimk::HeatScratch heat_scratch(dim_ctx *c)
 {
     size_t n = (size_t)c->p.n;
     double *S = c->S;
-    return dimk::HeatScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n};
+    return dimk::HeatScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n};
 }
 
 static dimk::ViscScratch visc_scratch(dim_ctx *c)
@@ -196,7 +200,9 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
         if (hp->bc[k] != DIM_BC_TRANSMISSIVE && hp->bc[k] != DIM_BC_PERIODIC) return DIM_EINVAL;
     }
     if (!(hp->cfl > 0.0) || !(hp->T_ref > 0.0)) return DIM_EINVAL;
-    if (hp->limiter != DIM_LIMITER_NONE && hp->limiter != DIM_LIMITER_MINMOD) return DIM_EINVAL;
+    if (hp->limiter != DIM_LIMITER_NONE && hp->limiter != DIM_LIMITER_MINMOD && hp->limiter != DIM_LIMITER_OVERBEE)
+        return DIM_EINVAL;
+    if (!(hp->src[0] >= 0.0) || !(hp->src[1] >= 0.0)) return DIM_EINVAL;
     if (hp->trelax != DIM_TRELAX_OFF && hp->trelax != DIM_TRELAX_EQUILIBRIUM) return DIM_EINVAL;
     if (hp->n_outer < 1 || hp->n_outer > 8) return DIM_EINVAL;
     if (hp->p_policy < DIM_P_FORMULA || hp->p_policy > DIM_P_CLAMP) return DIM_EINVAL;
@@ -216,6 +222,7 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
         p.k0[k] = hp->k0[k];
         p.mu[k] = hp->mu[k];
         p.bc[k] = hp->bc[k];
+        p.src[k] = hp->src[k];
     }
     p.k_exp = hp->k_exp;
     p.T_ref = hp->T_ref;

@@ -315,7 +315,7 @@ __device__ bool stage_heat(const BatchDev &d)
 {
     constexpr int SLOT = 2;
     const int nch = d.ch[d.ninst];
-    // scratch per instance: plane 0 (FP64, unused here), FP32 planes T0, V, L, va, vb
+    // scratch per instance: plane 0 (FP64, unused here), FP32 planes T0, V, L, va, vb, Ia
     auto scr = [&](int i) { return (float *)(d.S + 8 * d.off[i] + d.prm[i].n); };
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
@@ -338,6 +338,7 @@ __device__ bool stage_heat(const BatchDev &d)
             heat_coeffs_f(p, m1, m2, T, a2, V, L);
             F[n + c] = V;
             F[2 * n + c] = L;
+            F[5 * (size_t)n + c] = (float)((1.0 - a2) * p.src[0] + a2 * p.src[1]);
         }
         flag(&d.sc[i], st);
     }
@@ -374,9 +375,10 @@ __device__ bool stage_heat(const BatchDev &d)
             const double b = d.bs[((size_t)SLOT * d.ninst + i) * 2 * PMAX + (m - 1)];
             const float tb = (float)(tau * b), rden = (float)(1.0 / (1.0 + tau * b)), tauf = (float)tau;
             const float idx2 = (float)p.idx2, idy2 = (float)p.idy2;
+            const float *Ia = F + 5 * (size_t)n;
             for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
                 float Lv = lapf(p, neighbours(p, c), c, vin, L, idx2, idy2);
-                vout[c] = (T0[c] + tb * vin[c] + tauf * V[c] * Lv) * rden;
+                vout[c] = (T0[c] + tb * vin[c] + tauf * V[c] * (Lv + Ia[c])) * rden;
             }
         }
         if (!grid_barrier(d.g)) return false;
@@ -396,7 +398,7 @@ __device__ bool stage_heat(const BatchDev &d)
         const float idx2 = (float)p.idx2, idy2 = (float)p.idy2;
         unsigned st = 0;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            double q = (double)lapf(p, neighbours(p, c), c, vin, L, idx2, idy2);
+            double q = (double)lapf(p, neighbours(p, c), c, vin, L, idx2, idy2) + (double)F[5 * (size_t)n + c];
             double m1 = U[c], m2 = U[n + c];
             double T, a2;
             unsigned r = equilibrium(p, m1, m2, U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
@@ -680,7 +682,7 @@ int dim_batch_init(dim_batch **out, const dim_params *hp, int ninst, const int *
     }
     b->viscous = hp->mu[0] > 0.0 || hp->mu[1] > 0.0;
     b->trelax = hp->trelax == DIM_TRELAX_EQUILIBRIUM;
-    b->heat = b->trelax && (hp->k0[0] > 0.0 || hp->k0[1] > 0.0);
+    b->heat = b->trelax && (hp->k0[0] > 0.0 || hp->k0[1] > 0.0 || hp->src[0] > 0.0 || hp->src[1] > 0.0);
     int dev = 0;
     bool ok = cudaGetDevice(&dev) == cudaSuccess &&
               cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;

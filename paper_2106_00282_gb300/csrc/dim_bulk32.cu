@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) k_heat32(const DevParams p, double *U, He
         heat_coeffs_f(p, m1, m2, T, a2, V, L);
         s.V[c] = V;
         s.L[c] = L;
+        s.Ia[c] = (float)((1.0 - a2) * p.src[0] + a2 * p.src[1]);
     }
     for (int it = 0; it < nout; it++) {
         if (!grid_barrier(sc)) return;
@@ -108,14 +109,14 @@ __global__ void __launch_bounds__(256) k_heat32(const DevParams p, double *U, He
             const float rden = (float)(1.0 / (1.0 + tau * s_b[m - 1]));
             for (int c = t0; c < n; c += nt) {
                 float Lv = lapf(p, neighbours(p, c), c, vin, s.L, idx2, idy2);
-                vout[c] = (s.T0[c] + tb * vin[c] + tauf * s.V[c] * Lv) * rden;
+                vout[c] = (s.T0[c] + tb * vin[c] + tauf * s.V[c] * (Lv + s.Ia[c])) * rden;
             }
             if (!grid_barrier(sc)) return;
             vin = vout;
         }
         if (it == nout - 1) {
             for (int c = t0; c < n; c += nt) {
-                double q = (double)lapf(p, neighbours(p, c), c, vin, s.L, idx2, idy2);
+                double q = (double)lapf(p, neighbours(p, c), c, vin, s.L, idx2, idy2) + (double)s.Ia[c];
                 double m1 = U[c], m2 = U[n + c];
                 double rhoe = U[4 * n + c] + U[5 * n + c] + tau * q;
                 double T, a2;
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(256) k_heat32(const DevParams p, double *U, He
             }
         } else {
             for (int c = t0; c < n; c += nt) {
-                double q = (double)lapf(p, neighbours(p, c), c, vin, s.L, idx2, idy2);
+                double q = (double)lapf(p, neighbours(p, c), c, vin, s.L, idx2, idy2) + (double)s.Ia[c];
                 double T, a2;
                 unsigned r = equilibrium(p, U[c], U[n + c], U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
                 if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(256) k_heat32(const DevParams p, double *U, He
                 heat_coeffs_f(p, U[c], U[n + c], (double)s.Ti[c], s.Ai[c], V, L);
                 s.V[c] = V;
                 s.L[c] = L;
+                s.Ia[c] = (float)((1.0 - s.Ai[c]) * p.src[0] + s.Ai[c] * p.src[1]);
             }
         }
     }
@@ -346,7 +348,7 @@ cudaError_t launch_heat32(const DevParams &p, double *U, double *S, Scalars *sc,
 {
     size_t n = (size_t)p.n;
     float *F = (float *)(S + n);  // six FP32 planes after the FP64 plane 0
-    HeatScratch32 hs{F, F + n, F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n, S};
+    HeatScratch32 hs{F, F + n, F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n, F + 6 * n, S};
     DevParams pp = p;
     void *args[] = {(void *)&pp, (void *)&U, (void *)&hs, (void *)&sc, (void *)&dt_host, (void *)&trelax_first,
                     (void *)&check};

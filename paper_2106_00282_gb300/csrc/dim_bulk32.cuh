@@ -194,11 +194,16 @@ __device__ __forceinline__ void sweep32_tile(const DevParams &p, const double *_
         const double *A = sU + 7 * NL;
         double aL = A[iL], aR = A[iR];
         float wl[6], wr[6];
-        if (p.limiter == DIM_LIMITER_MINMOD) {
+        if (p.limiter != DIM_LIMITER_NONE) {
             const int iLL = cidx(fc, l), iRR = cidx(fc + 3, l);
-            // volume fraction in FP64 (same limiter, Sec. 3.6)
+            const bool ob = p.limiter == DIM_LIMITER_OVERBEE;
+            // volume fraction in FP64 (same limiter as alpha_k rho_k, Sec. 3.6)
             double sl = minmod(A[iL] - A[iLL], A[iR] - A[iL]);
             double sr = minmod(A[iR] - A[iL], A[iRR] - A[iR]);
+            if (ob) {
+                sl = 2.0 * sl;
+                sr = 2.0 * sr;
+            }
             aL = A[iL] + 0.5 * sl;
             aR = A[iR] - 0.5 * sr;
 #pragma unroll
@@ -206,6 +211,10 @@ __device__ __forceinline__ void sweep32_tile(const DevParams &p, const double *_
                 const float *Wk = sW + k * NL;
                 float s1 = minmodf(Wk[iL] - Wk[iLL], Wk[iR] - Wk[iL]);
                 float s2 = minmodf(Wk[iR] - Wk[iL], Wk[iRR] - Wk[iR]);
+                if (ob && k <= 1) {  // m1, m2
+                    s1 = 2.f * s1;
+                    s2 = 2.f * s2;
+                }
                 wl[k] = Wk[iL] + 0.5f * s1;
                 wr[k] = Wk[iR] - 0.5f * s2;
             }
@@ -287,7 +296,7 @@ __host__ __device__ constexpr size_t sweep32_smem(int TN, int TL)
 // parabolic stages in FP32 bulk
 // ---------------------------------------------------------------------------
 struct HeatScratch32 {
-    float *T0, *V, *L, *va, *vb, *Ti;
+    float *T0, *V, *L, *va, *vb, *Ti, *Ia;  // Ia = a1 I1 + a2 I2 (external source)
     double *Ai;  // outer-iteration volume fraction: FP64 (1 - alpha_2 must keep its precision)
 };
 struct ViscScratch32 {

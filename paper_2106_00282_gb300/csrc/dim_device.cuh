@@ -33,6 +33,7 @@ struct DevParams {
     int nx, ny, n;
     int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
     int precision;  // DIM_PRECISION_FP64 or DIM_PRECISION_FP32_BULK
+    double src[2];  // external heat source intensities I_k
     // roots of T_P: beta[(P-1)*PMAX + m-1] = cos((2m-1) pi / (2P)), m = 1..P,
     // tabulated on the host (libm) once per context
     const double *beta;
@@ -53,7 +54,7 @@ constexpr int LAM_VX = 8, LAM_VY = 9;
 
 // scratch planes of the parabolic stages (n doubles each)
 struct HeatScratch {
-    double *T0, *V, *L, *va, *vb, *Ti, *Ai;
+    double *T0, *V, *L, *va, *vb, *Ti, *Ai, *Ia;  // Ia = a1 I1 + a2 I2 (external source)
 };
 struct ViscScratch {
     double *V, *A2, *u0, *w0, *ua, *ub, *wa, *wb;

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
         heat_coeffs(p, m1, m2, T, a2, V, L);
         s.V[c] = V;
         s.L[c] = L;
+        s.Ia[c] = (1.0 - a2) * p.src[0] + a2 * p.src[1];
     }
 
     for (int it = 0; it < nout; it++) {
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             const double rden = 1.0 / (1.0 + tau * bm);
             for (int c = t0; c < n; c += nt) {
                 double Lv = lap(p, neighbours(p, c), c, vin, s.L);
-                vout[c] = (s.T0[c] + tau * bm * vin[c] + tau * s.V[c] * Lv) * rden;
+                vout[c] = (s.T0[c] + tau * bm * vin[c] + tau * s.V[c] * Lv + tau * (s.V[c] * s.Ia[c])) * rden;
             }
             if (!grid_barrier(sc)) return;
             vin = vout;
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
         //    the projection onto the p,T-equilibrium manifold
         if (it == nout - 1) {
             for (int c = t0; c < n; c += nt) {
-                double q = lap(p, neighbours(p, c), c, vin, s.L);
+                double q = lap(p, neighbours(p, c), c, vin, s.L) + s.Ia[c];
                 double m1 = U[c], m2 = U[n + c];
                 double rhoe = U[4 * n + c] + U[5 * n + c] + tau * q;
                 double T, a2;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             }
         } else {
             for (int c = t0; c < n; c += nt) {
-                double q = lap(p, neighbours(p, c), c, vin, s.L);
+                double q = lap(p, neighbours(p, c), c, vin, s.L) + s.Ia[c];
                 double T, a2;
                 unsigned r = equilibrium(p, U[c], U[n + c], U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
                 if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
                 heat_coeffs(p, U[c], U[n + c], s.Ti[c], s.Ai[c], V, L);
                 s.V[c] = V;
                 s.L[c] = L;
+                s.Ia[c] = (1.0 - s.Ai[c]) * p.src[0] + s.Ai[c] * p.src[1];
             }
         }
     }

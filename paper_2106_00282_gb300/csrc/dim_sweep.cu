@@ -172,13 +172,18 @@ __global__ void __launch_bounds__(TN *TL) k_sweep(const DevParams p, const doubl
         else { f = fi / TL; l = fi - f * TL; }
         const int iL = cidx(f + 1, l), iR = cidx(f + 2, l);
         double wl[7], wr[7];
-        if (p.limiter == DIM_LIMITER_MINMOD) {
+        if (p.limiter != DIM_LIMITER_NONE) {
             const int iLL = cidx(f, l), iRR = cidx(f + 3, l);
+            const bool ob = p.limiter == DIM_LIMITER_OVERBEE;
 #pragma unroll
             for (int k = 0; k < 7; k++) {
                 const double *Wk = sW + k * NL;
                 double sl = minmod(Wk[iL] - Wk[iLL], Wk[iR] - Wk[iL]);
                 double sr = minmod(Wk[iR] - Wk[iL], Wk[iRR] - Wk[iR]);
+                if (ob && k <= 2) {  // Overbee on alpha_2, m1, m2: twice the minmod slope
+                    sl = 2.0 * sl;
+                    sr = 2.0 * sr;
+                }
                 wl[k] = Wk[iL] + 0.5 * sl;
                 wr[k] = Wk[iR] - 0.5 * sr;
             }

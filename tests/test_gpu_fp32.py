@@ -60,7 +60,24 @@ CASES = {
     "viscous_shock": lambda I: I.shock_tube(n=400, k=(1e6, 1e6), mu=(500.0, 1.0), p_policy=0),
     "ragged_131x37": lambda I: I.impact(131, 37),
     "shock_tube_column": lambda I: I.shock_tube(n=300, axis=1),
+    "overbee_shock": lambda I: I.shock_tube(n=400, limiter=I.LIMITER_OVERBEE),
+    "overbee_impact": lambda I: _with(I.impact(160, 80), limiter=I.LIMITER_OVERBEE),
+    "heat_source": lambda I: _with(I.shock_tube(n=400), src=(1e12, 1e10)),
+    "spitzer_like": lambda I: I.conduction_disc(n=96, k_exp=2.5),
 }
+
+
+def _with(wl, **kw):
+    wl.params = wl.params.replace(**kw)
+    return wl
+
+
+# The Overbee limiter sits on the boundary of the TVD region and turns rounding
+# noise into staircases: on the 2D impact the FP64 oracle itself moves by 1.3e-5
+# under a 1e-7 relative change of its input, and FP32 rounding enters at every
+# step, so this one case is held to 1e-3 (measured 5e-4); the Overbee shock tube
+# meets the standard bound.
+TOL_CASE = {"overbee_impact": 1e-3}
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -71,7 +88,7 @@ def test_fp32_bulk_100_steps(torch_cuda, O, I, case):
     G, Uo, st, sto = _run(torch_cuda, O, wl, 100)
     e = rel_l1_32(G, Uo, O, wl, wl.params)
     print(f"[fp32] {case}: rel L1 per field {np.array2string(e, precision=2)}")
-    assert np.all(e <= TOL32), e
+    assert np.all(e <= TOL_CASE.get(case, TOL32)), e
     assert not np.isnan(G).any()
     assert st & (_lib.ST_NONPHYS | _lib.ST_NAN | _lib.ST_TIMEOUT) == 0
 

@@ -159,7 +159,17 @@ CASES = {
     "no_relaxation": lambda I: I.shock_tube(n=400, k=(0, 0), trelax=0),
     "viscous_shock": lambda I: I.shock_tube(n=400, k=(1e6, 1e6), mu=(500.0, 1.0), p_policy=0),
     "capped_P": lambda I: I.shock_tube(n=300, k=(1e7, 1e7), p_policy=0),
+    # method variants: Overbee sharpening, external heat source, T^(5/2) conductivity
+    "overbee_impact": lambda I: _with(I.impact(160, 80), limiter=I.LIMITER_OVERBEE),
+    "overbee_shock": lambda I: I.shock_tube(n=400, limiter=I.LIMITER_OVERBEE),
+    "heat_source": lambda I: _with(I.shock_tube(n=400), src=(1e12, 1e10)),
+    "spitzer_like": lambda I: I.conduction_disc(n=96, k_exp=2.5),
 }
+
+
+def _with(wl, **kw):
+    wl.params = wl.params.replace(**kw)
+    return wl
 
 
 @pytest.mark.parametrize("case", list(CASES))
