@@ -129,6 +129,19 @@ def flops_per_cell(kernel: str, wl) -> float:
     return flops.per_cell(kernel, wl.params)
 
 
+def aggregate(ms_local: float, units_per_rank: float, world: int, dev):
+    """Whole-job figures of `world` replicas: the slowest rank's time (max over
+    ranks) and the units all ranks processed divided by that time (per second).
+    With world > 1 every rank must call this (one all-reduce)."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
     import torch
 
@@ -170,14 +183,10 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
     clocks = clocks_sampler_stop(sampler)
     s.profile(False, reset=False)
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = aggregate(ms, ncell * K, world, dev)
     st = s.status()
     if st & 3:
         raise RuntimeError(f"inadmissible state during the timed steps (status {st})")
-    value = world * ncell * K / (ms_max / 1e3)
 
     # per-kernel device times over the timed region
     kern = {}
@@ -223,17 +232,15 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
             t0 = time.perf_counter()
             s.step_host(Uh, 1)
             tot += time.perf_counter() - t0
-        tt = torch.tensor([tot], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * ncell * Ke / float(tt.item()), "unit": UNIT,
+        _, e2e_value = aggregate(1e3 * tot, ncell * Ke, world, dev)
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(Uh.numel() * 8), "d2h_bytes_per_step": int(Uh.numel() * 8),
                "steps": Ke, "api": "dim_step_host (pinned host state, H2D + step + D2H per step)"}
     return dict(value=value, ms_per_step=step_us / 1e3, wl=wl, roofline=roofline, e2e=e2e, clocks=clocks,
                 launches=launches, hbm_frac=hbm_frac, status_warmup=st0)
 
 
-def run_batched(dev, steps=10, warmup=3):
+def run_batched(dev, world=1, steps=10, warmup=3):
     """256 independent water/air problems of uneven sizes (FP32 bulk), one
     persistent launch per step replayed from a CUDA graph; the packed state
     (4.1 GB) is larger than the L2, so no flush is needed."""
@@ -250,15 +257,20 @@ def run_batched(dev, steps=10, warmup=3):
     B.step(U, max(3, warmup))
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     for a, e in ev:
         a.record()
         B.step(U, 1)
         e.record()
     torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(e) for a, e in ev)
+    if world > 1:
+        torch.distributed.barrier()
+    ms, value = aggregate(sum(a.elapsed_time(e) for a, e in ev), B.ncell * steps, world, dev)
     flags, anyf = B.status()
     sizes = sorted({g[0] for g in grids} | {g[1] for g in grids})
-    out = {"value": B.ncell * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "instances": len(grids),
+    out = {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "instances": len(grids) * world,
            "cells": B.ncell, "sizes": sizes, "steps": steps, "status_or": anyf,
            "autotune": {"variant": cfg[0], "blocks": cfg[1], "x_tile": [cfg[2], cfg[3]], "y_tile": [cfg[4], cfg[5]]},
            "launch": "one persistent cooperative kernel per step, CUDA-graph replay",
@@ -298,7 +310,7 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=dev)
     r = run_ours(args, rank, world, dev)
     r32 = None if args.no_fp32 else run_ours(args, rank, world, dev, precision=1, with_e2e=False)
-    rb = None if args.no_batch else run_batched(dev)
+    rb = None if args.no_batch else run_batched(dev, world)
     if rank == 0:
         wl = r["wl"]
         cpu = None
