@@ -1,4 +1,4 @@
-"""ctypes binding of the FP64 CPU oracle (``dim_oracle.c``).
+"""ctypes binding of the FP64 CPU oracle (``dim_oracle.cc``).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
 CPU-baseline / reference leg of the benchmark.  The product path never loads
@@ -13,16 +13,19 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "dim_oracle.c")
+_SRC = os.path.join(_HERE, "dim_oracle.cc")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
-def build(force: bool = False, openmp: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction)."""
-    out = _LIB if not openmp else os.path.join(_HERE, "liboracle_omp.so")
+SCHED = 11  # doubles per step in a schedule record: S, lambda_max heat x8, viscous x, viscous y
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no FMA contraction)."""
+    out = _LIB
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, _SRC, "-lm"]
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, _SRC, "-lm"]
         subprocess.check_call(cmd)
     return out
 
@@ -79,6 +82,10 @@ def lib():
         L.orc_heat.argtypes = [P, i, i, d, d, d, _D, C.POINTER(i)]; L.orc_heat.restype = u
         L.orc_viscous.argtypes = [P, i, i, d, d, i, d, _D, C.POINTER(i)]; L.orc_viscous.restype = u
         L.orc_step.argtypes = [P, i, i, d, d, _D, i, d, _D, C.POINTER(i)]; L.orc_step.restype = u
+        L.orc_step_sched.argtypes = [P, i, i, d, d, _D, i, _D, i]; L.orc_step_sched.restype = u
+        L.orc_step_frozen.argtypes = [P, i, i, d, d, _D, i, _D, C.c_void_p, C.c_size_t, i, C.POINTER(C.c_size_t)]
+        L.orc_step_frozen.restype = u
+        L.orc_step_tangent.argtypes = [P, _D, i, i, d, d, _D, _D, i, _D]; L.orc_step_tangent.restype = u
         L.orc_cheb_P.argtypes = [P, d, d]; L.orc_cheb_P.restype = i
         L.orc_cheb_schedule.argtypes = [i, d, _D]; L.orc_cheb_schedule.restype = None
         L.orc_lim_solve.argtypes = [P, i, i, d, d, d, _D, _D, _D, _D, _D]; L.orc_lim_solve.restype = i
@@ -155,6 +162,65 @@ def step(params, U, dx, dy, nsteps=1, dt_fixed=0.0):
     st = lib().orc_step(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, _ptr(U), nsteps, dt_fixed,
                         C.byref(dtl), C.byref(ph))
     return U, st, dtl.value, ph.value
+
+
+def step_sched(params, U, dx, dy, nsteps, sched=None):
+    """nsteps steps; with sched=None the schedule (S and every lambda_max, per
+    step) is recorded and returned, with a given sched it is replayed.
+    Returns (U, status, sched)."""
+    U = _state(U).copy()
+    replay = sched is not None
+    if sched is None:
+        sched = np.zeros((nsteps, SCHED))
+    sched = np.ascontiguousarray(sched, dtype=np.float64)
+    assert sched.shape == (nsteps, SCHED)
+    st = lib().orc_step_sched(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, _ptr(U), nsteps,
+                              _ptr(sched), int(replay))
+    return U, st, sched
+
+
+def step_frozen(params, U, dx, dy, nsteps, frozen=None):
+    """nsteps steps.  frozen=None: record the schedule and every branch of the
+    sweeps (limiter operand, Davis bounds, HLLC region) and return them;
+    frozen=(sched, tape): replay them, so the run follows the recorded
+    branches (the branch-frozen map).  Returns (U, status, (sched, tape))."""
+    U = _state(U).copy()
+    lib_ = lib()
+    if frozen is None:
+        sched = np.zeros((nsteps, SCHED))
+        cap = 1 << 16
+        while True:
+            tape = np.zeros(cap, dtype=np.uint8)
+            used = C.c_size_t(0)
+            Ur = U.copy()
+            st = lib_.orc_step_frozen(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, _ptr(Ur), nsteps,
+                                      _ptr(sched), tape.ctypes.data, cap, 0, C.byref(used))
+            if used.value <= cap:
+                return Ur, st, (sched, tape[:used.value].copy())
+            cap = used.value
+    sched, tape = frozen
+    sched = np.ascontiguousarray(sched, dtype=np.float64).copy()
+    tape = np.ascontiguousarray(tape, dtype=np.uint8)
+    used = C.c_size_t(0)
+    st = lib_.orc_step_frozen(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, _ptr(U), nsteps, _ptr(sched),
+                              tape.ctypes.data, tape.size, 1, C.byref(used))
+    if used.value != tape.size:
+        raise ValueError(f"branch record of {tape.size} decisions replayed by a run taking {used.value}")
+    return U, st, (sched, tape)
+
+
+def step_tangent(params, U, dU, dx, dy, nsteps, dparams=None):
+    """Tangent-linear map of nsteps steps with the schedule frozen at the run's
+    own values: returns (U_T, dU_T, status, sched).  dparams: tangents of
+    (k0_1, k0_2, mu_1, mu_2, I_1, I_2) or None."""
+    U = _state(U).copy()
+    dU = _state(dU).copy()
+    assert dU.shape == U.shape
+    sched = np.zeros((nsteps, SCHED))
+    dp = None if dparams is None else np.ascontiguousarray(dparams, dtype=np.float64)
+    st = lib().orc_step_tangent(C.byref(_params(params)), None if dp is None else _ptr(dp), U.shape[2], U.shape[1],
+                                dx, dy, _ptr(U), _ptr(dU), nsteps, _ptr(sched))
+    return U, dU, st, sched
 
 
 def cheb_P(params, tau, lam_max) -> int:

@@ -215,6 +215,78 @@ def conduction_disc(n: int = 2048, seed: int = 3, steps=300, p_min=8, p_max=16, 
                     dict(seed=seed, modes=ms.tolist(), amp=amp.tolist(), phase=phase.tolist()))
 
 
+def smooth_mixture(nx: int = 64, ny: int = 1, seed: int = 0, k=(0.6, 0.026), mu=(1e-3, 1.8e-5),
+                   limiter=LIMITER_MINMOD, bc=(BC_PERIODIC, BC_PERIODIC), u_amp=20.0) -> Workload:
+    """A smooth water/air mixture on the periodic unit square (or segment):
+    alpha_2 = 0.5 + 0.3 f_1, p = 1e5 (1 + 0.05 f_2), T = 300 (1 + 0.05 f_3),
+    u = u_amp f_4, v = u_amp f_5, each f_i a seeded sum of two low Fourier modes
+    with |f_i| <= 1.  No cell pair has equal states, so slopes, wave-speed
+    bounds and limiter branches are generic: the workload of the derivative
+    checks (the step is piecewise smooth; at exactly uniform states the limiter
+    is not differentiable)."""
+    rng = np.random.default_rng(seed)
+    hx, hy = 1.0 / nx, 1.0 / ny
+    x = _centers(nx, 1.0)[None, :]
+    y = _centers(ny, 1.0)[:, None] if ny > 1 else np.zeros((1, 1))
+
+    def f():
+        kx = rng.integers(1, 3, size=2)
+        ky = rng.integers(1, 3, size=2) if ny > 1 else np.zeros(2, dtype=int)
+        ph = rng.uniform(0.0, 2.0 * math.pi, size=2)
+        g = (0.6 * np.sin(2.0 * math.pi * (kx[0] * x + ky[0] * y) + ph[0]) +
+             0.4 * np.cos(2.0 * math.pi * (kx[1] * x - ky[1] * y) + ph[1]))
+        return np.broadcast_to(g, (ny, nx))
+
+    params = Params(gamma=(WATER["gamma"], AIR["gamma"]), pinf=(WATER["pinf"], AIR["pinf"]),
+                    cv=(WATER["cv"], AIR["cv"]), k0=tuple(k), k_exp=2.0, T_ref=300.0, mu=tuple(mu), cfl=0.5,
+                    limiter=limiter, bc=tuple(bc), p_policy=P_FORMULA)
+    pr = _prim(ny, nx)
+    pr[0] = 0.5 + 0.3 * f()
+    pr[1] = 1e5 * (1.0 + 0.05 * f())
+    pr[2] = 300.0 * (1.0 + 0.05 * f())
+    pr[3] = u_amp * f()
+    pr[4] = u_amp * f() if ny > 1 else 0.0
+    dy = hy if ny > 1 else hx
+    return Workload("smooth_mixture", nx, ny, hx, dy, params, pr, 10, dict(seed=seed))
+
+
+def disc_interface(n: int, amp: np.ndarray, phase: np.ndarray, modes=(4, 19), r0: float = 0.2):
+    """The interface indicator s in [0, 1] of the perturbed disc of
+    `conduction_disc` (tanh profile of width 1.5 h), for given amplitudes."""
+    ms = np.arange(modes[0], modes[1] + 1)
+    h = 1.0 / n
+    x = _centers(n, 1.0)[None, :] - 0.5
+    y = _centers(n, 1.0)[:, None] - 0.5
+    r = np.hypot(x, y)
+    th = np.arctan2(y, x)
+    R = r0 + np.sum(np.asarray(amp)[:, None, None] * np.cos(ms[:, None, None] * th[None] +
+                                                          np.asarray(phase)[:, None, None]), axis=0)
+    return 0.5 * (1.0 + np.tanh((R - r) / (1.5 * h))), r, th, ms
+
+
+def disc_gradient(n: int = 512, seed: int = 3, steps: int = 200, ckpt: int = 20) -> Workload:
+    """Gradient problem on the conduction disc: 512^2 cells, FP64, 200 steps,
+    checkpoints every 20; 16 interface modes m = 4..19 with amplitudes
+    a_m ~ U[-1,1] 0.01 r0 and phases phi_m ~ U[0, 2 pi) from ``seed``; the
+    objective is the alpha(1-alpha)-weighted mean interface temperature, the
+    parameters of interest (k0_1, k0_2, mu_1, mu_2) and the 16 amplitudes."""
+    rng = np.random.default_rng(seed)
+    ms = np.arange(4, 20)
+    amp = rng.uniform(-1.0, 1.0, size=ms.size) * 0.01 * 0.2
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=ms.size)
+    params = Params(gamma=(WATER["gamma"], AIR["gamma"]), pinf=(WATER["pinf"], AIR["pinf"]),
+                    cv=(WATER["cv"], AIR["cv"]), k0=(0.6, 0.026), k_exp=2.0, T_ref=300.0,
+                    mu=(1e-3, 1.8e-5), cfl=0.5, p_policy=P_CLAMP, p_min=8, p_max=16)
+    s = disc_interface(n, amp, phase)[0]
+    pr = _prim(n, n)
+    pr[0] = ALPHA_FLOOR + (1.0 - 2.0 * ALPHA_FLOOR) * s
+    pr[1] = 1e5
+    pr[2] = 300.0 + (3000.0 - 300.0) * s
+    h = 1.0 / n
+    return Workload("disc_gradient", n, n, h, h, params, pr, steps,
+                    dict(seed=seed, modes=ms.tolist(), amp=amp.tolist(), phase=phase.tolist(), ckpt=ckpt))
+
+
 def random_states(ncell: int, seed: int, params: Params, p_range=(1e5, 1e9), T_range=(200.0, 2000.0),
                   a_range=(1e-6, 1 - 1e-6), u_range=(-300.0, 300.0)) -> np.ndarray:
     """Random per-cell (alpha_2, p, T, u, v) for pointwise tests, shape (5, 1, ncell)."""
