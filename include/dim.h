@@ -152,10 +152,54 @@ int dim_relax(dim_ctx *c, double *U, int which);
  * synchronizes). */
 int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used);
 
-/* Gradients of a final-time objective through nsteps steps (adjoint).  Not
- * implemented in this build: returns DIM_ENOTIMPL. */
+/* Schedule record of one step: DIM_SCHED doubles, [0] S = max_cells max_axis
+ * (|u_axis| + c)/h_axis (dt = cfl / S, Sec. 3.1), [1..8] the Gershgorin
+ * lambda_max of the heat-conduction solve of outer iterations 0..7 of Algorithm
+ * 1, [9] / [10] that of the viscous solve along x / y (Sec. 3.2); slots of
+ * stages that did not run are 0.  The Chebyshev parameter count P and the b_m
+ * of each solve follow from (dt, lambda_max). */
+#define DIM_SCHED 11
+/* Parameters a gradient is taken with respect to (dJ_dparams of dim_grad):
+ * k0_1, k0_2 (conductivity coefficients), mu_1, mu_2 (viscosities), I_1, I_2
+ * (external heat-source intensities, Eq. I). */
+#define DIM_GRAD_NPARAMS 6
+
+/* nsteps split steps as dim_step (FP64 precision only), recording (replay = 0)
+ * or replaying (replay != 0) the schedule: sched is a DEVICE array of
+ * nsteps * DIM_SCHED doubles, written per step, or read per step in place of
+ * the CFL reduction and of every LIM lambda_max reduction.  Replaying the
+ * record of a run on that run's initial state reproduces it bit for bit;
+ * replaying it on a perturbed state gives the map with the time steps and
+ * Chebyshev parameters held fixed, the map dim_grad differentiates.
+ * Asynchronous.  Errors: DIM_EINVAL (null pointers, nsteps < 0, FP32-bulk
+ * precision), DIM_ECUDA. */
+int dim_step_sched(dim_ctx *c, double *U, int nsteps, double *sched, int replay);
+
+/* Reverse-mode gradient (adjoint) of the map U0 -> U_T = nsteps split steps,
+ * FP64 precision, with the schedule of the run from U0 held fixed: the time
+ * step of every step (Sec. 3.1) and the lambda_max, hence P and b_m, of every
+ * LIM solve (Sec. 3.2), and every value-decided branch (limiter operand,
+ * Davis bounds, HLLC wave region) taken as in that run.  Given the adjoint
+ * dJ_dUT = dJ/dU_T of an objective J, returns dJ_dU0 = (dU_T/dU0)^T dJ_dUT and,
+ * when dJ_dparams != NULL, dJ/d(k0_1, k0_2, mu_1, mu_2, I_1, I_2).
+ *  - U0, dJ_dUT, dJ_dU0: DEVICE arrays of 8 planes (the state layout);
+ *    dJ_dU0 may alias dJ_dUT; U0 is not modified.
+ *  - dJ_dparams: HOST array of DIM_GRAD_NPARAMS doubles, or NULL.
+ *  - ckpt_every >= 1: the forward states are kept every ckpt_every steps and
+ *    each segment is recomputed from its checkpoint in the reverse sweep;
+ *    device memory ~ (nsteps/ckpt_every + ckpt_every + 10) states plus the
+ *    Chebyshev iterates of one step, allocated on the first call and reused.
+ * Synchronizes.  Errors: DIM_EINVAL (null pointers, nsteps < 0, ckpt_every < 1,
+ * FP32-bulk precision), DIM_ENONPHYS / DIM_ENOROOT / DIM_ETIMEOUT when the
+ * forward run meets them, DIM_ECUDA. */
 int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const double *dJ_dUT, double *dJ_dU0,
              double *dJ_dparams);
+
+/* Vector-Jacobian product of dim_from_primitive: primbar (DEVICE, 5 planes:
+ * alpha_2, p, T, u, v) = (dU/dprim)^T Ubar at the primitive state prim (DEVICE,
+ * 5 planes); Ubar DEVICE, 8 planes.  For chaining an initial-condition
+ * parametrisation to dim_grad.  Asynchronous.  Errors: DIM_EINVAL, DIM_ECUDA. */
+int dim_from_primitive_vjp(dim_ctx *c, const double *prim, const double *Ubar, double *primbar);
 
 /* The sweep of dim_hllc_sweep without a context and without any allocation.
  * The paper has no counterpart: this entry point exists for callers that

@@ -55,6 +55,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
+
 #define NQ 8
 #define ORC_PI 3.14159265358979323846
 #define ORC_SCHED 11
@@ -89,45 +91,50 @@ typedef struct {
 /* ------------------------------------------------------------------------- */
 /* Forward-mode dual numbers: (value, tangent), the rules of differentiation. */
 /* ------------------------------------------------------------------------- */
-struct Dual {
-    double v, d;
-    Dual() = default;
-    Dual(double x) : v(x), d(0.0) {}
-    Dual(double x, double t) : v(x), d(t) {}
+template <typename B>
+struct DualT {
+    B v, d;
+    DualT() = default;
+    DualT(B x) : v(x), d(0) {}
+    DualT(B x, B t) : v(x), d(t) {}
+    friend DualT operator+(DualT a, DualT b) { return DualT(a.v + b.v, a.d + b.d); }
+    friend DualT operator-(DualT a, DualT b) { return DualT(a.v - b.v, a.d - b.d); }
+    friend DualT operator-(DualT a) { return DualT(-a.v, -a.d); }
+    /* d(ab) = a db + b da */
+    friend DualT operator*(DualT a, DualT b) { return DualT(a.v * b.v, a.d * b.v + a.v * b.d); }
+    /* d(a/b) = (da - (a/b) db) / b */
+    friend DualT operator/(DualT a, DualT b)
+    {
+        B q = a.v / b.v;
+        return DualT(q, (a.d - q * b.d) / b.v);
+    }
+    friend DualT &operator+=(DualT &a, DualT b) { a = a + b; return a; }
+    friend DualT &operator-=(DualT &a, DualT b) { a = a - b; return a; }
+    friend bool operator<(DualT a, DualT b) { return a.v < b.v; }
+    friend bool operator>(DualT a, DualT b) { return a.v > b.v; }
+    friend bool operator<=(DualT a, DualT b) { return a.v <= b.v; }
+    friend bool operator>=(DualT a, DualT b) { return a.v >= b.v; }
+    /* d sqrt(a) = da / (2 sqrt(a)) */
+    friend DualT sqrt(DualT a)
+    {
+        B s = std::sqrt(a.v);
+        return DualT(s, a.d / (B(2) * s));
+    }
+    friend DualT fabs(DualT a) { return a.v < 0 ? -a : a; }
+    friend DualT fmin(DualT a, DualT b) { return b.v < a.v ? b : a; }
+    friend DualT fmax(DualT a, DualT b) { return b.v > a.v ? b : a; }
+    /* d a^e = e a^(e-1) da for a constant exponent */
+    friend DualT pow(DualT a, double e) { return DualT(std::pow(a.v, B(e)), B(e) * std::pow(a.v, B(e) - 1) * a.d); }
+    friend double val(DualT x) { return (double)x.v; }
+    friend bool is_nan(DualT x) { return std::isnan(x.v); }
 };
-static inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
-static inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
-static inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
-/* d(ab) = a db + b da */
-static inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
-/* d(a/b) = (da - (a/b) db) / b */
-static inline Dual operator/(Dual a, Dual b)
-{
-    double q = a.v / b.v;
-    return Dual(q, (a.d - q * b.d) / b.v);
-}
-static inline Dual &operator+=(Dual &a, Dual b) { a = a + b; return a; }
-static inline Dual &operator-=(Dual &a, Dual b) { a = a - b; return a; }
-static inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
-static inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
-static inline bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
-static inline bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
-/* d sqrt(a) = da / (2 sqrt(a)) */
-static inline Dual sqrt(Dual a)
-{
-    double s = sqrt(a.v);
-    return Dual(s, a.d / (2.0 * s));
-}
-static inline Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
-static inline Dual fmin(Dual a, Dual b) { return b.v < a.v ? b : a; }
-static inline Dual fmax(Dual a, Dual b) { return b.v > a.v ? b : a; }
-/* d a^e = e a^(e-1) da for a constant exponent */
-static inline Dual pow(Dual a, double e) { return Dual(pow(a.v, e), e * pow(a.v, e - 1.0) * a.d); }
+/* the tangent of the oracle: double values and tangents */
+typedef DualT<double> Dual;
+/* the same in extended precision (long double), a reference for the
+ * rounding error of the double tangent on badly conditioned states */
+typedef DualT<long double> DualL;
 static inline double val(double x) { return x; }
-static inline double val(Dual x) { return x.v; }
-static inline double tan_of(Dual x) { return x.d; }
 static inline bool is_nan(double x) { return isnan(x); }
-static inline bool is_nan(Dual x) { return isnan(x.v); }
 
 /* Branch record (test infrastructure for derivative checks): every value-decided
  * branch of the sweep -- the operand minmod returns, the Davis min / max, the
@@ -188,21 +195,31 @@ prm<double> make_prm<double>(const orc_params *P, const double *)
     return q;
 }
 
-template <>
-prm<Dual> make_prm<Dual>(const orc_params *P, const double *dp)
+template <typename B>
+static prm<DualT<B>> make_prm_dual(const orc_params *P, const double *dp)
 {
-    prm<Dual> q;
+    prm<DualT<B>> q;
     for (int k = 0; k < 2; k++) {
         q.gamma[k] = P->gamma[k]; q.pinf[k] = P->pinf[k]; q.cv[k] = P->cv[k];
-        q.k0[k] = Dual(P->k0[k], dp ? dp[k] : 0.0);
-        q.mu[k] = Dual(P->mu[k], dp ? dp[2 + k] : 0.0);
-        q.src[k] = Dual(P->src[k], dp ? dp[4 + k] : 0.0);
+        q.k0[k] = DualT<B>(P->k0[k], dp ? dp[k] : 0.0);
+        q.mu[k] = DualT<B>(P->mu[k], dp ? dp[2 + k] : 0.0);
+        q.src[k] = DualT<B>(P->src[k], dp ? dp[4 + k] : 0.0);
         q.bc[k] = P->bc[k];
     }
     q.k_exp = P->k_exp; q.T_ref = P->T_ref; q.cfl = P->cfl;
     q.limiter = P->limiter; q.trelax = P->trelax; q.n_outer = P->n_outer; q.p_policy = P->p_policy;
     q.p_fixed = P->p_fixed; q.p_min = P->p_min; q.p_max = P->p_max;
     return q;
+}
+template <>
+prm<Dual> make_prm<Dual>(const orc_params *P, const double *dp)
+{
+    return make_prm_dual<double>(P, dp);
+}
+template <>
+prm<DualL> make_prm<DualL>(const orc_params *P, const double *dp)
+{
+    return make_prm_dual<long double>(P, dp);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1201,20 +1218,51 @@ extern "C" unsigned orc_step_frozen(const orc_params *P, int nx, int ny, double 
  * advanced together; dparams (6 values or NULL) are the tangents of
  * (k0_1, k0_2, mu_1, mu_2, I_1, I_2).  dt and every lambda_max are frozen at
  * the values of the run (sched, when given, records them). */
-extern "C" unsigned orc_step_tangent(const orc_params *P, const double *dparams, int nx, int ny, double dx, double dy,
-                                     double *U, double *dU, int nsteps, double *sched)
+template <typename D>
+static unsigned tangent_run(const orc_params *P, const double *dparams, int nx, int ny, double dx, double dy,
+                            double *U, double *dU, int nsteps, double *sched, const unsigned char *tape,
+                            size_t tape_len)
 {
-    prm<Dual> Pd = make_prm<Dual>(P, dparams);
+    prm<D> Pd = make_prm<D>(P, dparams);
     size_t m = (size_t)NQ * nx * ny;
-    Dual *X = (Dual *)malloc(sizeof(Dual) * m);
-    for (size_t i = 0; i < m; i++) X[i] = Dual(U[i], dU[i]);
-    unsigned st = step_t(&Pd, nx, ny, dx, dy, X, nsteps, 0.0, NULL, NULL, sched, 0);
+    D *X = (D *)malloc(sizeof(D) * m);
+    for (size_t i = 0; i < m; i++) X[i] = D(U[i], dU[i]);
+    if (tape) {
+        g_tape.mode = 2;
+        g_tape.buf = (unsigned char *)tape;
+        g_tape.cap = tape_len;
+        g_tape.pos = 0;
+        g_tape.overflow = 0;
+    }
+    unsigned st = step_t(&Pd, nx, ny, dx, dy, X, nsteps, 0.0, NULL, NULL, sched, sched && tape ? 1 : 0);
+    if (tape) {
+        if (g_tape.overflow || g_tape.pos != tape_len) st |= ORC_EINVAL;
+        g_tape.mode = 0;
+        g_tape.buf = NULL;
+    }
     for (size_t i = 0; i < m; i++) {
-        U[i] = X[i].v;
-        dU[i] = tan_of(X[i]);
+        U[i] = (double)X[i].v;
+        dU[i] = (double)X[i].d;
     }
     free(X);
     return st;
+}
+
+extern "C" unsigned orc_step_tangent(const orc_params *P, const double *dparams, int nx, int ny, double dx, double dy,
+                                     double *U, double *dU, int nsteps, double *sched)
+{
+    return tangent_run<Dual>(P, dparams, nx, ny, dx, dy, U, dU, nsteps, sched, NULL, 0);
+}
+
+/* The same tangent with every value and tangent carried in long double, a
+ * reference for the rounding error of the double tangent.  sched and tape:
+ * the schedule and branch record of the double run (orc_step_frozen), replayed
+ * so that the extended run linearizes the same branch-frozen map. */
+extern "C" unsigned orc_step_tangent_ext(const orc_params *P, const double *dparams, int nx, int ny, double dx,
+                                         double dy, double *U, double *dU, int nsteps, double *sched,
+                                         const unsigned char *tape, size_t tape_len)
+{
+    return tangent_run<DualL>(P, dparams, nx, ny, dx, dy, U, dU, nsteps, sched, tape, tape_len);
 }
 
 /* diagnostics used by the tests: per-cell phase pressures and temperatures */

@@ -86,6 +86,8 @@ def lib():
         L.orc_step_frozen.argtypes = [P, i, i, d, d, _D, i, _D, C.c_void_p, C.c_size_t, i, C.POINTER(C.c_size_t)]
         L.orc_step_frozen.restype = u
         L.orc_step_tangent.argtypes = [P, _D, i, i, d, d, _D, _D, i, _D]; L.orc_step_tangent.restype = u
+        L.orc_step_tangent_ext.argtypes = [P, _D, i, i, d, d, _D, _D, i, _D, C.c_void_p, C.c_size_t]
+        L.orc_step_tangent_ext.restype = u
         L.orc_cheb_P.argtypes = [P, d, d]; L.orc_cheb_P.restype = i
         L.orc_cheb_schedule.argtypes = [i, d, _D]; L.orc_cheb_schedule.restype = None
         L.orc_lim_solve.argtypes = [P, i, i, d, d, d, _D, _D, _D, _D, _D]; L.orc_lim_solve.restype = i
@@ -221,6 +223,24 @@ def step_tangent(params, U, dU, dx, dy, nsteps, dparams=None):
     st = lib().orc_step_tangent(C.byref(_params(params)), None if dp is None else _ptr(dp), U.shape[2], U.shape[1],
                                 dx, dy, _ptr(U), _ptr(dU), nsteps, _ptr(sched))
     return U, dU, st, sched
+
+
+def step_tangent_ext(params, U, dU, dx, dy, nsteps, frozen, dparams=None):
+    """The tangent in long double following the double run's schedule and
+    branches (frozen = (sched, tape) from step_frozen): a reference for the
+    rounding error of the double tangent.  Returns (U_T, dU_T, status)."""
+    U = _state(U).copy()
+    dU = _state(dU).copy()
+    sched, tape = frozen
+    sched = np.ascontiguousarray(sched, dtype=np.float64).copy()
+    tape = np.ascontiguousarray(tape, dtype=np.uint8)
+    dp = None if dparams is None else np.ascontiguousarray(dparams, dtype=np.float64)
+    st = lib().orc_step_tangent_ext(C.byref(_params(params)), None if dp is None else _ptr(dp), U.shape[2],
+                                    U.shape[1], dx, dy, _ptr(U), _ptr(dU), nsteps, _ptr(sched), tape.ctypes.data,
+                                    tape.size)
+    if st & 64:
+        raise ValueError("branch record does not match the extended run")
+    return U, dU, st
 
 
 def cheb_P(params, tau, lam_max) -> int:

@@ -20,13 +20,15 @@ ST_NONPHYS, ST_NAN, ST_NOROOT, ST_TRANSIENT, ST_PCAP, ST_TIMEOUT = 1, 2, 4, 8, 1
 RELAX_PRESSURE, RELAX_TEMPERATURE = 0, 1
 PRECISION_FP64, PRECISION_FP32_BULK = 0, 1
 PARABOLIC_HEAT, PARABOLIC_VISCOUS_X, PARABOLIC_VISCOUS_Y = 0, 1, 2
+SCHED = 11          # doubles per step of a schedule record (DIM_SCHED)
+GRAD_NPARAMS = 6    # k0_1, k0_2, mu_1, mu_2, I_1, I_2 (DIM_GRAD_NPARAMS)
 
 # every entry point the header declares
 SYMBOLS = ["dim_init", "dim_destroy", "dim_from_primitive", "dim_cfl_dt", "dim_step", "dim_step_host",
            "dim_hllc_sweep", "dim_relax", "dim_cheb_parabolic", "dim_grad", "dim_status", "dim_profile",
            "dim_kernel_time", "dim_strerror", "dim_hllc_sweep_noalloc", "dim_batch_init", "dim_batch_destroy",
            "dim_batch_layout", "dim_batch_from_primitive", "dim_batch_step", "dim_batch_autotune",
-           "dim_batch_status"]
+           "dim_batch_status", "dim_step_sched", "dim_from_primitive_vjp"]
 
 
 class DimParams(C.Structure):
@@ -87,7 +89,9 @@ def load(path: str = LIB_PATH):
     L.dim_hllc_sweep.argtypes = [vp, vp, i, d, i]
     L.dim_relax.argtypes = [vp, vp, i]
     L.dim_cheb_parabolic.argtypes = [vp, vp, i, d, C.POINTER(i)]
-    L.dim_grad.argtypes = [vp, vp, i, i, vp, vp, vp]
+    L.dim_grad.argtypes = [vp, vp, i, i, vp, vp, pd]
+    L.dim_step_sched.argtypes = [vp, vp, i, vp, i]
+    L.dim_from_primitive_vjp.argtypes = [vp, vp, vp, vp]
     L.dim_status.argtypes = [vp, C.POINTER(u), i]
     L.dim_profile.argtypes = [vp, i, i]
     L.dim_kernel_time.argtypes = [vp, C.c_char_p, C.POINTER(i), pd]

@@ -7,11 +7,17 @@ or without libdim.so the calls raise.
     s = Solver(params, nx, ny, dx, dy)
     U = s.from_primitive(prim)          # prim: (5, ny, nx) float64 alpha_2, p, T, u, v
     dt = s.step(U, nsteps=10)           # U: (8, ny, nx) float64 on the device, in place
+
+Gradients (FP64): ``Solver.grad`` is the adjoint of nsteps steps (dim_grad);
+``steps`` and ``from_primitive`` are the same maps as torch.autograd functions,
+differentiable with respect to the state, the primitive fields and the
+parameter vector (k0_1, k0_2, mu_1, mu_2, I_1, I_2).
 """
 from __future__ import annotations
 
 import ctypes as C
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -102,6 +108,35 @@ class Solver:
         check(self.L.dim_status(self._ctx, C.byref(f), int(reset)), "dim_status")
         return f.value
 
+    def step_sched(self, U: torch.Tensor, nsteps: int, sched: torch.Tensor | None = None) -> torch.Tensor:
+        """nsteps steps (FP64) in place.  sched None: the schedule (CFL maximum S
+        and every LIM lambda_max, per step) is recorded and returned as a
+        (nsteps, 11) device tensor; a given sched is replayed (the map with time
+        steps and Chebyshev parameters held fixed)."""
+        replay = sched is not None
+        if sched is None:
+            sched = torch.zeros((nsteps, _lib.SCHED), dtype=torch.float64, device=U.device)
+        check(self.L.dim_step_sched(self._ctx, _dev_ptr(U, self.state_shape), nsteps,
+                                    _dev_ptr(sched, (nsteps, _lib.SCHED)), int(replay)), "dim_step_sched")
+        return sched
+
+    def grad(self, U0: torch.Tensor, nsteps: int, dJ_dUT: torch.Tensor, ckpt_every: int = 20):
+        """Adjoint of nsteps steps from U0 (dim_grad): returns (dJ/dU0 device
+        tensor, dJ/d(k0_1, k0_2, mu_1, mu_2, I_1, I_2) numpy array)."""
+        out = torch.empty_like(U0)
+        gp = (C.c_double * _lib.GRAD_NPARAMS)()
+        check(self.L.dim_grad(self._ctx, _dev_ptr(U0, self.state_shape), nsteps, ckpt_every,
+                              _dev_ptr(dJ_dUT, self.state_shape), _dev_ptr(out, self.state_shape), gp), "dim_grad")
+        return out, np.array(list(gp))
+
+    def from_primitive_vjp(self, prim: torch.Tensor, Ubar: torch.Tensor) -> torch.Tensor:
+        """(dU/dprim)^T Ubar of from_primitive at prim (dim_from_primitive_vjp)."""
+        out = torch.empty_like(prim)
+        check(self.L.dim_from_primitive_vjp(self._ctx, _dev_ptr(prim, (5, self.ny, self.nx)),
+                                            _dev_ptr(Ubar, self.state_shape), _dev_ptr(out, (5, self.ny, self.nx))),
+              "dim_from_primitive_vjp")
+        return out
+
     def profile(self, enable: bool = True, reset: bool = True):
         check(self.L.dim_profile(self._ctx, int(enable), int(reset)), "dim_profile")
 
@@ -110,6 +145,63 @@ class Solver:
         ms = C.c_double(0.0)
         check(self.L.dim_kernel_time(self._ctx, name.encode(), C.byref(n), C.byref(ms)), "dim_kernel_time")
         return n.value, ms.value
+
+
+def param_vector(params) -> torch.Tensor:
+    """(k0_1, k0_2, mu_1, mu_2, I_1, I_2) of a parameter set, float64 on the CPU."""
+    return torch.tensor([params.k0[0], params.k0[1], params.mu[0], params.mu[1], params.src[0], params.src[1]],
+                        dtype=torch.float64)
+
+
+class _Steps(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U0, pvec, solver, nsteps, ckpt_every):
+        ref = param_vector(solver.params)
+        if not torch.equal(pvec.detach().cpu().to(torch.float64), ref):
+            raise ValueError("pvec must hold the solver's (k0_1, k0_2, mu_1, mu_2, I_1, I_2)")
+        UT = U0.detach().clone()
+        solver.step(UT, nsteps)
+        ctx.solver, ctx.nsteps, ctx.ckpt = solver, nsteps, ckpt_every
+        ctx.pdev, ctx.pdtype = pvec.device, pvec.dtype
+        ctx.save_for_backward(U0.detach())
+        return UT
+
+    @staticmethod
+    def backward(ctx, gUT):
+        (U0,) = ctx.saved_tensors
+        gU0, gp = ctx.solver.grad(U0, ctx.nsteps, gUT.contiguous(), ctx.ckpt)
+        return gU0, torch.tensor(gp, dtype=ctx.pdtype, device=ctx.pdev), None, None, None
+
+
+class _FromPrimitive(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, prim, solver):
+        p = prim.detach().contiguous()
+        ctx.solver = solver
+        ctx.save_for_backward(p)
+        return solver.from_primitive(p)
+
+    @staticmethod
+    def backward(ctx, gU):
+        (p,) = ctx.saved_tensors
+        return ctx.solver.from_primitive_vjp(p, gU.contiguous()), None
+
+
+def steps(U0: torch.Tensor, solver: "Solver", nsteps: int, ckpt_every: int = 20, pvec: torch.Tensor | None = None):
+    """U_T = nsteps split steps of U0 (FP64), as a torch.autograd function.
+    Backward calls dim_grad (adjoint with the run's schedule and branches held
+    fixed, checkpoints every ckpt_every steps) and returns the gradients with
+    respect to U0 and pvec = (k0_1, k0_2, mu_1, mu_2, I_1, I_2), which must be
+    the solver's own values (param_vector(solver.params))."""
+    if pvec is None:
+        pvec = param_vector(solver.params)
+    return _Steps.apply(U0, pvec, solver, nsteps, ckpt_every)
+
+
+def from_primitive(prim: torch.Tensor, solver: "Solver") -> torch.Tensor:
+    """dim_from_primitive as a torch.autograd function (backward:
+    dim_from_primitive_vjp)."""
+    return _FromPrimitive.apply(prim, solver)
 
 
 class Batch:

@@ -1,6 +1,6 @@
 """Build the CUDA library libdim.so for sm_103a (in-tree, no cmake).
 
-The three translation units compile in parallel with nvcc and link into one
+The translation units compile in parallel with nvcc and link into one
 shared library next to this file.  Used by ``__graft_entry__.build()`` and by
 the tests; nothing here runs on the GPU.
 """
@@ -14,10 +14,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdim.so")
-SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulk32.cu", "dim_batch.cu"]
+SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulk32.cu", "dim_batch.cu",
+           "dim_adjoint.cu", "dim_grad.cu"]
 # the FP32-bulk kernels may contract multiply-adds (no bit-compatibility claim)
 FMA_SOURCES = {"dim_bulk32.cu", "dim_batch.cu"}
-HEADERS = ["dim_device.cuh", "dim_bulk32.cuh"]
+HEADERS = ["dim_device.cuh", "dim_bulk32.cuh", "dim_ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

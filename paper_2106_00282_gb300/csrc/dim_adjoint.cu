@@ -1,0 +1,1182 @@
+// dim_adjoint.cu -- adjoint (reverse-mode) kernels of the split step (sm_103a).
+//
+// Each stage of the step (Sec. 3) is differentiated with its schedule (dt,
+// Chebyshev lambda_max, hence P and b_m) and its value-decided branches
+// (limiter operand, Davis bounds, HLLC wave region) held fixed:
+//
+//  * pointwise stages (pressure relaxation Sec. 3.3, temperature relaxation
+//    Sec. 3.4.1, the equilibrium projection and the conduction coefficients
+//    of Sec. 3.4.2): the local Jacobian of the cell map is formed by
+//    forward-mode dual numbers over the cell's inputs and its transpose is
+//    applied to the cell's adjoint;
+//  * the hyperbolic sweep (Sec. 3.1, 3.6): the update of cell i is
+//    U_i - dt/h (F_{i+1/2} - F_{i-1/2}) - dt/h R(U_i)(u*_{i+1/2} - u*_{i-1/2});
+//    the adjoint of face f's outputs (F, u*) is dt/h times the difference of
+//    its two cells' adjoints (and of R.adjoint for u*), and every cell gathers
+//    the transposed Jacobian of each face whose four-cell stencil contains it,
+//    evaluated with that cell's eight inputs seeded;
+//  * the LIM solves (Sec. 3.2, Eqs. LIM, LIM_last): the sweeps
+//    v^m = (v^0 + tau b_m v^{m-1} + tau V (L v^{m-1} + f)) / (1 + tau b_m) are
+//    linear in v for frozen coefficients and L_h is symmetric, so the reverse
+//    sweep is  y = vbar^m/(1 + tau b_m),  vbar^{m-1} = tau b_m y + tau L(V y),
+//    accumulating the adjoints of v^0, V, the face coefficients and f; the
+//    coefficients' own dependence on the state (V, Lam of Sec. 3.4.2, 1/rho
+//    and mu of Sec. 3.2) is then transposed pointwise.
+// The primal values the kernels need (stage inputs, every LIM iterate) are
+// recomputed by the forward kernels and passed in.  Parameter gradients
+// (k0_k, mu_k, I_k) are block sums added to 6 device doubles.
+#include "dim_device.cuh"
+
+namespace dimk {
+namespace {
+
+// ---------------------------------------------------------------------------
+// forward-mode dual numbers: a value and N tangent components
+// ---------------------------------------------------------------------------
+template <int N>
+struct Dn {
+    double v;
+    double d[N];
+};
+
+template <int N>
+__device__ __forceinline__ Dn<N> dcst(double v)
+{
+    Dn<N> r;
+    r.v = v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = 0.0;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> dseed(double v, int k)
+{
+    Dn<N> r = dcst<N>(v);
+    r.d[k] = 1.0;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator+(const Dn<N> &a, const Dn<N> &b)
+{
+    Dn<N> r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] + b.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator+(const Dn<N> &a, double b)
+{
+    Dn<N> r = a;
+    r.v = a.v + b;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator+(double a, const Dn<N> &b)
+{
+    Dn<N> r = b;
+    r.v = a + b.v;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(const Dn<N> &a, const Dn<N> &b)
+{
+    Dn<N> r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] - b.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(const Dn<N> &a, double b)
+{
+    Dn<N> r = a;
+    r.v = a.v - b;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(double a, const Dn<N> &b)
+{
+    Dn<N> r;
+    r.v = a - b.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = -b.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(const Dn<N> &a)
+{
+    Dn<N> r;
+    r.v = -a.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = -a.d[i];
+    return r;
+}
+// d(ab) = b da + a db
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(const Dn<N> &a, const Dn<N> &b)
+{
+    Dn<N> r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(const Dn<N> &a, double b)
+{
+    Dn<N> r;
+    r.v = a.v * b;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] * b;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(double a, const Dn<N> &b)
+{
+    Dn<N> r;
+    r.v = a * b.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = a * b.d[i];
+    return r;
+}
+// d(a/b) = (da - (a/b) db) / b
+template <int N>
+__device__ __forceinline__ Dn<N> operator/(const Dn<N> &a, const Dn<N> &b)
+{
+    Dn<N> r;
+    r.v = a.v / b.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator/(const Dn<N> &a, double b)
+{
+    Dn<N> r;
+    r.v = a.v / b;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] / b;
+    return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator/(double a, const Dn<N> &b)
+{
+    Dn<N> r;
+    r.v = a / b.v;
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = (-r.v * b.d[i]) / b.v;
+    return r;
+}
+// d sqrt(a) = da / (2 sqrt(a))
+template <int N>
+__device__ __forceinline__ Dn<N> dsqrt(const Dn<N> &a)
+{
+    Dn<N> r;
+    r.v = sqrt(a.v);
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] / (2.0 * r.v);
+    return r;
+}
+// x^e for the conductivity law, derivative e x^(e-1) (k_pow: 0 constant, >0
+// integer power by repeated products, <0 general exponent)
+template <int N>
+__device__ __forceinline__ Dn<N> dpow_law(const DevParams &p, const Dn<N> &t)
+{
+    if (p.k_pow > 0) {
+        Dn<N> r = t;
+        for (int i = 1; i < p.k_pow; i++) r = r * t;
+        return r;
+    }
+    Dn<N> r;
+    r.v = pow(t.v, p.k_exp);
+    double dr = p.k_exp * pow(t.v, p.k_exp - 1.0);
+#pragma unroll
+    for (int i = 0; i < N; i++) r.d[i] = dr * t.d[i];
+    return r;
+}
+// value of (T/T_ref)^k_exp as the forward law evaluates it
+__device__ __forceinline__ double law_ratio(const DevParams &p, double T)
+{
+    if (p.k_pow == 0) return 1.0;
+    double t = T * p.inv_Tref;
+    if (p.k_pow > 0) {
+        double r = t;
+        for (int i = 1; i < p.k_pow; i++) r = r * t;
+        return r;
+    }
+    return pow(t, p.k_exp);
+}
+
+// ---------------------------------------------------------------------------
+// the stage formulas in dual arithmetic (same operation order as the forward)
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ Dn<N> d_sgp(const DevParams &p, int k, const Dn<N> &Ek, const Dn<N> &ak)
+{
+    return p.gm1[k] * Ek / ak - p.gpinf[k];
+}
+template <int N>
+__device__ __forceinline__ Dn<N> d_sgE(const DevParams &p, int k, const Dn<N> &pr, const Dn<N> &ak)
+{
+    return ak * (pr + p.gpinf[k]) * p.inv_gm1[k];
+}
+template <int N>
+__device__ __forceinline__ Dn<N> d_sgA(const DevParams &p, int k, const Dn<N> &pr)
+{
+    return p.g[k] * (pr + p.pinf[k]);
+}
+
+// mixture sound speed c = sqrt((a1 A1 + a2 A2) / rho) (Sec. 3.1, Eq. AK)
+template <int N>
+__device__ __forceinline__ Dn<N> d_mixc(const DevParams &p, const Dn<N> &a1, const Dn<N> &p1, const Dn<N> &a2,
+                                       const Dn<N> &p2, const Dn<N> &rho)
+{
+    return dsqrt((a1 * d_sgA(p, 0, p1) + a2 * d_sgA(p, 1, p2)) / rho);
+}
+
+// minmod with the operand choice of the forward: the smaller magnitude when
+// both are nonzero with one sign (the second on a tie), else 0
+template <int N>
+__device__ __forceinline__ Dn<N> d_minmod(const Dn<N> &a, const Dn<N> &b)
+{
+    if (a.v > 0.0 && b.v > 0.0) return a.v < b.v ? a : b;
+    if (a.v < 0.0 && b.v < 0.0) return a.v > b.v ? a : b;
+    return dcst<N>(0.0);
+}
+
+// line-local conserved (m1, m2, rho u_n, rho u_t, E1, E2, rho E, alpha_2) ->
+// primitive (alpha_2, m1, m2, u_n, u_t, p1, p2)
+template <int N>
+__device__ __forceinline__ void d_prims(const DevParams &p, const Dn<N> *q, Dn<N> *w)
+{
+    Dn<N> a2 = q[7], a1 = 1.0 - a2;
+    Dn<N> rho = q[0] + q[1];
+    w[0] = a2;
+    w[1] = q[0];
+    w[2] = q[1];
+    w[3] = q[2] / rho;
+    w[4] = q[3] / rho;
+    w[5] = d_sgp(p, 0, q[4], a1);
+    w[6] = d_sgp(p, 1, q[5], a2);
+}
+
+template <int N>
+struct DFace {
+    Dn<N> a2, un, ut, rho, p, c;
+    Dn<N> q[NQ];
+};
+
+template <int N>
+__device__ __forceinline__ void d_face_state(const DevParams &p, const Dn<N> *w, DFace<N> &s)
+{
+    Dn<N> a2 = w[0], a1 = 1.0 - a2;
+    Dn<N> m1 = w[1], m2 = w[2], un = w[3], ut = w[4], p1 = w[5], p2 = w[6];
+    Dn<N> rho = m1 + m2;
+    Dn<N> E1 = d_sgE(p, 0, p1, a1), E2 = d_sgE(p, 1, p2, a2);
+    s.a2 = a2;
+    s.un = un;
+    s.ut = ut;
+    s.rho = rho;
+    s.p = a1 * p1 + a2 * p2;
+    s.c = d_mixc(p, a1, p1, a2, p2, rho);
+    s.q[0] = m1;
+    s.q[1] = m2;
+    s.q[2] = rho * un;
+    s.q[3] = rho * ut;
+    s.q[4] = E1;
+    s.q[5] = E2;
+    s.q[6] = E1 + E2 + 0.5 * rho * (un * un + ut * ut);
+    s.q[7] = a2;
+}
+
+// HLLC face flux F[0..7] and u* = F[8] with the forward's branch rules
+template <int N>
+__device__ __forceinline__ void d_hllc(const DFace<N> &L, const DFace<N> &R, Dn<N> *F)
+{
+    Dn<N> sl1 = L.un - L.c, sl2 = R.un - R.c, sr1 = L.un + L.c, sr2 = R.un + R.c;
+    Dn<N> SL = sl2.v < sl1.v ? sl2 : sl1;
+    Dn<N> SR = sr2.v > sr1.v ? sr2 : sr1;
+    Dn<N> Ss = (R.p - L.p + L.rho * L.un * (SL - L.un) - R.rho * R.un * (SR - R.un)) /
+               (L.rho * (SL - L.un) - R.rho * (SR - R.un));
+    Dn<N> q[NQ], us, ps;
+    if (0.0 <= SL.v) {
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = L.q[k];
+        us = L.un;
+        ps = L.p;
+    } else if (0.0 <= SR.v) {
+        const bool starL = 0.0 <= Ss.v;
+        const DFace<N> &K = starL ? L : R;
+        Dn<N> SK = starL ? SL : SR;
+        Dn<N> chi = (SK - K.un) / (SK - Ss);
+        q[0] = chi * K.q[0];
+        q[1] = chi * K.q[1];
+        q[2] = chi * K.rho * Ss;
+        q[3] = chi * K.rho * K.ut;
+        q[4] = chi * K.q[4];
+        q[5] = chi * K.q[5];
+        q[6] = chi * (K.q[6] + (Ss - K.un) * (K.rho * Ss + K.p / (SK - K.un)));
+        q[7] = K.a2;
+        us = Ss;
+        ps = K.p + K.rho * (SK - K.un) * (Ss - K.un);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = R.q[k];
+        us = R.un;
+        ps = R.p;
+    }
+    F[0] = us * q[0];
+    F[1] = us * q[1];
+    F[2] = us * q[2] + ps;
+    F[3] = us * q[3];
+    F[4] = us * q[4];
+    F[5] = us * q[5];
+    F[6] = us * (q[6] + ps);
+    F[7] = us * q[7];
+    F[8] = us;
+}
+
+// pressure relaxation (Sec. 3.3) of one cell, global plane order, in place
+template <int N>
+__device__ __forceinline__ void d_prelax(const DevParams &p, Dn<N> *q)
+{
+    const double g1 = p.g[0], g2 = p.g[1];
+    Dn<N> a2 = q[7], a1 = 1.0 - a2;
+    Dn<N> ak1 = p.gm1[0] * q[4], bk1 = p.gm1[0] * a1;
+    Dn<N> ak2 = p.gm1[1] * q[5], bk2 = p.gm1[1] * a2;
+    const double ek1 = p.gpinf[0], ek2 = p.gpinf[1];
+    Dn<N> A = g1 * g2 - bk1 * g2 - bk2 * g1;
+    Dn<N> B = g1 * ek2 + ek1 * g2 - (ak1 * g2 + bk1 * ek2 + ak2 * g1 + bk2 * ek1);
+    Dn<N> C = ek1 * ek2 - ak1 * ek2 - ak2 * ek1;
+    Dn<N> disc = B * B - 4.0 * A * C;
+    if (disc.v < 0.0) disc = dcst<N>(0.0);
+    Dn<N> sq = dsqrt(disc);
+    Dn<N> pr = B.v <= 0.0 ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
+    Dn<N> a2n = (ak2 + bk2 * pr) / (g2 * pr + ek2);
+    Dn<N> a1n = 1.0 - a2n;
+    Dn<N> rho = q[0] + q[1];
+    Dn<N> rhoe = q[6] - 0.5 * (q[2] * q[2] + q[3] * q[3]) / rho;
+    Dn<N> p2 = (rhoe - (a1n * p.g[0] * p.pinf[0] * p.inv_gm1[0] + a2n * p.g[1] * p.pinf[1] * p.inv_gm1[1])) /
+               (a1n * p.inv_gm1[0] + a2n * p.inv_gm1[1]);
+    q[4] = d_sgE(p, 0, p2, a1n);
+    q[5] = d_sgE(p, 1, p2, a2n);
+    q[7] = a2n;
+}
+
+// p,T equilibrium at fixed (m1, m2, rho e) (Sec. 3.4.1 / 3.4.2)
+template <int N>
+__device__ __forceinline__ void d_equilibrium(const DevParams &p, const Dn<N> &m1, const Dn<N> &m2, const Dn<N> &rhoe,
+                                              Dn<N> &T, Dn<N> &a)
+{
+    Dn<N> C1 = m1 * p.cv[0], C2 = m2 * p.cv[1], C = C1 + C2;
+    Dn<N> G1C1 = p.gm1[0] * C1, G2C2 = p.gm1[1] * C2, G = G1C1 + G2C2;
+    const double B1 = p.pinf[0] - p.pinf[1];
+    Dn<N> E = rhoe - p.pinf[0];
+    Dn<N> qa = B1 * (G + C);
+    Dn<N> qb = E * G - B1 * G2C2 - C * B1;
+    Dn<N> qc = -E * G2C2;
+    Dn<N> disc = qb * qb - 4.0 * qa * qc;
+    if (disc.v < 0.0) disc = dcst<N>(0.0);
+    Dn<N> sq = dsqrt(disc);
+    a = qb.v > 0.0 ? (-2.0 * qc) / (qb + sq) : (sq - qb) / (2.0 * qa);
+    T = (E + B1 * a) / C;
+}
+
+// conduction coefficients V = 1/(C + B1^2/K), Lam = sum_k a_k lambda_k(T)
+// (Sec. 3.4.2) and the source a1 I1 + a2 I2 (Eq. I) at (m1, m2, T, a2)
+template <int N>
+__device__ __forceinline__ void d_heat_coeffs(const DevParams &p, const Dn<N> &m1, const Dn<N> &m2, const Dn<N> &T,
+                                              const Dn<N> &a2, Dn<N> &V, Dn<N> &Lam, Dn<N> &Ia)
+{
+    Dn<N> a1 = 1.0 - a2;
+    Dn<N> C1 = m1 * p.cv[0], C2 = m2 * p.cv[1];
+    const double B1 = p.pinf[0] - p.pinf[1];
+    Dn<N> r1 = p.gm1[0] * C1 * T / (a1 * a1);
+    Dn<N> r2 = p.gm1[1] * C2 * T / (a2 * a2);
+    Dn<N> K = T * (r1 + r2);
+    V = 1.0 / (C1 + C2 + B1 * B1 / K);
+    if (p.k_pow == 0) {
+        Lam = a1 * p.k0[0] + a2 * p.k0[1];
+    } else {
+        Dn<N> r = dpow_law(p, T * p.inv_Tref);
+        Lam = a1 * (p.k0[0] * r) + a2 * (p.k0[1] * r);
+    }
+    Ia = a1 * p.src[0] + a2 * p.src[1];
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int line_map(int a, int len, int bc)
+{
+    if (a >= 0 && a < len) return a;
+    if (bc == DIM_BC_PERIODIC) return ((a % len) + len) % len;
+    return a < 0 ? 0 : len - 1;
+}
+
+// neighbours along one axis: -1 at a transmissive wall (zero flux), wrapped
+// when periodic, -1 when the axis has a single cell
+__device__ __forceinline__ void axis_nb(const DevParams &p, int axis, int c, int &cm, int &cp)
+{
+    const int x = c % p.nx, y = c / p.nx;
+    const int len = axis == 0 ? p.nx : p.ny, i = axis == 0 ? x : y;
+    const int stride = axis == 0 ? 1 : p.nx;
+    cm = cp = -1;
+    if (len < 2) return;
+    if (i > 0) cm = c - stride;
+    else if (p.bc[axis] == DIM_BC_PERIODIC) cm = c + (len - 1) * stride;
+    if (i < len - 1) cp = c + stride;
+    else if (p.bc[axis] == DIM_BC_PERIODIC) cp = c - (len - 1) * stride;
+}
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ void add_param(double *pbar, int k, double v)
+{
+    double s = block_sum(v);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(pbar + k, s);
+}
+
+#define GRID_LOOP(c, n) for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (n); c += gridDim.x * blockDim.x)
+
+
+// ---------------------------------------------------------------------------
+// pointwise stages: Gin = J^T G in place (G: 8 planes)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_prelax(const DevParams p, const double *Uin, double *G)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        Dn<8> q[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = dseed<8>(Uin[k * n + c], k);
+        d_prelax(p, q);
+        double g[NQ], r[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) g[k] = G[k * n + c];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) {
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < NQ; j++) s += g[j] * q[j].d[k];
+            r[k] = s;
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; k++) G[k * n + c] = r[k];
+    }
+}
+
+// temperature relaxation (Sec. 3.4.1): (T, a) = equilibrium(m1, m2, E1 + E2),
+// E_k = m_k Cv_k T + a_k pinf_k
+__global__ void __launch_bounds__(256) k_adj_trelax(const DevParams p, const double *Uin, double *G)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        // inputs m1, m2, E1, E2
+        Dn<4> m1 = dseed<4>(Uin[c], 0), m2 = dseed<4>(Uin[n + c], 1);
+        Dn<4> E1 = dseed<4>(Uin[4 * n + c], 2), E2 = dseed<4>(Uin[5 * n + c], 3);
+        Dn<4> T, a;
+        d_equilibrium(p, m1, m2, E1 + E2, T, a);
+        Dn<4> o4 = m1 * p.cv[0] * T + (1.0 - a) * p.pinf[0];
+        Dn<4> o5 = m2 * p.cv[1] * T + a * p.pinf[1];
+        const double g4 = G[4 * n + c], g5 = G[5 * n + c], g7 = G[7 * n + c];
+        double r[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) r[k] = g4 * o4.d[k] + g5 * o5.d[k] + g7 * a.d[k];
+        G[c] += r[0];
+        G[n + c] += r[1];
+        G[4 * n + c] = r[2];
+        G[5 * n + c] = r[3];
+        G[7 * n + c] = 0.0;  // alpha_2 is replaced by the equilibrium value
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hyperbolic sweep: per-cell gather of the transposed face Jacobians
+// ---------------------------------------------------------------------------
+// the face between line positions f-1 and f, stencil positions f-2 .. f+1;
+// inputs of stencil positions with seed[k] carry the identity tangent
+template <int AXIS>
+__device__ __forceinline__ void face_eval(const DevParams &p, const double *U, const int *cells, const bool *seed,
+                                          Dn<8> *F)
+{
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    const int n = p.n;
+    const int gmap[NQ] = {0, 1, QN, QT, 4, 5, 6, 7};
+    Dn<8> W[4][7];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        Dn<8> q[NQ];
+#pragma unroll
+        for (int j = 0; j < NQ; j++) {
+            double v = U[gmap[j] * n + cells[k]];
+            q[j] = seed[k] ? dseed<8>(v, j) : dcst<8>(v);
+        }
+        d_prims(p, q, W[k]);
+    }
+    Dn<8> wl[7], wr[7];
+    if (p.limiter != DIM_LIMITER_NONE) {
+        const bool ob = p.limiter == DIM_LIMITER_OVERBEE;
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            Dn<8> sl = d_minmod(W[1][j] - W[0][j], W[2][j] - W[1][j]);
+            Dn<8> sr = d_minmod(W[2][j] - W[1][j], W[3][j] - W[2][j]);
+            if (ob && j <= 2) {
+                sl = 2.0 * sl;
+                sr = 2.0 * sr;
+            }
+            wl[j] = W[1][j] + 0.5 * sl;
+            wr[j] = W[2][j] - 0.5 * sr;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            wl[j] = W[1][j];
+            wr[j] = W[2][j];
+        }
+    }
+    DFace<8> L, R;
+    d_face_state(p, wl, L);
+    d_face_state(p, wr, R);
+    d_hllc(L, R, F);
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(128) k_adj_sweep(const DevParams p, const double *Uin, const double *Gout,
+                                                   double *Gin, double dtdx)
+{
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    const int gmap[NQ] = {0, 1, QN, QT, 4, 5, 6, 7};
+    const int n = p.n;
+    const int len = AXIS == 0 ? p.nx : p.ny;
+    const int bc = p.bc[AXIS];
+    GRID_LOOP(c, n)
+    {
+        const int x = c % p.nx, y = c / p.nx;
+        const int i = AXIS == 0 ? x : y;
+        auto cell_of = [&](int pos) { return AXIS == 0 ? y * p.nx + pos : pos * p.nx + x; };
+        // adjoint and R.adjoint of line position pos (0 outside the line: ghosts are not updated)
+        auto lam_r = [&](int pos, double *lam) -> double {
+            if (pos < 0 || pos >= len) {
+#pragma unroll
+                for (int k = 0; k < NQ; k++) lam[k] = 0.0;
+                return 0.0;
+            }
+            const int cc = cell_of(pos);
+#pragma unroll
+            for (int k = 0; k < NQ; k++) lam[k] = Gout[gmap[k] * n + cc];
+            const double a2 = Uin[7 * n + cc], a1 = 1.0 - a2;
+            const double p1 = sg_p(p, 0, Uin[4 * n + cc], a1), p2 = sg_p(p, 1, Uin[5 * n + cc], a2);
+            return lam[4] * (a1 * p1) + lam[5] * (a2 * p2) - lam[7] * a2;
+        };
+        double li[NQ];
+        lam_r(i, li);
+        double acc[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) acc[k] = li[k];
+        double us_m = 0.0, us_p = 0.0;
+        // faces whose stencil may contain line position i (windows shifted by
+        // the period for a periodic axis; every face of a short line)
+        const int nwin = len <= 8 ? 1 : (bc == DIM_BC_PERIODIC ? 3 : 1);
+        for (int w = 0; w < nwin; w++) {
+            int f0, f1;
+            if (len <= 8) { f0 = 0; f1 = len; }
+            else {
+                const int sh = w == 0 ? 0 : (w == 1 ? len : -len);
+                f0 = max(i - 1 + sh, 0);
+                f1 = min(i + 2 + sh, len);
+            }
+            for (int f = f0; f <= f1; f++) {
+                int cells[4];
+                bool seed[4], any = false;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int src = line_map(f - 2 + k, len, bc);
+                    cells[k] = cell_of(src);
+                    seed[k] = src == i;
+                    any = any || seed[k];
+                }
+                if (!any) continue;
+                double lamL[NQ], lamR[NQ];
+                const double rL = lam_r(f - 1, lamL), rR = lam_r(f, lamR);
+                double gF[9];
+#pragma unroll
+                for (int o = 0; o < NQ; o++) gF[o] = dtdx * (lamR[o] - lamL[o]);
+                gF[8] = dtdx * (rR - rL);
+                Dn<8> F[9];
+                face_eval<AXIS>(p, Uin, cells, seed, F);
+#pragma unroll
+                for (int o = 0; o < 9; o++) {
+#pragma unroll
+                    for (int k = 0; k < NQ; k++) acc[k] += gF[o] * F[o].d[k];
+                }
+                if (f == i) us_m = F[8].v;
+                if (f == i + 1) us_p = F[8].v;
+            }
+        }
+        // the cell's own R(U_i) (u*_{i+1/2} - u*_{i-1/2}) term:
+        // R.lam = lam4 a1 p1 + lam5 a2 p2 - lam7 a2, a_k p_k = (g_k-1) E_k - a_k g_k pinf_k
+        const double du = dtdx * (us_p - us_m);
+        acc[4] -= du * li[4] * p.gm1[0];
+        acc[5] -= du * li[5] * p.gm1[1];
+        acc[7] -= du * (li[4] * p.gpinf[0] - li[5] * p.gpinf[1] - li[7]);
+#pragma unroll
+        for (int k = 0; k < NQ; k++) Gin[gmap[k] * n + c] = acc[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// viscous stage along one axis (Sec. 3.2)
+// ---------------------------------------------------------------------------
+// coefficient planes: V = 1/rho, mu = a1 mu1 + a2 mu2, u0 = rho u_n / rho,
+// w0 = rho u_t / rho
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_adj_visc_prep(const DevParams p, const double *Uin, double *V, double *mu,
+                                                       double *u0, double *w0)
+{
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        double rho = Uin[c] + Uin[n + c];
+        double a2 = Uin[7 * n + c];
+        V[c] = 1.0 / rho;
+        mu[c] = (1.0 - a2) * p.mu[0] + a2 * p.mu[1];
+        u0[c] = Uin[QN * n + c] / rho;
+        w0[c] = Uin[QT * n + c] / rho;
+    }
+}
+
+// the contribution of face (l, r) to J through the conservative last sweep:
+// S = sum over s in {l (+), r (-)} of sign_s tau/h [G_s^n Fn + G_s^t Ft +
+//     G_s^E W + (G_s^E1 aF1 + G_s^E2 aF2)(W - uh_s Fn - wh_s Ft)]
+// with inputs x = (uh_l, uh_r, wh_l, wh_r, a_l, a_r, mu_l, mu_r)
+// (ih = 1/h; the factor tau/h of the update is folded into Gl, Gr by the caller)
+__device__ __forceinline__ Dn<8> visc_face_J(const double *x, const double *Gl, const double *Gr, double ih)
+{
+    Dn<8> ul = dseed<8>(x[0], 0), ur = dseed<8>(x[1], 1), wl = dseed<8>(x[2], 2), wr = dseed<8>(x[3], 3);
+    Dn<8> al = dseed<8>(x[4], 4), ar = dseed<8>(x[5], 5), ml = dseed<8>(x[6], 6), mr = dseed<8>(x[7], 7);
+    Dn<8> lnf = 0.5 * (4.0 / 3.0 * ml + 4.0 / 3.0 * mr);
+    Dn<8> lmf = 0.5 * (ml + mr);
+    Dn<8> Fn = lnf * (ur - ul) * ih;
+    Dn<8> Ft = lmf * (wr - wl) * ih;
+    Dn<8> W = 0.5 * (ul + ur) * Fn + 0.5 * (wl + wr) * Ft;
+    Dn<8> aF2 = 0.5 * (al + ar);
+    Dn<8> aF1 = 0.5 * ((1.0 - al) + (1.0 - ar));
+    // Gl/Gr: (G^n, G^t, G^E, G^E1, G^E2) of the two cells, each already times tau/h
+    Dn<8> Sl = Gl[0] * Fn + Gl[1] * Ft + Gl[2] * W + (Gl[3] * aF1 + Gl[4] * aF2) * (W - ul * Fn - wl * Ft);
+    Dn<8> Sr = Gr[0] * Fn + Gr[1] * Ft + Gr[2] * W + (Gr[3] * aF1 + Gr[4] * aF2) * (W - ur * Fn - wr * Ft);
+    return Sl - Sr;
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(128) k_adj_visc_final(const DevParams p, const double *G, const double *A2,
+                                                        const double *mu, const double *uh, const double *wh,
+                                                        double *Gin, double *ub, double *wb, double *ab,
+                                                        double *mub, double tau)
+{
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    const int n = p.n;
+    const double ih = AXIS == 0 ? 1.0 / p.dx : 1.0 / p.dy;
+    const double tih = tau * ih;
+    GRID_LOOP(c, n)
+    {
+        int cm, cp;
+        axis_nb(p, AXIS, c, cm, cp);
+        double su = 0.0, sw = 0.0, sa = 0.0, sm = 0.0;
+        for (int sd = 0; sd < 2; sd++) {
+            const int nb = sd == 0 ? cm : cp;
+            if (nb < 0) continue;
+            const int l = sd == 0 ? cm : c, r = sd == 0 ? c : cp;
+            double x[8] = {uh[l], uh[r], wh[l], wh[r], A2[l], A2[r], mu[l], mu[r]};
+            double Gl[5] = {tih * G[QN * n + l], tih * G[QT * n + l], tih * G[6 * n + l], tih * G[4 * n + l],
+                            tih * G[5 * n + l]};
+            double Gr[5] = {tih * G[QN * n + r], tih * G[QT * n + r], tih * G[6 * n + r], tih * G[4 * n + r],
+                            tih * G[5 * n + r]};
+            Dn<8> S = visc_face_J(x, Gl, Gr, ih);
+            // this cell is r of the minus face, l of the plus face
+            const int o = sd == 0 ? 1 : 0;
+            su += S.d[0 + o];
+            sw += S.d[2 + o];
+            sa += S.d[4 + o];
+            sm += S.d[6 + o];
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; k++) Gin[k * n + c] = G[k * n + c];
+        ub[c] = su;
+        wb[c] = sw;
+        ab[c] = sa;
+        mub[c] = sm;
+    }
+}
+
+// one reverse LIM sweep of both velocity fields; uprev/wprev = u^{m-1}, w^{m-1}
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_adj_visc_lim(const DevParams p, const double *V, const double *mu,
+                                                      const double *uprev, const double *wprev, const double *ubi,
+                                                      const double *wbi, double *ubo, double *wbo, double *u0b,
+                                                      double *w0b, double *Vb, double *mub, double tau, double bm,
+                                                      double rden)
+{
+    const int n = p.n;
+    const double ih2 = AXIS == 0 ? p.idx2 : p.idy2;
+    GRID_LOOP(c, n)
+    {
+        int cm, cp;
+        axis_nb(p, AXIS, c, cm, cp);
+        const double mc = mu[c];
+        const double yu = rden * ubi[c], yw = rden * wbi[c];
+        const double zu = V[c] * yu, zw = V[c] * yw;
+        double lu = 0.0, lw = 0.0;      // L(V y) at c
+        double Lup = 0.0, Lwp = 0.0;    // L(u^{m-1}) at c
+        double mb = 0.0;
+        for (int sd = 0; sd < 2; sd++) {
+            const int nb = sd == 0 ? cm : cp;
+            if (nb < 0) continue;
+            const double mn = mu[nb];
+            const double lnf = 0.5 * (4.0 / 3.0 * mn + 4.0 / 3.0 * mc), lmf = 0.5 * (mn + mc);
+            const double zun = V[nb] * (rden * ubi[nb]), zwn = V[nb] * (rden * wbi[nb]);
+            lu += lnf * (zun - zu) * ih2;
+            lw += lmf * (zwn - zw) * ih2;
+            const double du = uprev[nb] - uprev[c], dw = wprev[nb] - wprev[c];
+            Lup += lnf * du * ih2;
+            Lwp += lmf * dw * ih2;
+            // face coefficient adjoints tau (z_c - z_nb)(u_nb - u_c)/h^2, half to this cell
+            const double lnb = tau * (zu - zun) * du * ih2, lmb = tau * (zw - zwn) * dw * ih2;
+            mb += 0.5 * (4.0 / 3.0) * lnb + 0.5 * lmb;
+        }
+        ubo[c] = tau * bm * yu + tau * lu;
+        wbo[c] = tau * bm * yw + tau * lw;
+        u0b[c] += yu;
+        w0b[c] += yw;
+        Vb[c] += tau * (yu * Lup + yw * Lwp);
+        mub[c] += mb;
+    }
+}
+
+// V = 1/rho, u0 = rho u_n / rho, w0, mu = a1 mu1 + a2 mu2 -> G
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_adj_visc_coef(const DevParams p, const double *Uin, const double *u0,
+                                                       const double *w0, const double *u0b, const double *w0b,
+                                                       const double *ub0, const double *wb0, const double *Vb,
+                                                       const double *mub, const double *ab, double *Gin, double *pbar)
+{
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    const int n = p.n;
+    double s2 = 0.0, s3 = 0.0;
+    GRID_LOOP(c, n)
+    {
+        const double rho = Uin[c] + Uin[n + c], a2 = Uin[7 * n + c];
+        const double V = 1.0 / rho;
+        const double ubt = u0b[c] + ub0[c], wbt = w0b[c] + wb0[c];
+        Gin[QN * n + c] += ubt / rho;
+        Gin[QT * n + c] += wbt / rho;
+        const double rb = -(ubt * u0[c] + wbt * w0[c]) / rho - Vb[c] * V * V;
+        Gin[c] += rb;
+        Gin[n + c] += rb;
+        Gin[7 * n + c] += ab[c] + mub[c] * (p.mu[1] - p.mu[0]);
+        s2 += mub[c] * (1.0 - a2);
+        s3 += mub[c] * a2;
+    }
+    add_param(pbar, 2, s2);
+    add_param(pbar, 3, s3);
+}
+
+// ---------------------------------------------------------------------------
+// heat-conduction stage (Sec. 3.4.2, Algorithm 1 with the LIM)
+// ---------------------------------------------------------------------------
+// (L v)_c with face coefficient the mean of the two cells' Lam (Eq. qk_dis)
+__device__ __forceinline__ double lap_v(const DevParams &p, int c, const double *v, const double *L)
+{
+    double r = 0.0;
+    const double vc = v[c], Lc = L[c];
+    for (int ax = 0; ax < 2; ax++) {
+        int cm, cp;
+        axis_nb(p, ax, c, cm, cp);
+        const double ih2 = ax == 0 ? p.idx2 : p.idy2;
+        const double fl = cm >= 0 ? 0.5 * (L[cm] + Lc) * (vc - v[cm]) * ih2 : 0.0;
+        const double fr = cp >= 0 ? 0.5 * (Lc + L[cp]) * (v[cp] - vc) * ih2 : 0.0;
+        r += fr - fl;
+    }
+    return r;
+}
+
+// sum over the faces of c of (a_c - a_nb)(v_nb - v_c)/h^2: half of it is the
+// adjoint of Lam_c through the two-cell face means
+__device__ __forceinline__ double face_lam_adj(const DevParams &p, int c, const double *a, const double *v)
+{
+    double s = 0.0;
+    for (int ax = 0; ax < 2; ax++) {
+        int cm, cp;
+        axis_nb(p, ax, c, cm, cp);
+        const double ih2 = ax == 0 ? p.idx2 : p.idy2;
+        if (cm >= 0) s += (a[c] - a[cm]) * (v[cm] - v[c]) * ih2;
+        if (cp >= 0) s += (a[c] - a[cp]) * (v[cp] - v[c]) * ih2;
+    }
+    return s;
+}
+
+// T0 = mixture temperature of the stage input; T0bar cleared
+__global__ void __launch_bounds__(256) k_adj_heat_prep(const DevParams p, const double *Uin, double *T0, double *T0b)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        T0[c] = mixture_T(p, Uin[c], Uin[n + c], Uin[4 * n + c], Uin[5 * n + c], Uin[7 * n + c]);
+        T0b[c] = 0.0;
+    }
+}
+
+// frozen coefficients of one outer iteration from its (T_it, a_it)
+__global__ void __launch_bounds__(256) k_adj_heat_coef_fwd(const DevParams p, const double *Uin, const double *Tit,
+                                                           const double *ait, double *V, double *L, double *Ia)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        double v, l;
+        heat_coeffs(p, Uin[c], Uin[n + c], Tit[c], ait[c], v, l);
+        V[c] = v;
+        L[c] = l;
+        Ia[c] = (1.0 - ait[c]) * p.src[0] + ait[c] * p.src[1];
+    }
+}
+
+// adjoint through (T, a) = equilibrium(m1, m2, rho e0 + tau q) of one outer
+// iteration; last: the iteration whose result is the stage output
+// (E_k = m_k Cv_k T + a_k pinf_k, rho E = rho E0 + tau q, alpha_2 = a)
+__global__ void __launch_bounds__(256) k_adj_heat_eq(const DevParams p, const double *Uin, const double *G,
+                                                     const double *vM, const double *L, const double *Ia,
+                                                     const double *Tb, const double *ab, double *Gin, double *qb,
+                                                     double tau, int last)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        const double m1v = Uin[c], m2v = Uin[n + c];
+        const double q = lap_v(p, c, vM, L) + Ia[c];
+        Dn<3> m1 = dseed<3>(m1v, 0), m2 = dseed<3>(m2v, 1);
+        Dn<3> re = dseed<3>(Uin[4 * n + c] + Uin[5 * n + c] + tau * q, 2);
+        Dn<3> T, a;
+        d_equilibrium(p, m1, m2, re, T, a);
+        double tb, abr, g0 = 0.0, g1 = 0.0, qbc = 0.0;
+        if (last) {
+            const double g4 = G[4 * n + c], g5 = G[5 * n + c];
+            tb = g4 * m1v * p.cv[0] + g5 * m2v * p.cv[1];
+            abr = -g4 * p.pinf[0] + g5 * p.pinf[1] + G[7 * n + c];
+            g0 = g4 * p.cv[0] * T.v;
+            g1 = g5 * p.cv[1] * T.v;
+            qbc = tau * G[6 * n + c];
+#pragma unroll
+            for (int k = 0; k < 4; k++) Gin[k * n + c] = G[k * n + c];
+            Gin[6 * n + c] = G[6 * n + c];
+            Gin[4 * n + c] = 0.0;
+            Gin[5 * n + c] = 0.0;
+            Gin[7 * n + c] = 0.0;
+        } else {
+            tb = Tb[c];
+            abr = ab[c];
+        }
+        const double rb = tb * T.d[2] + abr * a.d[2];
+        Gin[c] += g0 + tb * T.d[0] + abr * a.d[0];
+        Gin[n + c] += g1 + tb * T.d[1] + abr * a.d[1];
+        // rho e0 = E1 + E2
+        Gin[4 * n + c] += rb;
+        Gin[5 * n + c] += rb;
+        qb[c] = qbc + tau * rb;
+    }
+}
+
+// q = L(v^M) + Ia: vbar^M = L(qbar) (L symmetric), Lam and Ia adjoints
+__global__ void __launch_bounds__(256) k_adj_heat_q(const DevParams p, const double *qb, const double *vM,
+                                                    const double *L, double *vb, double *Lb, double *Iab, double *Vb)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        vb[c] = lap_v(p, c, qb, L);
+        Lb[c] = 0.5 * face_lam_adj(p, c, qb, vM);
+        Iab[c] = qb[c];
+        Vb[c] = 0.0;
+    }
+}
+
+// one reverse predictor sweep: vprev = v^{m-1}
+__global__ void __launch_bounds__(256) k_adj_heat_lim(const DevParams p, const double *V, const double *L,
+                                                      const double *Ia, const double *vprev, const double *vbi,
+                                                      double *vbo, double *T0b, double *Vb, double *Lb, double *Iab,
+                                                      double *z, double tau, double bm, double rden, int phase)
+{
+    const int n = p.n;
+    if (phase == 0) {
+        // z = V y, y = vbar^m / (1 + tau b_m)
+        GRID_LOOP(c, n) z[c] = V[c] * (rden * vbi[c]);
+        return;
+    }
+    GRID_LOOP(c, n)
+    {
+        const double y = rden * vbi[c];
+        vbo[c] = tau * bm * y + tau * lap_v(p, c, z, L);
+        T0b[c] += y;
+        Vb[c] += tau * y * (lap_v(p, c, vprev, L) + Ia[c]);
+        Lb[c] += 0.5 * tau * face_lam_adj(p, c, z, vprev);
+        Iab[c] += tau * V[c] * y;
+    }
+}
+
+// coefficients (V, Lam, Ia) at (m1, m2, T_it, a_it) -> m1, m2 and (T_it, a_it);
+// first: iteration 0, whose (T, a) are the stage input's (T0, alpha_2)
+__global__ void __launch_bounds__(256) k_adj_heat_coef(const DevParams p, const double *Uin, const double *Tit,
+                                                       const double *ait, const double *Vb, const double *Lb,
+                                                       const double *Iab, const double *vb0, double *T0b, double *Tb,
+                                                       double *ab, double *Gin, double *pbar, int first)
+{
+    const int n = p.n;
+    double sk0 = 0.0, sk1 = 0.0, si0 = 0.0, si1 = 0.0;
+    GRID_LOOP(c, n)
+    {
+        Dn<4> m1 = dseed<4>(Uin[c], 0), m2 = dseed<4>(Uin[n + c], 1);
+        Dn<4> T = dseed<4>(Tit[c], 2), a = dseed<4>(ait[c], 3);
+        Dn<4> V, L, I;
+        d_heat_coeffs(p, m1, m2, T, a, V, L, I);
+        const double vb = Vb[c], lb = Lb[c], ib = Iab[c];
+        double g[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) g[k] = vb * V.d[k] + lb * L.d[k] + ib * I.d[k];
+        Gin[c] += g[0];
+        Gin[n + c] += g[1];
+        // the LIM start v^0 = T0: its adjoint after the reverse sweeps
+        T0b[c] += vb0[c];
+        if (first) {
+            T0b[c] += g[2];
+            Gin[7 * n + c] += g[3];
+        } else {
+            Tb[c] = g[2];
+            ab[c] = g[3];
+        }
+        const double r = law_ratio(p, Tit[c]);
+        sk0 += lb * (1.0 - ait[c]) * r;
+        sk1 += lb * ait[c] * r;
+        si0 += ib * (1.0 - ait[c]);
+        si1 += ib * ait[c];
+    }
+    add_param(pbar, 0, sk0);
+    add_param(pbar, 1, sk1);
+    add_param(pbar, 4, si0);
+    add_param(pbar, 5, si1);
+}
+
+// T0 = (E1 + E2 - a1 pinf_1 - a2 pinf_2)/(m1 Cv_1 + m2 Cv_2) -> G
+__global__ void __launch_bounds__(256) k_adj_heat_T0(const DevParams p, const double *Uin, const double *T0b,
+                                                     double *Gin)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        const double m1 = Uin[c], m2 = Uin[n + c], a2 = Uin[7 * n + c];
+        const double C = m1 * p.cv[0] + m2 * p.cv[1];
+        const double T = mixture_T(p, m1, m2, Uin[4 * n + c], Uin[5 * n + c], a2);
+        const double tb = T0b[c];
+        const double w = tb / C;
+        Gin[c] += -w * T * p.cv[0];
+        Gin[n + c] += -w * T * p.cv[1];
+        Gin[4 * n + c] += w;
+        Gin[5 * n + c] += w;
+        Gin[7 * n + c] += w * (p.pinf[0] - p.pinf[1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// initial data: primbar = (dU/dprim)^T Ubar of the conversion (alpha_2, p, T,
+// u, v) -> U with both phases at (p, T) (Eqs. eos_stiffened, eos_stiffened2)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_from_primitive(const DevParams p, const double *prim,
+                                                            const double *Ub, double *pb)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        Dn<5> a2 = dseed<5>(prim[c], 0), pr = dseed<5>(prim[n + c], 1), T = dseed<5>(prim[2 * n + c], 2);
+        Dn<5> u = dseed<5>(prim[3 * n + c], 3), v = dseed<5>(prim[4 * n + c], 4);
+        Dn<5> a1 = 1.0 - a2;
+        Dn<5> rho1 = (pr + p.pinf[0]) / (p.gm1[0] * p.cv[0] * T);
+        Dn<5> rho2 = (pr + p.pinf[1]) / (p.gm1[1] * p.cv[1] * T);
+        Dn<5> m1 = a1 * rho1, m2 = a2 * rho2, rho = m1 + m2;
+        Dn<5> E1 = d_sgE(p, 0, pr, a1), E2 = d_sgE(p, 1, pr, a2);
+        Dn<5> out[NQ];
+        out[0] = m1;
+        out[1] = m2;
+        out[2] = rho * u;
+        out[3] = rho * v;
+        out[4] = E1;
+        out[5] = E2;
+        out[6] = E1 + E2 + 0.5 * rho * (u * u + v * v);
+        out[7] = a2;
+        double r[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < NQ; k++) {
+            const double g = Ub[k * n + c];
+#pragma unroll
+            for (int j = 0; j < 5; j++) r[j] += g * out[k].d[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 5; j++) pb[j * n + c] = r[j];
+    }
+}
+
+int grid_for(int n, int threads)
+{
+    int b = (n + threads - 1) / threads;
+    return b < 152 * 16 ? b : 152 * 16;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers (stream-ordered, asynchronous)
+// ---------------------------------------------------------------------------
+cudaError_t adj_prelax(const DevParams &p, const double *Uin, double *G, cudaStream_t s)
+{
+    k_adj_prelax<<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, G);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_trelax(const DevParams &p, const double *Uin, double *G, cudaStream_t s)
+{
+    k_adj_trelax<<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, G);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_sweep(const DevParams &p, int axis, const double *Uin, const double *Gout, double *Gin, double dtdx,
+                      cudaStream_t s)
+{
+    if (axis == 0) k_adj_sweep<0><<<grid_for(p.n, 128), 128, 0, s>>>(p, Uin, Gout, Gin, dtdx);
+    else k_adj_sweep<1><<<grid_for(p.n, 128), 128, 0, s>>>(p, Uin, Gout, Gin, dtdx);
+    return cudaGetLastError();
+}
+
+// planes of the viscous adjoint: 11 work planes W[0..10] (V, mu, u0, w0, ub x2,
+// wb x2, u0b, w0b, Vb) + ab, mub = 13
+constexpr int VISC_WORK_PLANES = 13;
+
+// Reverse of one viscous stage.  hist: u^1..u^M, w^1..w^M (M = 2P - 2);
+// b[m-1], m = 1..M: the frozen Chebyshev parameters.  G: adjoint of the stage
+// output, Gin: adjoint of the stage input (out).  work: 13 planes.
+cudaError_t adj_visc(const DevParams &p, int axis, const double *Uin, const double *hist, int M, const double *b,
+                     double tau, const double *G, double *Gin, double *work, double *pbar, cudaStream_t s)
+{
+    const size_t n = (size_t)p.n;
+    double *V = work, *mu = work + n, *u0 = work + 2 * n, *w0 = work + 3 * n;
+    double *ubA = work + 4 * n, *ubB = work + 5 * n, *wbA = work + 6 * n, *wbB = work + 7 * n;
+    double *u0b = work + 8 * n, *w0b = work + 9 * n, *Vb = work + 10 * n, *ab = work + 11 * n, *mub = work + 12 * n;
+    const int gb = grid_for(p.n, 256), gb2 = grid_for(p.n, 128);
+    cudaError_t e;
+    if (axis == 0) k_adj_visc_prep<0><<<gb, 256, 0, s>>>(p, Uin, V, mu, u0, w0);
+    else k_adj_visc_prep<1><<<gb, 256, 0, s>>>(p, Uin, V, mu, u0, w0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double *uh = M > 0 ? hist + (size_t)(M - 1) * n : u0;
+    const double *wh = M > 0 ? hist + (size_t)(2 * M - 1) * n : w0;
+    if (axis == 0) k_adj_visc_final<0><<<gb2, 128, 0, s>>>(p, G, Uin + 7 * n, mu, uh, wh, Gin, ubA, wbA, ab, mub, tau);
+    else k_adj_visc_final<1><<<gb2, 128, 0, s>>>(p, G, Uin + 7 * n, mu, uh, wh, Gin, ubA, wbA, ab, mub, tau);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(u0b, 0, 3 * n * sizeof(double), s)) != cudaSuccess) return e;  // u0b, w0b, Vb
+    double *ui = ubA, *uo = ubB, *wi = wbA, *wo = wbB;
+    for (int m = M; m >= 1; m--) {
+        const double bm = b[m - 1], rden = 1.0 / (1.0 + tau * bm);
+        const double *up = m >= 2 ? hist + (size_t)(m - 2) * n : u0;
+        const double *wp = m >= 2 ? hist + (size_t)(M + m - 2) * n : w0;
+        if (axis == 0)
+            k_adj_visc_lim<0><<<gb, 256, 0, s>>>(p, V, mu, up, wp, ui, wi, uo, wo, u0b, w0b, Vb, mub, tau, bm, rden);
+        else
+            k_adj_visc_lim<1><<<gb, 256, 0, s>>>(p, V, mu, up, wp, ui, wi, uo, wo, u0b, w0b, Vb, mub, tau, bm, rden);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        double *t = ui; ui = uo; uo = t;
+        t = wi; wi = wo; wo = t;
+    }
+    if (axis == 0) k_adj_visc_coef<0><<<gb, 256, 0, s>>>(p, Uin, u0, w0, u0b, w0b, ui, wi, Vb, mub, ab, Gin, pbar);
+    else k_adj_visc_coef<1><<<gb, 256, 0, s>>>(p, Uin, u0, w0, u0b, w0b, ui, wi, Vb, mub, ab, Gin, pbar);
+    return cudaGetLastError();
+}
+
+// planes of the heat adjoint: T0, T0b, V, L, Ia, qb, vb x2, Lb, Iab, Vb, Tb, ab, z
+constexpr int HEAT_WORK_PLANES = 14;
+
+// Reverse of one heat-conduction stage (Algorithm 1, N outer iterations).
+// hist: per iteration it, 2 P_it planes (T_it, a_it, v^1..v^{M_it}); Ms[it] =
+// 2 P_it - 2; bs: the frozen b of every iteration, concatenated (M_it each).
+cudaError_t adj_heat(const DevParams &p, const double *Uin, const double *hist, int N, const int *Ms,
+                     const double *bs, double tau, const double *G, double *Gin, double *work, double *pbar,
+                     cudaStream_t s)
+{
+    const size_t n = (size_t)p.n;
+    double *T0 = work, *T0b = work + n, *V = work + 2 * n, *L = work + 3 * n, *Ia = work + 4 * n;
+    double *qb = work + 5 * n, *vbA = work + 6 * n, *vbB = work + 7 * n, *Lb = work + 8 * n, *Iab = work + 9 * n;
+    double *Vb = work + 10 * n, *Tb = work + 11 * n, *ab = work + 12 * n, *z = work + 13 * n;
+    const int gb = grid_for(p.n, 256);
+    cudaError_t e;
+    k_adj_heat_prep<<<gb, 256, 0, s>>>(p, Uin, T0, T0b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // history offsets of the iterations
+    size_t off[8];
+    size_t boff[8];
+    size_t o = 0, ob = 0;
+    for (int it = 0; it < N; it++) {
+        off[it] = o;
+        boff[it] = ob;
+        o += (size_t)Ms[it] + 2;
+        ob += (size_t)Ms[it];
+    }
+    for (int it = N - 1; it >= 0; it--) {
+        const int M = Ms[it];
+        const double *Tit = hist + off[it] * n, *ait = hist + (off[it] + 1) * n;
+        auto v_of = [&](int m) -> const double * { return m == 0 ? T0 : hist + (off[it] + 1 + m) * n; };
+        k_adj_heat_coef_fwd<<<gb, 256, 0, s>>>(p, Uin, Tit, ait, V, L, Ia);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_adj_heat_eq<<<gb, 256, 0, s>>>(p, Uin, G, v_of(M), L, Ia, Tb, ab, Gin, qb, tau, it == N - 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_adj_heat_q<<<gb, 256, 0, s>>>(p, qb, v_of(M), L, vbA, Lb, Iab, Vb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        double *vi = vbA, *vo = vbB;
+        for (int m = M; m >= 1; m--) {
+            const double bm = bs[boff[it] + m - 1], rden = 1.0 / (1.0 + tau * bm);
+            k_adj_heat_lim<<<gb, 256, 0, s>>>(p, V, L, Ia, v_of(m - 1), vi, vo, T0b, Vb, Lb, Iab, z, tau, bm, rden, 0);
+            k_adj_heat_lim<<<gb, 256, 0, s>>>(p, V, L, Ia, v_of(m - 1), vi, vo, T0b, Vb, Lb, Iab, z, tau, bm, rden, 1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            double *t = vi; vi = vo; vo = t;
+        }
+        k_adj_heat_coef<<<gb, 256, 0, s>>>(p, Uin, Tit, ait, Vb, Lb, Iab, vi, T0b, Tb, ab, Gin, pbar, it == 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_adj_heat_T0<<<gb, 256, 0, s>>>(p, Uin, T0b, Gin);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_from_primitive(const DevParams &p, const double *prim, const double *Ub, double *pb, cudaStream_t s)
+{
+    k_adj_from_primitive<<<grid_for(p.n, 256), 256, 0, s>>>(p, prim, Ub, pb);
+    return cudaGetLastError();
+}
+
+int adj_visc_work_planes() { return VISC_WORK_PLANES; }
+int adj_heat_work_planes() { return HEAT_WORK_PLANES; }
+
+}  // namespace dimk

@@ -11,62 +11,12 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "../../include/dim.h"
-#include "dim_device.cuh"
+#include "dim_ctx.h"
 
-namespace dimk {
-cudaError_t sweep_setup();
-cudaError_t parabolic_setup(int nsm);
-cudaError_t launch_sweep(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
-                         int relax, int check, cudaStream_t s);
-cudaError_t launch_from_primitive(const DevParams &p, const double *prim, double *U, Scalars *sc, cudaStream_t s);
-cudaError_t launch_wave_max(const DevParams &p, const double *U, Scalars *sc, cudaStream_t s);
-cudaError_t launch_relax(const DevParams &p, double *U, Scalars *sc, int which, int check, cudaStream_t s);
-cudaError_t launch_heat(const DevParams &p, double *U, const HeatScratch &s, Scalars *sc, double dt_host,
-                        int trelax_first, int check, cudaStream_t st);
-cudaError_t launch_visc(const DevParams &p, int axis, double *U, const ViscScratch &s, Scalars *sc, double dt_host,
-                        int relax, int check, cudaStream_t st);
-cudaError_t bulk32_setup(int nsm);
-cudaError_t launch_sweep32(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
-                           int relax, int check, cudaStream_t s);
-cudaError_t launch_wave_max32(const DevParams &p, const double *U, Scalars *sc, cudaStream_t s);
-cudaError_t launch_heat32(const DevParams &p, double *U, double *S, Scalars *sc, double dt_host, int trelax_first,
-                          int check, cudaStream_t st);
-cudaError_t launch_visc32(const DevParams &p, int axis, double *U, double *S, Scalars *sc, double dt_host, int relax,
-                          int check, cudaStream_t st);
-}  // namespace dimk
+using namespace dimctx;
 
-using dimk::DevParams;
-using dimk::Scalars;
-
-namespace {
-
-enum KernelId { K_SWEEP_X, K_SWEEP_Y, K_HEAT, K_VISC_X, K_VISC_Y, K_WAVE, K_RELAX, K_COPY, K_NKERNELS };
-const char *kKernelNames[K_NKERNELS] = {"sweep_x", "sweep_y", "heat", "viscous_x", "viscous_y", "wave_max", "relax",
-                                        "copy"};
-
-struct ProfRec {
-    int kid;
-    cudaEvent_t a, b;
-};
-
-}  // namespace
-
-struct dim_ctx {
-    dim_params hp;
-    DevParams p;
-    cudaStream_t stream;
-    double *U2;   // 8 planes: out-of-place target of the sweeps
-    double *S;    // 8 scratch planes for the parabolic stages
-    double *Uh;   // 8 planes: device copy of a host state (dim_step_host), lazily allocated
-    double *beta; // Chebyshev roots table (PMAX x PMAX)
-    Scalars *sc;
-    int device;
-    // profiling
-    int prof;
-    ProfRec *recs;
-    int nrec, caprec;
-};
+static const char *const kKernelNames[K_NKERNELS] = {"sweep_x", "sweep_y", "heat", "viscous_x",
+                                                     "viscous_y", "wave_max", "relax", "copy"};
 
 static bool g_setup_done[64];
 
@@ -119,14 +69,14 @@ static dimk::HeatScratch heat_scratch(dim_ctx *c)
 {
     size_t n = (size_t)c->p.n;
     double *S = c->S;
-    return dimk::HeatScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n};
+    return dimk::HeatScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n, nullptr};
 }
 
 static dimk::ViscScratch visc_scratch(dim_ctx *c)
 {
     size_t n = (size_t)c->p.n;
     double *S = c->S;
-    return dimk::ViscScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n};
+    return dimk::ViscScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n, nullptr};
 }
 
 static bool fp32(const dim_ctx *c) { return c->p.precision == DIM_PRECISION_FP32_BULK; }
@@ -151,12 +101,6 @@ static cudaError_t run_visc(dim_ctx *c, int axis, double *U, double dt, int rela
     return fp32(c) ? dimk::launch_visc32(c->p, axis, U, c->S, c->sc, dt, relax, check, c->stream)
                    : dimk::launch_visc(c->p, axis, U, visc_scratch(c), c->sc, dt, relax, check, c->stream);
 }
-
-#define TRY(x)                                     \
-    do {                                           \
-        cudaError_t e_ = (x);                      \
-        if (e_ != cudaSuccess) return DIM_ECUDA;   \
-    } while (0)
 
 #define TIMED(c, kid, launch)                      \
     do {                                           \
@@ -310,6 +254,7 @@ void dim_destroy(dim_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    grad_free(c);
     cudaFree(c->U2);
     cudaFree(c->S);
     cudaFree(c->Uh);
@@ -480,13 +425,6 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
     return DIM_OK;
 }
 
-int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const double *dJ_dUT, double *dJ_dU0,
-             double *dJ_dparams)
-{
-    (void)c; (void)U0; (void)nsteps; (void)ckpt_every; (void)dJ_dUT; (void)dJ_dU0; (void)dJ_dparams;
-    return DIM_ENOTIMPL;
-}
-
 int dim_status(dim_ctx *c, unsigned *flags, int reset)
 {
     if (!c || !flags) return DIM_EINVAL;
@@ -530,3 +468,20 @@ int dim_kernel_time(dim_ctx *c, const char *name, int *launches, double *ms)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// helpers for the gradient driver (dim_grad.cu)
+// ---------------------------------------------------------------------------
+int ctx_step_once(dim_ctx *c, double *U) { return step_once(c, U); }
+cudaError_t ctx_reset_scalars(dim_ctx *c) { return reset_accumulators(c); }
+dimk::HeatScratch ctx_heat_scratch(dim_ctx *c) { return heat_scratch(c); }
+dimk::ViscScratch ctx_visc_scratch(dim_ctx *c) { return visc_scratch(c); }
+bool ctx_viscous_on(const dim_params &h) { return viscous_on(h); }
+bool ctx_heat_on(const dim_params &h) { return heat_on(h); }
+int ctx_status_code(dim_ctx *c)
+{
+    unsigned st = 0;
+    TRY(cudaMemcpyAsync(&st, &c->sc->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    return status_to_code(st);
+}

@@ -34,6 +34,9 @@ struct DevParams {
     int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
     int precision;  // DIM_PRECISION_FP64 or DIM_PRECISION_FP32_BULK
     double src[2];  // external heat source intensities I_k
+    // 1: the Chebyshev lambda_max of every LIM solve is read from the context
+    // scalars (a replayed schedule) instead of being reduced from the state
+    int frozen;
     // roots of T_P: beta[(P-1)*PMAX + m-1] = cos((2m-1) pi / (2P)), m = 1..P,
     // tabulated on the host (libm) once per context
     const double *beta;
@@ -53,11 +56,16 @@ struct Scalars {
 constexpr int LAM_VX = 8, LAM_VY = 9;
 
 // scratch planes of the parabolic stages (n doubles each)
+// hist (may be null): every LIM iterate is kept there instead of in the
+// ping-pong planes -- heat: per outer iteration it, 2 P_it planes
+// (T_it, alpha_it, v^1 .. v^{2P_it - 2}); viscous: u^1 .. u^{2P-2}, w^1 .. w^{2P-2}
 struct HeatScratch {
     double *T0, *V, *L, *va, *vb, *Ti, *Ai, *Ia;  // Ia = a1 I1 + a2 I2 (external source)
+    double *hist;
 };
 struct ViscScratch {
     double *V, *A2, *u0, *w0, *ua, *ub, *wa, *wb;
+    double *hist;
 };
 
 __device__ __forceinline__ double dmax_bits(unsigned long long b) { return __longlong_as_double((long long)b); }

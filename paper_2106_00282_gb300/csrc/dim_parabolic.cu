@@ -93,12 +93,15 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
         s.Ia[c] = (1.0 - a2) * p.src[0] + a2 * p.src[1];
     }
 
+    size_t hoff = 0;  // history planes used by the earlier outer iterations
     for (int it = 0; it < nout; it++) {
         if (!grid_barrier(sc)) return;
         // B. lambda_max (Gershgorin) of this iteration's frozen operator
-        double lm = 0.0;
-        for (int c = t0; c < n; c += nt) lm = fmax(lm, gersh(p, neighbours(p, c), c, s.V, s.L));
-        block_max_to(&sc->lam[it], lm);
+        if (!p.frozen) {
+            double lm = 0.0;
+            for (int c = t0; c < n; c += nt) lm = fmax(lm, gersh(p, neighbours(p, c), c, s.V, s.L));
+            block_max_to(&sc->lam[it], lm);
+        }
         if (!grid_barrier(sc)) return;
         double lam = read_acc(&sc->lam[it]);
         unsigned capped;
@@ -109,10 +112,16 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             if (capped) st |= capped;
         }
         __syncthreads();
+        if (s.hist) {
+            for (int c = t0; c < n; c += nt) {
+                s.hist[hoff * n + c] = it == 0 ? s.T0[c] : s.Ti[c];
+                s.hist[(hoff + 1) * n + c] = it == 0 ? U[7 * n + c] : s.Ai[c];
+            }
+        }
         // C. the 2P-2 predictor sweeps from v^(0) = T^n
         const double *vin = s.T0;
         for (int m = 1; m <= 2 * P - 2; m++) {
-            double *vout = (m & 1) ? s.va : s.vb;
+            double *vout = s.hist ? s.hist + (hoff + 1 + m) * n : ((m & 1) ? s.va : s.vb);
             const double bm = s_b[m - 1];
             const double rden = 1.0 / (1.0 + tau * bm);
             for (int c = t0; c < n; c += nt) {
@@ -122,6 +131,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             if (!grid_barrier(sc)) return;
             vin = vout;
         }
+        hoff += 2 * (size_t)P;
         // D. last (explicit, b = 0) sweep in conservative form on the energy and
         //    the projection onto the p,T-equilibrium manifold
         if (it == nout - 1) {
@@ -212,16 +222,18 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
         return (1.0 - a2) * p.mu[0] + a2 * p.mu[1];
     };
     // B. lambda_max with the normal coefficient 4/3 mu (bounds the tangential one too)
-    double lm = 0.0;
-    for (int c = t0; c < n; c += nt) {
-        int cm, cp;
-        visc_nb<AXIS>(p, c, cm, cp);
-        double lc = 4.0 / 3.0 * mu_of(c);
-        double fl = cm >= 0 ? 0.5 * (4.0 / 3.0 * mu_of(cm) + lc) : 0.0;
-        double fr = cp >= 0 ? 0.5 * (lc + 4.0 / 3.0 * mu_of(cp)) : 0.0;
-        lm = fmax(lm, 2.0 * s.V[c] * ((fl + fr) * ih2));
+    if (!p.frozen) {
+        double lm = 0.0;
+        for (int c = t0; c < n; c += nt) {
+            int cm, cp;
+            visc_nb<AXIS>(p, c, cm, cp);
+            double lc = 4.0 / 3.0 * mu_of(c);
+            double fl = cm >= 0 ? 0.5 * (4.0 / 3.0 * mu_of(cm) + lc) : 0.0;
+            double fr = cp >= 0 ? 0.5 * (lc + 4.0 / 3.0 * mu_of(cp)) : 0.0;
+            lm = fmax(lm, 2.0 * s.V[c] * ((fl + fr) * ih2));
+        }
+        block_max_to(&sc->lam[SLOT], lm);
     }
-    block_max_to(&sc->lam[SLOT], lm);
     if (!grid_barrier(sc)) return;
     double lam = read_acc(&sc->lam[SLOT]);
     unsigned capped;
@@ -234,9 +246,10 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
     __syncthreads();
     // C. predictor sweeps on u_n (4/3 mu) and u_t (mu)
     const double *uin = s.u0, *win = s.w0;
+    const size_t M = 2 * (size_t)P - 2;
     for (int m = 1; m <= 2 * P - 2; m++) {
-        double *uo = (m & 1) ? s.ua : s.ub;
-        double *wo = (m & 1) ? s.wa : s.wb;
+        double *uo = s.hist ? s.hist + (size_t)(m - 1) * n : ((m & 1) ? s.ua : s.ub);
+        double *wo = s.hist ? s.hist + (M + m - 1) * n : ((m & 1) ? s.wa : s.wb);
         const double bm = s_b[m - 1];
         const double rden = 1.0 / (1.0 + tau * bm);
         for (int c = t0; c < n; c += nt) {

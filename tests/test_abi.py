@@ -60,4 +60,6 @@ def test_init_rejects_bad_arguments(lib):
         s = _lib.make_params(p)
         assert lib.dim_init(C.byref(ctx), C.byref(s), nx, ny, dx, dy, None) == _lib.DIM_EINVAL
     assert lib.dim_step(None, None, 1, None) == _lib.DIM_EINVAL
-    assert lib.dim_grad(None, None, 1, 1, None, None, None) == _lib.DIM_ENOTIMPL
+    assert lib.dim_grad(None, None, 1, 1, None, None, None) == _lib.DIM_EINVAL
+    assert lib.dim_step_sched(None, None, 1, None, 0) == _lib.DIM_EINVAL
+    assert lib.dim_from_primitive_vjp(None, None, None, None) == _lib.DIM_EINVAL

@@ -171,3 +171,22 @@ def test_branch_record_changes_nothing_without_perturbation(O, I):
     Ufrozen = O.step_frozen(p, U0 + 0.5 * dU, wl.dx, wl.dy, 5, fr)[0]
     assert not np.array_equal(Ufree, Ufrozen)
     assert np.array_equal(O.step_frozen(p, U0, wl.dx, wl.dy, 5, fr)[0], U1)
+
+
+def test_extended_tangent_agrees_on_well_conditioned_flows(O, I):
+    """The long-double tangent, replaying the double run's schedule and
+    branches, agrees with the double tangent where the flow is well
+    conditioned (it is the rounding reference of the adjoint comparisons)."""
+    for wl, steps in [(I.smooth_mixture(24, 16, seed=2), 4), (I.shock_tube(n=100), 6), (I.conduction_disc(40), 4)]:
+        p = wl.params
+        U0 = O.from_primitive(p, wl.prim)
+        fr = O.step_frozen(p, U0, wl.dx, wl.dy, steps)[2]
+        d = direction(U0, p, 5)
+        dp = np.array([0.1, 0.01, 1e-4, 1e-6, 1e6, 1e5])
+        t = O.step_tangent(p, U0, d, wl.dx, wl.dy, steps, dp)[1]
+        te = O.step_tangent_ext(p, U0, d, wl.dx, wl.dy, steps, fr, dp)[1]
+        sc = np.abs(te).reshape(8, -1).max(1)[:, None] + 1e-300
+        err = (np.abs(t - te).reshape(8, -1) / sc).max()
+        print(f"[tangent] double vs long-double tangent ({wl.name}): {err:.1e}")
+        assert err < 1e-10
+
