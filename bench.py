@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk variant")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched configuration")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (dim_grad) measurement")
     return ap.parse_args()
 
 
@@ -279,6 +280,49 @@ def run_batched(dev, world=1, steps=10, warmup=3):
     return out
 
 
+def run_adjoint(dev, world=1):
+    """The gradient problem on the conduction disc (512^2, FP64, 200 steps,
+    checkpoints every 20): time of the forward run alone (dim_step) and of
+    dim_grad (forward with checkpoints + reverse sweep with recomputation),
+    each between device synchronizations, after one untimed call that
+    allocates the workspace."""
+    import torch
+
+    from paper_2106_00282_gb300 import inputs as I
+    from paper_2106_00282_gb300.api import Solver
+
+    wl = I.disc_gradient()
+    nsteps, ckpt = wl.steps, wl.meta["ckpt"]
+    s = Solver(wl.params, wl.nx, wl.ny, wl.dx, wl.dy)
+    U0 = s.from_primitive(torch.from_numpy(wl.prim).to(dev))
+    g = torch.randn(U0.shape, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(5))
+    g /= U0.abs().reshape(8, -1).mean(1).clamp_min(1.0)[:, None, None]
+    s.grad(U0, 4, g, 2)
+    U = U0.clone()
+    s.step(U, 2)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    U = U0.clone()
+    s.step(U, nsteps)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gU, gp = s.grad(U0, nsteps, g, ckpt)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    cells = wl.nx * wl.ny
+    _, value = aggregate(1e3 * t_grad, cells * nsteps, world, dev)
+    s.close()
+    return {"workload": f"conduction-disc gradient problem {wl.nx}x{wl.ny}, {nsteps} steps, checkpoints every {ckpt}",
+            "value": value, "unit": "cell-steps/s (forward + reverse)", "grad_s": t_grad, "forward_s": t_fwd,
+            "grad_over_forward": t_grad / t_fwd, "precision": "fp64",
+            "params_grad": [float(x) for x in gp]}
+
+
 def oracle_rate(wl, budget_s=10.0, max_steps=1000):
     """FP64 oracle (single-threaded C) on the same workload: steps until the budget."""
     from oracle import oracle as O
@@ -311,6 +355,7 @@ def main():
     r = run_ours(args, rank, world, dev)
     r32 = None if args.no_fp32 else run_ours(args, rank, world, dev, precision=1, with_e2e=False)
     rb = None if args.no_batch else run_batched(dev, world)
+    ra = None if args.no_adjoint else run_adjoint(dev, world)
     if rank == 0:
         wl = r["wl"]
         cpu = None
@@ -329,6 +374,8 @@ def main():
                 "e2e": r["e2e"], "clocks": r["clocks"], "gpu_launches": r["launches"]}
         if rb is not None:
             line["batched"] = rb
+        if ra is not None:
+            line["adjoint"] = ra
         if r32 is not None:
             line["fp32_bulk"] = {
                 "value": r32["value"], "unit": UNIT, "ms_per_step": r32["ms_per_step"],
