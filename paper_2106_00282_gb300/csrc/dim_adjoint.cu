@@ -140,14 +140,17 @@ __device__ __forceinline__ Dn<N> operator*(double a, const Dn<N> &b)
     for (int i = 0; i < N; i++) r.d[i] = a * b.d[i];
     return r;
 }
-// d(a/b) = (da - (a/b) db) / b
+// d(a/b) = (da - (a/b) db) / b.  The value is the IEEE quotient (the branch
+// decisions of the forward depend on it); the tangents multiply by one
+// reciprocal.
 template <int N>
 __device__ __forceinline__ Dn<N> operator/(const Dn<N> &a, const Dn<N> &b)
 {
     Dn<N> r;
     r.v = a.v / b.v;
+    const double ib = 1.0 / b.v;
 #pragma unroll
-    for (int i = 0; i < N; i++) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    for (int i = 0; i < N; i++) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
     return r;
 }
 template <int N>
@@ -155,8 +158,9 @@ __device__ __forceinline__ Dn<N> operator/(const Dn<N> &a, double b)
 {
     Dn<N> r;
     r.v = a.v / b;
+    const double ib = 1.0 / b;
 #pragma unroll
-    for (int i = 0; i < N; i++) r.d[i] = a.d[i] / b;
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] * ib;
     return r;
 }
 template <int N>
@@ -164,8 +168,9 @@ __device__ __forceinline__ Dn<N> operator/(double a, const Dn<N> &b)
 {
     Dn<N> r;
     r.v = a / b.v;
+    const double s = -r.v / b.v;
 #pragma unroll
-    for (int i = 0; i < N; i++) r.d[i] = (-r.v * b.d[i]) / b.v;
+    for (int i = 0; i < N; i++) r.d[i] = s * b.d[i];
     return r;
 }
 // d sqrt(a) = da / (2 sqrt(a))
@@ -174,8 +179,9 @@ __device__ __forceinline__ Dn<N> dsqrt(const Dn<N> &a)
 {
     Dn<N> r;
     r.v = sqrt(a.v);
+    const double h = 0.5 / r.v;
 #pragma unroll
-    for (int i = 0; i < N; i++) r.d[i] = a.d[i] / (2.0 * r.v);
+    for (int i = 0; i < N; i++) r.d[i] = a.d[i] * h;
     return r;
 }
 // x^e for the conductivity law, derivative e x^(e-1) (k_pow: 0 constant, >0
@@ -511,89 +517,199 @@ __global__ void __launch_bounds__(256) k_adj_trelax(const DevParams p, const dou
 }
 
 // ---------------------------------------------------------------------------
-// hyperbolic sweep: per-cell gather of the transposed face Jacobians
+// hyperbolic sweep (two kernels)
 // ---------------------------------------------------------------------------
-// the face between line positions f-1 and f, stencil positions f-2 .. f+1;
-// inputs of stencil positions with seed[k] carry the identity tangent
+// The flux (F, u*) of face f depends on its 4-cell stencil only through the
+// reconstructed primitives wl (cell f-1) and wr (cell f): 14 values.
+// k_adj_sweep_face, per face: the adjoint of the face outputs
+// gbar = dt/h (adj_R - adj_L) [and dt/h (R.adj_R - R.adj_L) for u*], the
+// transposed HLLC Jacobian with respect to (wl, wr) by two 7-wide dual passes,
+// then the transposed reconstruction (slopes: the minmod operand chosen, times
+// 1 or 2 for Overbee) -> the adjoint of the primitives W of the 4 stencil
+// cells, stored per face (28 values) with the face's u*.
+// k_adj_sweep_cell, per cell: the sum over the faces whose stencil holds the
+// cell (ghost positions mapped as in the forward), the transposed Jacobian of
+// the conversion q -> W, the identity of the update and the cell's own
+// R(U_i)(u*_{i+1/2} - u*_{i-1/2}) term.
+constexpr int FACE_ADJ_PLANES = 29;  // 4 x 7 primitive adjoints + u*
+
 template <int AXIS>
-__device__ __forceinline__ void face_eval(const DevParams &p, const double *U, const int *cells, const bool *seed,
-                                          Dn<8> *F)
+__device__ __forceinline__ void line_cell(const DevParams &p, int l, int pos, int &c)
 {
-    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
-    const int n = p.n;
-    const int gmap[NQ] = {0, 1, QN, QT, 4, 5, 6, 7};
-    Dn<8> W[4][7];
+    c = AXIS == 0 ? l * p.nx + pos : pos * p.nx + l;
+}
+
+__device__ __forceinline__ void prims_v(const DevParams &p, const double *q, double *w)
+{
+    double a2 = q[7], a1 = 1.0 - a2;
+    double rho = q[0] + q[1];
+    w[0] = a2;
+    w[1] = q[0];
+    w[2] = q[1];
+    w[3] = q[2] / rho;
+    w[4] = q[3] / rho;
+    w[5] = sg_p(p, 0, q[4], a1);
+    w[6] = sg_p(p, 1, q[5], a2);
+}
+
+// minmod operand choice with the forward's rules: 0 zero, 1 first, 2 second
+__device__ __forceinline__ int mm_choice(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return a < b ? 1 : 2;
+    if (a < 0.0 && b < 0.0) return a > b ? 1 : 2;
+    return 0;
+}
+
+// one dual pass over the face: seed = 0 differentiates w.r.t. wl, 1 w.r.t. wr;
+// returns sum_o gbar_o dF_o/dw
+__device__ __forceinline__ double face_pass(const DevParams &p, const double *wl, const double *wr, int seed,
+                                            const double *gF, double *wbar)
+{
+    Dn<7> a[7], b[7];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        Dn<8> q[NQ];
-#pragma unroll
-        for (int j = 0; j < NQ; j++) {
-            double v = U[gmap[j] * n + cells[k]];
-            q[j] = seed[k] ? dseed<8>(v, j) : dcst<8>(v);
-        }
-        d_prims(p, q, W[k]);
+    for (int j = 0; j < 7; j++) {
+        a[j] = seed == 0 ? dseed<7>(wl[j], j) : dcst<7>(wl[j]);
+        b[j] = seed == 1 ? dseed<7>(wr[j], j) : dcst<7>(wr[j]);
     }
-    Dn<8> wl[7], wr[7];
-    if (p.limiter != DIM_LIMITER_NONE) {
-        const bool ob = p.limiter == DIM_LIMITER_OVERBEE;
-#pragma unroll
-        for (int j = 0; j < 7; j++) {
-            Dn<8> sl = d_minmod(W[1][j] - W[0][j], W[2][j] - W[1][j]);
-            Dn<8> sr = d_minmod(W[2][j] - W[1][j], W[3][j] - W[2][j]);
-            if (ob && j <= 2) {
-                sl = 2.0 * sl;
-                sr = 2.0 * sr;
-            }
-            wl[j] = W[1][j] + 0.5 * sl;
-            wr[j] = W[2][j] - 0.5 * sr;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 7; j++) {
-            wl[j] = W[1][j];
-            wr[j] = W[2][j];
-        }
-    }
-    DFace<8> L, R;
-    d_face_state(p, wl, L);
-    d_face_state(p, wr, R);
+    DFace<7> L, R;
+    d_face_state(p, a, L);
+    d_face_state(p, b, R);
+    Dn<7> F[9];
     d_hllc(L, R, F);
+#pragma unroll
+    for (int j = 0; j < 7; j++) {
+        double s = 0.0;
+#pragma unroll
+        for (int o = 0; o < 9; o++) s += gF[o] * F[o].d[j];
+        wbar[j] = s;
+    }
+    return F[8].v;  // u* of the face
 }
 
 template <int AXIS>
-__global__ void __launch_bounds__(128) k_adj_sweep(const DevParams p, const double *Uin, const double *Gout,
-                                                   double *Gin, double dtdx)
+__global__ void __launch_bounds__(128) k_adj_sweep_face(const DevParams p, const double *Uin, const double *Gout,
+                                                        double *fw, double dtdx)
 {
     constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
     const int gmap[NQ] = {0, 1, QN, QT, 4, 5, 6, 7};
     const int n = p.n;
-    const int len = AXIS == 0 ? p.nx : p.ny;
+    const int len = AXIS == 0 ? p.nx : p.ny, nlines = AXIS == 0 ? p.ny : p.nx;
+    const int nf = (len + 1) * nlines;
+    const int bc = p.bc[AXIS];
+    const bool lim = p.limiter != DIM_LIMITER_NONE, ob = p.limiter == DIM_LIMITER_OVERBEE;
+    GRID_LOOP(fid, nf)
+    {
+        const int l = fid / (len + 1), f = fid - l * (len + 1);
+        double W[4][7];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int c;
+            line_cell<AXIS>(p, l, line_map(f - 2 + k, len, bc), c);
+            double q[NQ];
+#pragma unroll
+            for (int j = 0; j < NQ; j++) q[j] = Uin[gmap[j] * n + c];
+            prims_v(p, q, W[k]);
+        }
+        // reconstruction (values and limiter choices as in the forward)
+        double wl[7], wr[7];
+        int cl[7], cr[7];
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            if (lim) {
+                const double dml = W[1][j] - W[0][j], dpl = W[2][j] - W[1][j];
+                const double dmr = W[2][j] - W[1][j], dpr = W[3][j] - W[2][j];
+                cl[j] = mm_choice(dml, dpl);
+                cr[j] = mm_choice(dmr, dpr);
+                double sl = cl[j] == 1 ? dml : (cl[j] == 2 ? dpl : 0.0);
+                double sr = cr[j] == 1 ? dmr : (cr[j] == 2 ? dpr : 0.0);
+                if (ob && j <= 2) {
+                    sl = 2.0 * sl;
+                    sr = 2.0 * sr;
+                }
+                wl[j] = W[1][j] + 0.5 * sl;
+                wr[j] = W[2][j] - 0.5 * sr;
+            } else {
+                cl[j] = cr[j] = 0;
+                wl[j] = W[1][j];
+                wr[j] = W[2][j];
+            }
+        }
+        // adjoint of the face outputs: cells f-1 (plus face) and f (minus face)
+        double gF[9];
+        {
+            double rL = 0.0, rR = 0.0;
+#pragma unroll
+            for (int o = 0; o < NQ; o++) gF[o] = 0.0;
+            if (f - 1 >= 0) {
+                int c;
+                line_cell<AXIS>(p, l, f - 1, c);
+                double lam[NQ];
+#pragma unroll
+                for (int o = 0; o < NQ; o++) lam[o] = Gout[gmap[o] * n + c];
+#pragma unroll
+                for (int o = 0; o < NQ; o++) gF[o] -= lam[o];
+                const double a2 = W[1][0], a1 = 1.0 - a2;
+                rL = lam[4] * (a1 * W[1][5]) + lam[5] * (a2 * W[1][6]) - lam[7] * a2;
+            }
+            if (f < len) {
+                int c;
+                line_cell<AXIS>(p, l, f, c);
+                double lam[NQ];
+#pragma unroll
+                for (int o = 0; o < NQ; o++) lam[o] = Gout[gmap[o] * n + c];
+#pragma unroll
+                for (int o = 0; o < NQ; o++) gF[o] += lam[o];
+                const double a2 = W[2][0], a1 = 1.0 - a2;
+                rR = lam[4] * (a1 * W[2][5]) + lam[5] * (a2 * W[2][6]) - lam[7] * a2;
+            }
+#pragma unroll
+            for (int o = 0; o < NQ; o++) gF[o] *= dtdx;
+            gF[8] = dtdx * (rR - rL);
+        }
+        double wlb[7], wrb[7];
+        fw[28 * (size_t)nf + fid] = face_pass(p, wl, wr, 0, gF, wlb);
+        face_pass(p, wl, wr, 1, gF, wrb);
+        // transposed reconstruction
+        double Wb[4][7];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int j = 0; j < 7; j++) Wb[k][j] = 0.0;
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            const double h = (ob && j <= 2) ? 1.0 : 0.5;
+            // wl = W1 + h * (chosen slope)
+            if (cl[j] == 1) { Wb[1][j] += wlb[j] * (1.0 + h); Wb[0][j] -= h * wlb[j]; }
+            else if (cl[j] == 2) { Wb[1][j] += wlb[j] * (1.0 - h); Wb[2][j] += h * wlb[j]; }
+            else Wb[1][j] += wlb[j];
+            // wr = W2 - h * (chosen slope)
+            if (cr[j] == 1) { Wb[2][j] += wrb[j] * (1.0 - h); Wb[1][j] += h * wrb[j]; }
+            else if (cr[j] == 2) { Wb[2][j] += wrb[j] * (1.0 + h); Wb[3][j] -= h * wrb[j]; }
+            else Wb[2][j] += wrb[j];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int j = 0; j < 7; j++) fw[(size_t)(7 * k + j) * nf + fid] = Wb[k][j];
+    }
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_adj_sweep_cell(const DevParams p, const double *Uin, const double *Gout,
+                                                        const double *fw, double *Gin, double dtdx)
+{
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    const int gmap[NQ] = {0, 1, QN, QT, 4, 5, 6, 7};
+    const int n = p.n;
+    const int len = AXIS == 0 ? p.nx : p.ny, nlines = AXIS == 0 ? p.ny : p.nx;
+    const int nf = (len + 1) * nlines;
     const int bc = p.bc[AXIS];
     GRID_LOOP(c, n)
     {
         const int x = c % p.nx, y = c / p.nx;
-        const int i = AXIS == 0 ? x : y;
-        auto cell_of = [&](int pos) { return AXIS == 0 ? y * p.nx + pos : pos * p.nx + x; };
-        // adjoint and R.adjoint of line position pos (0 outside the line: ghosts are not updated)
-        auto lam_r = [&](int pos, double *lam) -> double {
-            if (pos < 0 || pos >= len) {
-#pragma unroll
-                for (int k = 0; k < NQ; k++) lam[k] = 0.0;
-                return 0.0;
-            }
-            const int cc = cell_of(pos);
-#pragma unroll
-            for (int k = 0; k < NQ; k++) lam[k] = Gout[gmap[k] * n + cc];
-            const double a2 = Uin[7 * n + cc], a1 = 1.0 - a2;
-            const double p1 = sg_p(p, 0, Uin[4 * n + cc], a1), p2 = sg_p(p, 1, Uin[5 * n + cc], a2);
-            return lam[4] * (a1 * p1) + lam[5] * (a2 * p2) - lam[7] * a2;
-        };
-        double li[NQ];
-        lam_r(i, li);
-        double acc[NQ];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) acc[k] = li[k];
-        double us_m = 0.0, us_p = 0.0;
+        const int i = AXIS == 0 ? x : y, l = AXIS == 0 ? y : x;
+        const int fbase = l * (len + 1);
+        double Wb[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         // faces whose stencil may contain line position i (windows shifted by
         // the period for a periodic axis; every face of a short line)
         const int nwin = len <= 8 ? 1 : (bc == DIM_BC_PERIODIC ? 3 : 1);
@@ -606,39 +722,39 @@ __global__ void __launch_bounds__(128) k_adj_sweep(const DevParams p, const doub
                 f1 = min(i + 2 + sh, len);
             }
             for (int f = f0; f <= f1; f++) {
-                int cells[4];
-                bool seed[4], any = false;
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const int src = line_map(f - 2 + k, len, bc);
-                    cells[k] = cell_of(src);
-                    seed[k] = src == i;
-                    any = any || seed[k];
+                    if (line_map(f - 2 + k, len, bc) != i) continue;
+#pragma unroll
+                    for (int j = 0; j < 7; j++) Wb[j] += fw[(size_t)(7 * k + j) * nf + fbase + f];
                 }
-                if (!any) continue;
-                double lamL[NQ], lamR[NQ];
-                const double rL = lam_r(f - 1, lamL), rR = lam_r(f, lamR);
-                double gF[9];
-#pragma unroll
-                for (int o = 0; o < NQ; o++) gF[o] = dtdx * (lamR[o] - lamL[o]);
-                gF[8] = dtdx * (rR - rL);
-                Dn<8> F[9];
-                face_eval<AXIS>(p, Uin, cells, seed, F);
-#pragma unroll
-                for (int o = 0; o < 9; o++) {
-#pragma unroll
-                    for (int k = 0; k < NQ; k++) acc[k] += gF[o] * F[o].d[k];
-                }
-                if (f == i) us_m = F[8].v;
-                if (f == i + 1) us_p = F[8].v;
             }
         }
-        // the cell's own R(U_i) (u*_{i+1/2} - u*_{i-1/2}) term:
-        // R.lam = lam4 a1 p1 + lam5 a2 p2 - lam7 a2, a_k p_k = (g_k-1) E_k - a_k g_k pinf_k
-        const double du = dtdx * (us_p - us_m);
-        acc[4] -= du * li[4] * p.gm1[0];
-        acc[5] -= du * li[5] * p.gm1[1];
-        acc[7] -= du * (li[4] * p.gpinf[0] - li[5] * p.gpinf[1] - li[7]);
+        double q[NQ], lam[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) {
+            q[k] = Uin[gmap[k] * n + c];
+            lam[k] = Gout[gmap[k] * n + c];
+        }
+        // transposed Jacobian of q -> W (line-local order)
+        Dn<8> qd[NQ], W[7];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) qd[k] = dseed<8>(q[k], k);
+        d_prims(p, qd, W);
+        double acc[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) {
+            double s = lam[k];
+#pragma unroll
+            for (int j = 0; j < 7; j++) s += Wb[j] * W[j].d[k];
+            acc[k] = s;
+        }
+        // R(U_i) (u*_{i+1/2} - u*_{i-1/2}): R.lam = lam4 a1 p1 + lam5 a2 p2 - lam7 a2,
+        // a_k p_k = (g_k-1) E_k - a_k g_k pinf_k
+        const double du = dtdx * (fw[28 * (size_t)nf + fbase + i + 1] - fw[28 * (size_t)nf + fbase + i]);
+        acc[4] -= du * lam[4] * p.gm1[0];
+        acc[5] -= du * lam[5] * p.gm1[1];
+        acc[7] -= du * (lam[4] * p.gpinf[0] - lam[5] * p.gpinf[1] - lam[7]);
 #pragma unroll
         for (int k = 0; k < NQ; k++) Gin[gmap[k] * n + c] = acc[k];
     }
@@ -1066,13 +1182,23 @@ cudaError_t adj_trelax(const DevParams &p, const double *Uin, double *G, cudaStr
     return cudaGetLastError();
 }
 
+// fw: FACE_ADJ_PLANES x (nx*ny + max(nx, ny)) doubles of workspace
 cudaError_t adj_sweep(const DevParams &p, int axis, const double *Uin, const double *Gout, double *Gin, double dtdx,
-                      cudaStream_t s)
+                      double *fw, cudaStream_t s)
 {
-    if (axis == 0) k_adj_sweep<0><<<grid_for(p.n, 128), 128, 0, s>>>(p, Uin, Gout, Gin, dtdx);
-    else k_adj_sweep<1><<<grid_for(p.n, 128), 128, 0, s>>>(p, Uin, Gout, Gin, dtdx);
+    const int len = axis == 0 ? p.nx : p.ny, nlines = axis == 0 ? p.ny : p.nx;
+    const int nf = (len + 1) * nlines;
+    if (axis == 0) {
+        k_adj_sweep_face<0><<<grid_for(nf, 128), 128, 0, s>>>(p, Uin, Gout, fw, dtdx);
+        k_adj_sweep_cell<0><<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, Gout, fw, Gin, dtdx);
+    } else {
+        k_adj_sweep_face<1><<<grid_for(nf, 128), 128, 0, s>>>(p, Uin, Gout, fw, dtdx);
+        k_adj_sweep_cell<1><<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, Gout, fw, Gin, dtdx);
+    }
     return cudaGetLastError();
 }
+
+int adj_face_planes() { return FACE_ADJ_PLANES; }
 
 // planes of the viscous adjoint: 11 work planes W[0..10] (V, mu, u0, w0, ub x2,
 // wb x2, u0b, w0b, Vb) + ab, mub = 13

@@ -21,7 +21,8 @@ namespace dimk {
 cudaError_t adj_prelax(const DevParams &p, const double *Uin, double *G, cudaStream_t s);
 cudaError_t adj_trelax(const DevParams &p, const double *Uin, double *G, cudaStream_t s);
 cudaError_t adj_sweep(const DevParams &p, int axis, const double *Uin, const double *Gout, double *Gin, double dtdx,
-                      cudaStream_t s);
+                      double *fw, cudaStream_t s);
+int adj_face_planes();
 cudaError_t adj_visc(const DevParams &p, int axis, const double *Uin, const double *hist, int M, const double *b,
                      double tau, const double *G, double *Gin, double *work, double *pbar, cudaStream_t s);
 cudaError_t adj_heat(const DevParams &p, const double *Uin, const double *hist, int N, const int *Ms,
@@ -219,7 +220,11 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
     TRY(ensure(w, GW_G, 2 * n8));
     const int wp = dimk::adj_visc_work_planes() > dimk::adj_heat_work_planes() ? dimk::adj_visc_work_planes()
                                                                                : dimk::adj_heat_work_planes();
-    TRY(ensure(w, GW_WORK, n * (size_t)wp));
+    // work planes of the parabolic adjoints, then the per-face adjoints of the sweeps
+    const size_t nfmax = n + (size_t)(p.nx > p.ny ? p.nx : p.ny);
+    const size_t nwork = n * (size_t)wp > nfmax * dimk::adj_face_planes() ? n * (size_t)wp
+                                                                          : nfmax * dimk::adj_face_planes();
+    TRY(ensure(w, GW_WORK, nwork));
     double *ck = w->buf[GW_CK], *seg = w->buf[GW_SEG], *stg = w->buf[GW_STG];
     double *G = w->buf[GW_G], *G2 = w->buf[GW_G] + n8, *work = w->buf[GW_WORK];
 
@@ -297,7 +302,7 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
                 case ST_TRELAX: TRY(dimk::adj_trelax(pf, in, G, s)); break;
                 case ST_SWEEP: {
                     const double dtdx = tau / (st[k].axis == 0 ? p.dx : p.dy);
-                    TRY(dimk::adj_sweep(pf, st[k].axis, in, G, G2, dtdx, s));
+                    TRY(dimk::adj_sweep(pf, st[k].axis, in, G, G2, dtdx, work, s));
                     double *tmp = G; G = G2; G2 = tmp;
                     break;
                 }
