@@ -124,10 +124,11 @@ def measured_peak():
 
 def flops_per_cell(kernel: str, wl) -> float:
     """Algorithmic FP64 operations per cell of one launch (+ - * / sqrt each
-    one; counted from the kernels' formulas; see the design notes)."""
+    one, as the plain FP64 statement of the stage performs them)."""
     from paper_2106_00282_gb300 import flops
 
-    return flops.per_cell(kernel, wl.params)
+    ndim = 2 if wl.nx > 1 and wl.ny > 1 else 1
+    return flops.per_cell(kernel, wl.params, ndim=ndim)
 
 
 def aggregate(ms_local: float, units_per_rank: float, world: int, dev):
@@ -219,6 +220,26 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
     alg_bytes = 128.0 * ncell  # the 8-plane FP64 state read and written once per step
     step_us = 1e3 * ms_max / K
     hbm_frac = (alg_bytes / (step_us * 1e-6) / 1e9) / hbm if hbm else None
+    # DRAM bytes of a whole step from the recorded per-kernel traffic (ncu),
+    # when every kernel of the step has a record for the current kernels
+    dram_step = 0.0
+    try:
+        with open(TRAFFIC) as f:
+            trw = json.load(f).get(args.workload, {})
+        for name, v in kern.items():
+            if name == "copy":
+                continue
+            e = trw.get(name)
+            if not e or e.get("kernel_hash") != kernel_hash():
+                dram_step = None
+                break
+            dram_step += e["bytes_per_launch"] * v["launches"] / K
+    except Exception:
+        dram_step = None
+    hbm_obj = {"peak_gbs": hbm, "alg_bytes_per_step": alg_bytes,
+               "eta_alg": hbm_frac,
+               "dram_bytes_per_step": dram_step,
+               "eta_dram": (dram_step / (step_us * 1e-6) / 1e9) / hbm if (hbm and dram_step) else None}
 
     # end to end: host buffers through dim_step_host (copies inside the timed region)
     e2e = None
@@ -238,7 +259,7 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
                "h2d_bytes_per_step": int(Uh.numel() * 8), "d2h_bytes_per_step": int(Uh.numel() * 8),
                "steps": Ke, "api": "dim_step_host (pinned host state, H2D + step + D2H per step)"}
     return dict(value=value, ms_per_step=step_us / 1e3, wl=wl, roofline=roofline, e2e=e2e, clocks=clocks,
-                launches=launches, hbm_frac=hbm_frac, status_warmup=st0)
+                launches=launches, hbm_frac=hbm_frac, hbm=hbm_obj, status_warmup=st0)
 
 
 def run_batched(dev, world=1, steps=10, warmup=3):
@@ -370,7 +391,8 @@ def main():
                 "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": dict(workload_desc(wl), parallelism=f"replicas{world}" if world > 1 else "single"),
-                "hbm_roofline_frac_alg": r["hbm_frac"], "roofline": r["roofline"], "cpu_baseline": cpu,
+                "hbm_roofline_frac_alg": r["hbm_frac"], "hbm": r["hbm"], "roofline": r["roofline"],
+                "cpu_baseline": cpu,
                 "e2e": r["e2e"], "clocks": r["clocks"], "gpu_launches": r["launches"]}
         if rb is not None:
             line["batched"] = rb

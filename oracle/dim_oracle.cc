@@ -136,6 +136,35 @@ typedef DualT<long double> DualL;
 static inline double val(double x) { return x; }
 static inline bool is_nan(double x) { return isnan(x); }
 
+/* Operation counting (test infrastructure): a double that counts the
+ * floating-point operations applied to state-dependent values -- + and -,
+ * *, /, sqrt, pow; comparisons, min/max, abs and selects are free -- so that
+ * running a stage once on it counts the stage's algorithmic work. */
+static unsigned long long g_ops[5]; /* add/sub, mul, div, sqrt, pow */
+struct Cnt {
+    double v;
+    Cnt() = default;
+    Cnt(double x) : v(x) {}
+    friend Cnt operator+(Cnt a, Cnt b) { g_ops[0]++; return Cnt(a.v + b.v); }
+    friend Cnt operator-(Cnt a, Cnt b) { g_ops[0]++; return Cnt(a.v - b.v); }
+    friend Cnt operator-(Cnt a) { return Cnt(-a.v); }
+    friend Cnt operator*(Cnt a, Cnt b) { g_ops[1]++; return Cnt(a.v * b.v); }
+    friend Cnt operator/(Cnt a, Cnt b) { g_ops[2]++; return Cnt(a.v / b.v); }
+    friend Cnt &operator+=(Cnt &a, Cnt b) { a = a + b; return a; }
+    friend Cnt &operator-=(Cnt &a, Cnt b) { a = a - b; return a; }
+    friend bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
+    friend bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
+    friend bool operator<=(Cnt a, Cnt b) { return a.v <= b.v; }
+    friend bool operator>=(Cnt a, Cnt b) { return a.v >= b.v; }
+    friend Cnt sqrt(Cnt a) { g_ops[3]++; return Cnt(std::sqrt(a.v)); }
+    friend Cnt fabs(Cnt a) { return Cnt(std::fabs(a.v)); }
+    friend Cnt fmin(Cnt a, Cnt b) { return b.v < a.v ? b : a; }
+    friend Cnt fmax(Cnt a, Cnt b) { return b.v > a.v ? b : a; }
+    friend Cnt pow(Cnt a, double e) { g_ops[4]++; return Cnt(std::pow(a.v, e)); }
+    friend double val(Cnt x) { return x.v; }
+    friend bool is_nan(Cnt x) { return std::isnan(x.v); }
+};
+
 /* Branch record (test infrastructure for derivative checks): every value-decided
  * branch of the sweep -- the operand minmod returns, the Davis min / max, the
  * HLLC wave region -- can be recorded on one run and replayed on another, so
@@ -211,6 +240,21 @@ static prm<DualT<B>> make_prm_dual(const orc_params *P, const double *dp)
     q.p_fixed = P->p_fixed; q.p_min = P->p_min; q.p_max = P->p_max;
     return q;
 }
+template <>
+prm<Cnt> make_prm<Cnt>(const orc_params *P, const double *)
+{
+    prm<Cnt> q;
+    for (int k = 0; k < 2; k++) {
+        q.gamma[k] = P->gamma[k]; q.pinf[k] = P->pinf[k]; q.cv[k] = P->cv[k];
+        q.k0[k] = Cnt(P->k0[k]); q.mu[k] = Cnt(P->mu[k]); q.src[k] = Cnt(P->src[k]);
+        q.bc[k] = P->bc[k];
+    }
+    q.k_exp = P->k_exp; q.T_ref = P->T_ref; q.cfl = P->cfl;
+    q.limiter = P->limiter; q.trelax = P->trelax; q.n_outer = P->n_outer; q.p_policy = P->p_policy;
+    q.p_fixed = P->p_fixed; q.p_min = P->p_min; q.p_max = P->p_max;
+    return q;
+}
+
 template <>
 prm<Dual> make_prm<Dual>(const orc_params *P, const double *dp)
 {
@@ -758,6 +802,7 @@ struct orc_op {
     int bc[2];
     R *lx, *ly;
     double idx2, idy2; /* the 1/h^2 factors of Eq. (qk_dis), formed once per grid */
+    int only;          /* -1: both axes; 0 / 1: the operator along x / y only (viscous step) */
 };
 
 template <typename R>
@@ -767,6 +812,7 @@ static void op_init(orc_op<R> *o, int nx, int ny, double dx, double dy, const in
     o->bc[0] = bc[0]; o->bc[1] = bc[1];
     o->idx2 = 1.0 / (dx * dx);
     o->idy2 = 1.0 / (dy * dy);
+    o->only = -1;
     o->lx = (R *)malloc(sizeof(R) * (nx + 1) * ny);
     o->ly = (R *)malloc(sizeof(R) * nx * (ny + 1));
 }
@@ -778,13 +824,13 @@ static void op_apply(const orc_op<R> *o, const R *v, R *out)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             R r = 0.0;
-            if (nx > 1) {
+            if (nx > 1 && o->only != 1) {
                 int il = i == 0 ? nx - 1 : i - 1, ir = i == nx - 1 ? 0 : i + 1;
                 R fl = o->lx[j * (nx + 1) + i] * (v[j * nx + i] - v[j * nx + il]) * o->idx2;
                 R fr = o->lx[j * (nx + 1) + i + 1] * (v[j * nx + ir] - v[j * nx + i]) * o->idx2;
                 r += fr - fl;
             }
-            if (ny > 1) {
+            if (ny > 1 && o->only != 0) {
                 int jl = j == 0 ? ny - 1 : j - 1, jr = j == ny - 1 ? 0 : j + 1;
                 R fl = o->ly[j * nx + i] * (v[j * nx + i] - v[jl * nx + i]) * o->idy2;
                 R fr = o->ly[(j + 1) * nx + i] * (v[jr * nx + i] - v[j * nx + i]) * o->idy2;
@@ -800,7 +846,9 @@ template <typename R>
 static void op_faces(orc_op<R> *o, const R *lam)
 {
     int nx = o->nx, ny = o->ny;
-    for (int j = 0; j < ny; j++)
+    if (o->only == 1) memset(o->lx, 0, sizeof(R) * (nx + 1) * ny);
+    if (o->only == 0) memset(o->ly, 0, sizeof(R) * nx * (ny + 1));
+    for (int j = 0; j < ny && o->only != 1; j++)
         for (int i = 0; i <= nx; i++) {
             R v;
             if (i == 0 || i == nx)
@@ -809,7 +857,7 @@ static void op_faces(orc_op<R> *o, const R *lam)
                 v = 0.5 * (lam[j * nx + i - 1] + lam[j * nx + i]);
             o->lx[j * (nx + 1) + i] = v;
         }
-    for (int j = 0; j <= ny; j++)
+    for (int j = 0; j <= ny && o->only != 0; j++)
         for (int i = 0; i < nx; i++) {
             R v;
             if (j == 0 || j == ny)
@@ -830,8 +878,8 @@ static double op_lam_max(const orc_op<R> *o, const R *V)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             R s = 0.0;
-            if (nx > 1) s += (o->lx[j * (nx + 1) + i] + o->lx[j * (nx + 1) + i + 1]) * o->idx2;
-            if (ny > 1) s += (o->ly[j * nx + i] + o->ly[(j + 1) * nx + i]) * o->idy2;
+            if (nx > 1 && o->only != 1) s += (o->lx[j * (nx + 1) + i] + o->lx[j * (nx + 1) + i + 1]) * o->idx2;
+            if (ny > 1 && o->only != 0) s += (o->ly[j * nx + i] + o->ly[(j + 1) * nx + i]) * o->idy2;
             double r = val(2.0 * V[j * nx + i] * s);
             if (r > lm) lm = r;
         }
@@ -1031,16 +1079,11 @@ static unsigned viscous_t(const prm<R> *P, int nx, int ny, double dx, double dy,
     op_init(&o, nx, ny, dx, dy, P->bc);
     op_init(&ot, nx, ny, dx, dy, P->bc);
     double ih = 1.0 / h; /* the 1/dx factor of the face fluxes of Sec. 3.2, formed once */
+    /* both operators act along the sweep axis only */
+    o.only = axis;
+    ot.only = axis;
     op_faces(&o, ln);
     op_faces(&ot, mu);
-    /* restrict both operators to the sweep axis */
-    if (axis == 0) {
-        memset(o.ly, 0, sizeof(R) * nx * (ny + 1));
-        memset(ot.ly, 0, sizeof(R) * nx * (ny + 1));
-    } else {
-        memset(o.lx, 0, sizeof(R) * (nx + 1) * ny);
-        memset(ot.lx, 0, sizeof(R) * (nx + 1) * ny);
-    }
     double lm = lam_of(op_lam_max(&o, V), lam_io, replay);
     int Pn = cheb_P_viscous(P, tau, lm);
     unsigned st = Pn < cheb_P_formula(tau, lm) ? ORC_PCAP : 0u;
@@ -1263,6 +1306,36 @@ extern "C" unsigned orc_step_tangent_ext(const orc_params *P, const double *dpar
                                          const unsigned char *tape, size_t tape_len)
 {
     return tangent_run<DualL>(P, dparams, nx, ny, dx, dy, U, dU, nsteps, sched, tape, tape_len);
+}
+
+/* Operation counts of one stage on state U (test infrastructure): stage 0 CFL
+ * maximum, 1 / 2 sweep along x / y, 3 pressure relaxation, 4 temperature
+ * relaxation, 5 heat conduction (P by the parameters' policy), 6 / 7 viscous
+ * step along x / y.  out[0..4] = additions and subtractions, multiplications,
+ * divisions, square roots, powers; returns the Chebyshev P used (or 0). */
+extern "C" int orc_count_ops(const orc_params *P, int nx, int ny, double dx, double dy, const double *U, int stage,
+                             double tau, unsigned long long *out)
+{
+    prm<Cnt> Pc = make_prm<Cnt>(P, NULL);
+    size_t m = (size_t)NQ * nx * ny;
+    Cnt *X = (Cnt *)malloc(sizeof(Cnt) * m);
+    for (size_t i = 0; i < m; i++) X[i] = Cnt(U[i]);
+    for (int k = 0; k < 5; k++) g_ops[k] = 0;
+    int Pn = 0;
+    switch (stage) {
+    case 0: (void)wave_max(&Pc, nx, ny, dx, dy, X); break;
+    case 1: sweep_t(&Pc, nx, ny, dx, dy, 0, tau, X); break;
+    case 2: sweep_t(&Pc, nx, ny, dx, dy, 1, tau, X); break;
+    case 3: prelax_t(&Pc, nx * ny, X); break;
+    case 4: trelax_t(&Pc, nx * ny, X); break;
+    case 5: heat_t(&Pc, nx, ny, dx, dy, tau, X, &Pn, NULL, 0); break;
+    case 6: viscous_t(&Pc, nx, ny, dx, dy, 0, tau, X, &Pn, NULL, 0); break;
+    case 7: viscous_t(&Pc, nx, ny, dx, dy, 1, tau, X, &Pn, NULL, 0); break;
+    default: break;
+    }
+    for (int k = 0; k < 5; k++) out[k] = g_ops[k];
+    free(X);
+    return Pn;
 }
 
 /* diagnostics used by the tests: per-cell phase pressures and temperatures */

@@ -83,6 +83,8 @@ def lib():
         L.orc_viscous.argtypes = [P, i, i, d, d, i, d, _D, C.POINTER(i)]; L.orc_viscous.restype = u
         L.orc_step.argtypes = [P, i, i, d, d, _D, i, d, _D, C.POINTER(i)]; L.orc_step.restype = u
         L.orc_step_sched.argtypes = [P, i, i, d, d, _D, i, _D, i]; L.orc_step_sched.restype = u
+        L.orc_count_ops.argtypes = [P, i, i, d, d, _D, i, d, C.POINTER(C.c_ulonglong)]
+        L.orc_count_ops.restype = i
         L.orc_step_frozen.argtypes = [P, i, i, d, d, _D, i, _D, C.c_void_p, C.c_size_t, i, C.POINTER(C.c_size_t)]
         L.orc_step_frozen.restype = u
         L.orc_step_tangent.argtypes = [P, _D, i, i, d, d, _D, _D, i, _D]; L.orc_step_tangent.restype = u
@@ -241,6 +243,23 @@ def step_tangent_ext(params, U, dU, dx, dy, nsteps, frozen, dparams=None):
     if st & 64:
         raise ValueError("branch record does not match the extended run")
     return U, dU, st
+
+
+COUNT_STAGES = {"wave_max": 0, "sweep_x": 1, "sweep_y": 2, "prelax": 3, "trelax": 4, "heat": 5, "viscous_x": 6,
+                "viscous_y": 7}
+
+
+def count_ops(params, U, dx, dy, stage, tau=0.0):
+    """Floating-point operations one stage applies to state-dependent values:
+    dict(add, mul, div, sqrt, pow, total, P)."""
+    U = _state(U)
+    out = (C.c_ulonglong * 5)()
+    Pn = lib().orc_count_ops(C.byref(_params(params)), U.shape[2], U.shape[1], dx, dy, _ptr(U), COUNT_STAGES[stage],
+                             tau, out)
+    c = dict(zip(("add", "mul", "div", "sqrt", "pow"), (int(x) for x in out)))
+    c["total"] = sum(c[k] for k in ("add", "mul", "div", "sqrt", "pow"))
+    c["P"] = Pn
+    return c
 
 
 def cheb_P(params, tau, lam_max) -> int:

@@ -1,47 +1,54 @@
-"""Algorithmic FP64 operation counts per cell for each kernel of the step.
+"""Algorithmic FP64 operations per cell for each kernel of the step.
 
-Counted from the formulas the kernels evaluate (one + - * / or sqrt = one
-operation; comparisons, min/max and selects are free).  Face quantities are
-counted once per face (one face per cell and axis); halo recomputation inside a
-tile is not algorithmic work and is not counted.
+The algorithmic work of a stage is what the plain FP64 statement of the method
+performs: the oracle run once on an operation-counting scalar type, counting
++ - * / sqrt and powers on state-dependent values (comparisons, min/max, abs
+and selects are free; operations on constants are not counted), per cell in
+the limit of a large grid (ghost cells of the sweeps and boundary faces
+excluded).  tests/test_flops.py checks every entry below against that count.
 
-hyperbolic sweep (one axis), per cell:
-  primitives (alpha_1, rho, u_n, u_t, p_1, p_2)                          10
-  minmod slopes (2 differences x 7) + face values (2 sides x 7 x 2)       42
-  face states, 2 sides x (E_k, p, c^2 = (a1 A1 + a2 A2)/rho, rho u, rho E) 58
-  HLLC: S_L, S_R, S*, star state, flux                                    53
-  Godunov update with the R term                                          37
-  pressure relaxation (quadratic, alpha, p from rho E, E_k)               65
-                                                                  total  265
-CFL wave-speed maximum, per cell                                          24
-heat stage (temperature relaxation fused), per cell:
-  equilibrium 28 + energies 10 + temperature 10 + coefficients 28 = 76 (A)
-  Gershgorin bound 13 (B); per predictor sweep 19 (C, 2P - 2 of them);
-  conservative last sweep + projection + check 63 (D)     total 152 + 19 (2P - 2)
-viscous stage (one axis), per cell:
-  velocities 4, bound 13, per predictor sweep 24 (two fields), fluxes 18,
-  conservative update 48, + 65 when the pressure relaxation is fused
-                                                 total 83 (+65) + 24 (2P - 2)
+per cell                                   1D      2D
+  sweep, one axis (no limiter / minmod / Overbee)   201 / 215 / 218
+  pressure relaxation (Sec. 3.3)                    62
+  temperature relaxation (Sec. 3.4.1)               36
+  CFL maximum                              21      24
+  heat stage (Sec. 3.4.2), P = 1           96      105   (+4 with a power-law conductivity)
+  heat, per Chebyshev predictor sweep      16      24
+  viscous stage, one axis, P = 1                    104
+  viscous, per Chebyshev predictor sweep            30   (two velocity fields)
+
+The kernels fuse stages: a sweep kernel applies the pressure relaxation to
+its output, the heat kernel starts with the temperature relaxation, the
+viscous kernel of the last axis ends with the pressure relaxation.
 """
 from __future__ import annotations
 
-SWEEP = 265
-WAVE = 24
-HEAT_BASE, HEAT_SWEEP = 152, 19
-VISC_BASE, VISC_SWEEP, PRELAX = 83, 24, 65
+SWEEP = {0: 201, 1: 215, 2: 218}   # by limiter: none, minmod, Overbee
+PRELAX = 62
+TRELAX = 36
+WAVE = {1: 21, 2: 24}              # by number of active axes
+HEAT_BASE = {1: 96, 2: 105}
+HEAT_POWER_LAW = 4
+HEAT_SWEEP = {1: 16, 2: 24}
+VISC_BASE = 104
+VISC_SWEEP = 30
 
 
-def per_cell(kernel: str, params, P: int = 1) -> float:
+def per_cell(kernel: str, params, P: int = 1, ndim: int = 2) -> float:
+    """Algorithmic FP64 operations per cell of one launch of `kernel` (the
+    names bench.py and dim_kernel_time use) with P Chebyshev parameters."""
+    lim = params.limiter if params.limiter in SWEEP else 1
     if kernel in ("sweep_x", "sweep_y"):
-        return float(SWEEP)
+        return float(SWEEP[lim] + PRELAX)
     if kernel == "wave_max":
-        return float(WAVE)
+        return float(WAVE[ndim])
     if kernel == "heat":
-        return float(HEAT_BASE + HEAT_SWEEP * (2 * P - 2))
+        law = HEAT_POWER_LAW if params.k_exp != 0.0 else 0
+        return float(TRELAX + HEAT_BASE[ndim] + law + HEAT_SWEEP[ndim] * (2 * P - 2))
     if kernel == "viscous_x":
-        return float(VISC_BASE + VISC_SWEEP * (2 * P - 2))
+        return float(VISC_BASE + VISC_SWEEP * (2 * P - 2) + (PRELAX if ndim == 1 else 0))
     if kernel == "viscous_y":
-        return float(VISC_BASE + PRELAX + VISC_SWEEP * (2 * P - 2))
+        return float(VISC_BASE + VISC_SWEEP * (2 * P - 2) + PRELAX)
     if kernel == "relax":
         return float(PRELAX)
     raise ValueError(kernel)
