@@ -227,30 +227,6 @@ __device__ __forceinline__ Dn<N> d_sgE(const DevParams &p, int k, const Dn<N> &p
 {
     return ak * (pr + p.gpinf[k]) * p.inv_gm1[k];
 }
-template <int N>
-__device__ __forceinline__ Dn<N> d_sgA(const DevParams &p, int k, const Dn<N> &pr)
-{
-    return p.g[k] * (pr + p.pinf[k]);
-}
-
-// mixture sound speed c = sqrt((a1 A1 + a2 A2) / rho) (Sec. 3.1, Eq. AK)
-template <int N>
-__device__ __forceinline__ Dn<N> d_mixc(const DevParams &p, const Dn<N> &a1, const Dn<N> &p1, const Dn<N> &a2,
-                                       const Dn<N> &p2, const Dn<N> &rho)
-{
-    return dsqrt((a1 * d_sgA(p, 0, p1) + a2 * d_sgA(p, 1, p2)) / rho);
-}
-
-// minmod with the operand choice of the forward: the smaller magnitude when
-// both are nonzero with one sign (the second on a tie), else 0
-template <int N>
-__device__ __forceinline__ Dn<N> d_minmod(const Dn<N> &a, const Dn<N> &b)
-{
-    if (a.v > 0.0 && b.v > 0.0) return a.v < b.v ? a : b;
-    if (a.v < 0.0 && b.v < 0.0) return a.v > b.v ? a : b;
-    return dcst<N>(0.0);
-}
-
 // line-local conserved (m1, m2, rho u_n, rho u_t, E1, E2, rho E, alpha_2) ->
 // primitive (alpha_2, m1, m2, u_n, u_t, p1, p2)
 template <int N>
@@ -265,109 +241,6 @@ __device__ __forceinline__ void d_prims(const DevParams &p, const Dn<N> *q, Dn<N
     w[4] = q[3] / rho;
     w[5] = d_sgp(p, 0, q[4], a1);
     w[6] = d_sgp(p, 1, q[5], a2);
-}
-
-template <int N>
-struct DFace {
-    Dn<N> a2, un, ut, rho, p, c;
-    Dn<N> q[NQ];
-};
-
-template <int N>
-__device__ __forceinline__ void d_face_state(const DevParams &p, const Dn<N> *w, DFace<N> &s)
-{
-    Dn<N> a2 = w[0], a1 = 1.0 - a2;
-    Dn<N> m1 = w[1], m2 = w[2], un = w[3], ut = w[4], p1 = w[5], p2 = w[6];
-    Dn<N> rho = m1 + m2;
-    Dn<N> E1 = d_sgE(p, 0, p1, a1), E2 = d_sgE(p, 1, p2, a2);
-    s.a2 = a2;
-    s.un = un;
-    s.ut = ut;
-    s.rho = rho;
-    s.p = a1 * p1 + a2 * p2;
-    s.c = d_mixc(p, a1, p1, a2, p2, rho);
-    s.q[0] = m1;
-    s.q[1] = m2;
-    s.q[2] = rho * un;
-    s.q[3] = rho * ut;
-    s.q[4] = E1;
-    s.q[5] = E2;
-    s.q[6] = E1 + E2 + 0.5 * rho * (un * un + ut * ut);
-    s.q[7] = a2;
-}
-
-// HLLC face flux F[0..7] and u* = F[8] with the forward's branch rules
-template <int N>
-__device__ __forceinline__ void d_hllc(const DFace<N> &L, const DFace<N> &R, Dn<N> *F)
-{
-    Dn<N> sl1 = L.un - L.c, sl2 = R.un - R.c, sr1 = L.un + L.c, sr2 = R.un + R.c;
-    Dn<N> SL = sl2.v < sl1.v ? sl2 : sl1;
-    Dn<N> SR = sr2.v > sr1.v ? sr2 : sr1;
-    Dn<N> Ss = (R.p - L.p + L.rho * L.un * (SL - L.un) - R.rho * R.un * (SR - R.un)) /
-               (L.rho * (SL - L.un) - R.rho * (SR - R.un));
-    Dn<N> q[NQ], us, ps;
-    if (0.0 <= SL.v) {
-#pragma unroll
-        for (int k = 0; k < NQ; k++) q[k] = L.q[k];
-        us = L.un;
-        ps = L.p;
-    } else if (0.0 <= SR.v) {
-        const bool starL = 0.0 <= Ss.v;
-        const DFace<N> &K = starL ? L : R;
-        Dn<N> SK = starL ? SL : SR;
-        Dn<N> chi = (SK - K.un) / (SK - Ss);
-        q[0] = chi * K.q[0];
-        q[1] = chi * K.q[1];
-        q[2] = chi * K.rho * Ss;
-        q[3] = chi * K.rho * K.ut;
-        q[4] = chi * K.q[4];
-        q[5] = chi * K.q[5];
-        q[6] = chi * (K.q[6] + (Ss - K.un) * (K.rho * Ss + K.p / (SK - K.un)));
-        q[7] = K.a2;
-        us = Ss;
-        ps = K.p + K.rho * (SK - K.un) * (Ss - K.un);
-    } else {
-#pragma unroll
-        for (int k = 0; k < NQ; k++) q[k] = R.q[k];
-        us = R.un;
-        ps = R.p;
-    }
-    F[0] = us * q[0];
-    F[1] = us * q[1];
-    F[2] = us * q[2] + ps;
-    F[3] = us * q[3];
-    F[4] = us * q[4];
-    F[5] = us * q[5];
-    F[6] = us * (q[6] + ps);
-    F[7] = us * q[7];
-    F[8] = us;
-}
-
-// pressure relaxation (Sec. 3.3) of one cell, global plane order, in place
-template <int N>
-__device__ __forceinline__ void d_prelax(const DevParams &p, Dn<N> *q)
-{
-    const double g1 = p.g[0], g2 = p.g[1];
-    Dn<N> a2 = q[7], a1 = 1.0 - a2;
-    Dn<N> ak1 = p.gm1[0] * q[4], bk1 = p.gm1[0] * a1;
-    Dn<N> ak2 = p.gm1[1] * q[5], bk2 = p.gm1[1] * a2;
-    const double ek1 = p.gpinf[0], ek2 = p.gpinf[1];
-    Dn<N> A = g1 * g2 - bk1 * g2 - bk2 * g1;
-    Dn<N> B = g1 * ek2 + ek1 * g2 - (ak1 * g2 + bk1 * ek2 + ak2 * g1 + bk2 * ek1);
-    Dn<N> C = ek1 * ek2 - ak1 * ek2 - ak2 * ek1;
-    Dn<N> disc = B * B - 4.0 * A * C;
-    if (disc.v < 0.0) disc = dcst<N>(0.0);
-    Dn<N> sq = dsqrt(disc);
-    Dn<N> pr = B.v <= 0.0 ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
-    Dn<N> a2n = (ak2 + bk2 * pr) / (g2 * pr + ek2);
-    Dn<N> a1n = 1.0 - a2n;
-    Dn<N> rho = q[0] + q[1];
-    Dn<N> rhoe = q[6] - 0.5 * (q[2] * q[2] + q[3] * q[3]) / rho;
-    Dn<N> p2 = (rhoe - (a1n * p.g[0] * p.pinf[0] * p.inv_gm1[0] + a2n * p.g[1] * p.pinf[1] * p.inv_gm1[1])) /
-               (a1n * p.inv_gm1[0] + a2n * p.inv_gm1[1]);
-    q[4] = d_sgE(p, 0, p2, a1n);
-    q[5] = d_sgE(p, 1, p2, a2n);
-    q[7] = a2n;
 }
 
 // p,T equilibrium at fixed (m1, m2, rho e) (Sec. 3.4.1 / 3.4.2)
@@ -466,27 +339,72 @@ __device__ __forceinline__ void add_param(double *pbar, int k, double v)
 // ---------------------------------------------------------------------------
 // pointwise stages: Gin = J^T G in place (G: 8 planes)
 // ---------------------------------------------------------------------------
+// Pressure relaxation (Sec. 3.3) in reverse, per cell.  Forward: a_k(p) =
+// (ak_k + bk_k p)/(g_k p + ek_k) with ak_k = (g_k-1)E_k, bk_k = (g_k-1)a_k,
+// ek_k = g_k pinf_k; p the admissible root of A p^2 + B p + C = 0, hence
+// dp = -(p^2 dA + p dB + dC)/sqrt(disc); a2n = a_2(p); p2 from
+// rho e = rho E - |rho u|^2/(2 rho); E_k = a_kn (p2 + g_k pinf_k)/(g_k - 1).
+// The outputs are E_1, E_2, alpha_2; m_k, rho u, rho v, rho E pass through.
 __global__ void __launch_bounds__(256) k_adj_prelax(const DevParams p, const double *Uin, double *G)
 {
     const int n = p.n;
+    const double g1 = p.g[0], g2 = p.g[1], ek1 = p.gpinf[0], ek2 = p.gpinf[1];
+    const double i1 = p.inv_gm1[0], i2 = p.inv_gm1[1];
+    const double c1 = p.g[0] * p.pinf[0] * p.inv_gm1[0], c2 = p.g[1] * p.pinf[1] * p.inv_gm1[1];
     GRID_LOOP(c, n)
     {
-        Dn<8> q[NQ];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) q[k] = dseed<8>(Uin[k * n + c], k);
-        d_prelax(p, q);
-        double g[NQ], r[NQ];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) g[k] = G[k * n + c];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) {
-            double s = 0.0;
-#pragma unroll
-            for (int j = 0; j < NQ; j++) s += g[j] * q[j].d[k];
-            r[k] = s;
-        }
-#pragma unroll
-        for (int k = 0; k < NQ; k++) G[k * n + c] = r[k];
+        const double m1 = Uin[c], m2 = Uin[n + c], mu = Uin[2 * n + c], mv = Uin[3 * n + c];
+        const double E1 = Uin[4 * n + c], E2 = Uin[5 * n + c], rE = Uin[6 * n + c], a2 = Uin[7 * n + c];
+        // forward values (the operation order of the forward relaxation)
+        const double a1 = 1.0 - a2;
+        const double ak1 = p.gm1[0] * E1, bk1 = p.gm1[0] * a1, ak2 = p.gm1[1] * E2, bk2 = p.gm1[1] * a2;
+        const double A = g1 * g2 - bk1 * g2 - bk2 * g1;
+        const double B = g1 * ek2 + ek1 * g2 - (ak1 * g2 + bk1 * ek2 + ak2 * g1 + bk2 * ek1);
+        const double C = ek1 * ek2 - ak1 * ek2 - ak2 * ek1;
+        double disc = B * B - 4.0 * A * C;
+        if (disc < 0.0) disc = 0.0;
+        const double sq = sqrt(disc);
+        const double pr = B <= 0.0 ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
+        const double Xa = ak2 + bk2 * pr, Ya = g2 * pr + ek2;
+        const double a2n = Xa / Ya, a1n = 1.0 - a2n;
+        const double rho = m1 + m2;
+        const double ke = 0.5 * (mu * mu + mv * mv) / rho;
+        const double rhoe = rE - ke;
+        const double Nn = rhoe - (a1n * c1 + a2n * c2), Dd = a1n * i1 + a2n * i2;
+        const double p2 = Nn / Dd;
+        // reverse
+        const double G4 = G[4 * n + c], G5 = G[5 * n + c], G7 = G[7 * n + c];
+        const double p2b = G4 * a1n * i1 + G5 * a2n * i2;
+        double a1nb = G4 * (p2 + ek1) * i1;
+        double a2nb = G5 * (p2 + ek2) * i2 + G7;
+        const double Nb = p2b / Dd, Db = -p2b * p2 / Dd;
+        const double rhoeb = Nb;
+        a1nb += -Nb * c1 + Db * i1;
+        a2nb += -Nb * c2 + Db * i2;
+        a2nb -= a1nb;
+        const double rEb = rhoeb;
+        const double mub = -rhoeb * mu / rho, mvb = -rhoeb * mv / rho;
+        const double rhob = rhoeb * ke / rho;
+        const double Xb = a2nb / Ya, Yb = -a2nb * a2n / Ya;
+        double ak2b = Xb, bk2b = Xb * pr;
+        const double prb = Xb * bk2 + Yb * g2;
+        const double Ab = -prb * pr * pr / sq, Bb = -prb * pr / sq, Cb = -prb / sq;
+        double bk1b = -Ab * g2;
+        bk2b += -Ab * g1;
+        double ak1b = -Bb * g2;
+        bk1b += -Bb * ek2;
+        ak2b += -Bb * g1;
+        bk2b += -Bb * ek1;
+        ak1b += -Cb * ek2;
+        ak2b += -Cb * ek1;
+        G[c] += rhob;
+        G[n + c] += rhob;
+        G[2 * n + c] += mub;
+        G[3 * n + c] += mvb;
+        G[4 * n + c] = ak1b * p.gm1[0];
+        G[5 * n + c] = ak2b * p.gm1[1];
+        G[6 * n + c] += rEb;
+        G[7 * n + c] = -bk1b * p.gm1[0] + bk2b * p.gm1[1];
     }
 }
 
@@ -560,30 +478,212 @@ __device__ __forceinline__ int mm_choice(double a, double b)
     return 0;
 }
 
-// one dual pass over the face: seed = 0 differentiates w.r.t. wl, 1 w.r.t. wr;
-// returns sum_o gbar_o dF_o/dw
-__device__ __forceinline__ double face_pass(const DevParams &p, const double *wl, const double *wr, int seed,
-                                            const double *gF, double *wbar)
+// A face state of Eq. (vectorForm) from reconstructed primitives (values, the
+// forward's operation order) and its reverse: the adjoints of (q[8], u_n, p,
+// c, rho) -> the adjoint of w = (alpha_2, m1, m2, u_n, u_t, p1, p2).
+struct FaceV {
+    double a2, a1, m1, m2, un, ut, p1, p2, rho, E1, E2, p, A1, A2, X, c;
+    double q[NQ];
+};
+
+__device__ __forceinline__ void face_fwd(const DevParams &p, const double *w, FaceV &s)
 {
-    Dn<7> a[7], b[7];
+    s.a2 = w[0];
+    s.a1 = 1.0 - s.a2;
+    s.m1 = w[1];
+    s.m2 = w[2];
+    s.un = w[3];
+    s.ut = w[4];
+    s.p1 = w[5];
+    s.p2 = w[6];
+    s.rho = s.m1 + s.m2;
+    s.E1 = sg_E(p, 0, s.p1, s.a1);
+    s.E2 = sg_E(p, 1, s.p2, s.a2);
+    s.p = s.a1 * s.p1 + s.a2 * s.p2;
+    s.A1 = sg_A(p, 0, s.p1);
+    s.A2 = sg_A(p, 1, s.p2);
+    s.X = s.a1 * s.A1 + s.a2 * s.A2;
+    s.c = sqrt(s.X / s.rho);
+    s.q[0] = s.m1;
+    s.q[1] = s.m2;
+    s.q[2] = s.rho * s.un;
+    s.q[3] = s.rho * s.ut;
+    s.q[4] = s.E1;
+    s.q[5] = s.E2;
+    s.q[6] = s.E1 + s.E2 + 0.5 * s.rho * (s.un * s.un + s.ut * s.ut);
+    s.q[7] = s.a2;
+}
+
+// qb: adjoint of q[8]; unb, utb, pb, cb, rhob: direct adjoints of u_n, u_t, p,
+// c, rho
+__device__ __forceinline__ void face_rev(const DevParams &p, const FaceV &s, const double *qb, double unb,
+                                         double utb, double pb, double cb, double rhob, double *wb)
+{
+    double m1b = qb[0], m2b = qb[1], E1b = qb[4], E2b = qb[5], a2b = qb[7], a1b = 0.0;
+    double p1b = 0.0, p2b = 0.0;
+    // q2 = rho un, q3 = rho ut
+    rhob += qb[2] * s.un + qb[3] * s.ut;
+    unb += qb[2] * s.rho;
+    utb += qb[3] * s.rho;
+    // q6 = E1 + E2 + rho (un^2 + ut^2)/2
+    E1b += qb[6];
+    E2b += qb[6];
+    rhob += qb[6] * 0.5 * (s.un * s.un + s.ut * s.ut);
+    unb += qb[6] * s.rho * s.un;
+    utb += qb[6] * s.rho * s.ut;
+    // c = sqrt(X / rho)
+    const double c2b = cb / (2.0 * s.c);
+    const double Xb = c2b / s.rho;
+    rhob -= c2b * (s.X / s.rho) / s.rho;
+    a1b += Xb * s.A1;
+    a2b += Xb * s.A2;
+    p1b += Xb * s.a1 * p.g[0];
+    p2b += Xb * s.a2 * p.g[1];
+    // p = a1 p1 + a2 p2
+    a1b += pb * s.p1;
+    a2b += pb * s.p2;
+    p1b += pb * s.a1;
+    p2b += pb * s.a2;
+    // E_k = a_k (p_k + g_k pinf_k) / (g_k - 1)
+    a1b += E1b * (s.p1 + p.gpinf[0]) * p.inv_gm1[0];
+    p1b += E1b * s.a1 * p.inv_gm1[0];
+    a2b += E2b * (s.p2 + p.gpinf[1]) * p.inv_gm1[1];
+    p2b += E2b * s.a2 * p.inv_gm1[1];
+    // rho = m1 + m2, a1 = 1 - a2
+    m1b += rhob;
+    m2b += rhob;
+    a2b -= a1b;
+    wb[0] = a2b;
+    wb[1] = m1b;
+    wb[2] = m2b;
+    wb[3] = unb;
+    wb[4] = utb;
+    wb[5] = p1b;
+    wb[6] = p2b;
+}
+
+// The HLLC flux of the face (the forward's branch rules) and its reverse:
+// gF = adjoint of (F[0..7], u*) -> adjoints of wl and wr; returns u*.
+__device__ __forceinline__ double face_reverse(const DevParams &p, const double *wl, const double *wr,
+                                               const double *gF, double *wlb, double *wrb)
+{
+    FaceV L, R;
+    face_fwd(p, wl, L);
+    face_fwd(p, wr, R);
+    const double sl1 = L.un - L.c, sl2 = R.un - R.c, sr1 = L.un + L.c, sr2 = R.un + R.c;
+    const bool slR = sl2 < sl1, srR = sr2 > sr1;
+    const double SL = slR ? sl2 : sl1, SR = srR ? sr2 : sr1;
+    const double num = R.p - L.p + L.rho * L.un * (SL - L.un) - R.rho * R.un * (SR - R.un);
+    const double den = L.rho * (SL - L.un) - R.rho * (SR - R.un);
+    const double Ss = num / den;
+    const int region = 0.0 <= SL ? 0 : (0.0 <= SR ? (0.0 <= Ss ? 1 : 2) : 3);
+    double qb_L[NQ], qb_R[NQ];
 #pragma unroll
-    for (int j = 0; j < 7; j++) {
-        a[j] = seed == 0 ? dseed<7>(wl[j], j) : dcst<7>(wl[j]);
-        b[j] = seed == 1 ? dseed<7>(wr[j], j) : dcst<7>(wr[j]);
+    for (int k = 0; k < NQ; k++) qb_L[k] = qb_R[k] = 0.0;
+    double unLb = 0.0, unRb = 0.0, pLb = 0.0, pRb = 0.0, cLb = 0.0, cRb = 0.0, rhoLb = 0.0, rhoRb = 0.0;
+    double us;
+    if (region == 0 || region == 3) {
+        const FaceV &K = region == 0 ? L : R;
+        us = K.un;
+        double *qbK = region == 0 ? qb_L : qb_R;
+        double usb = gF[8] + gF[6] * (K.q[6] + K.p);
+#pragma unroll
+        for (int k = 0; k < NQ; k++) {
+            qbK[k] = gF[k] * us;
+            if (k != 6) usb += gF[k] * K.q[k];
+        }
+        // F2 = u* q2 + p*, F6 = u* (q6 + p*)
+        const double psb = gF[2] + gF[6] * us;
+        if (region == 0) { unLb += usb; pLb += psb; }
+        else { unRb += usb; pRb += psb; }
+        face_rev(p, L, qb_L, unLb, 0.0, pLb, cLb, rhoLb, wlb);
+        face_rev(p, R, qb_R, unRb, 0.0, pRb, cRb, rhoRb, wrb);
+        return us;
+    } else {
+        const bool kl = region == 1;
+        const FaceV &K = kl ? L : R;
+        const double SK = kl ? SL : SR;
+        const double t = SK - K.un, d2 = SK - Ss, chi = t / d2;
+        const double e = Ss - K.un, fv = K.rho * Ss + K.p / t, gv = K.q[6] + e * fv;
+        double q[NQ];
+        q[0] = chi * K.q[0];
+        q[1] = chi * K.q[1];
+        q[2] = chi * K.rho * Ss;
+        q[3] = chi * K.rho * K.ut;
+        q[4] = chi * K.q[4];
+        q[5] = chi * K.q[5];
+        q[6] = chi * gv;
+        q[7] = K.a2;
+        us = Ss;
+        const double ps = K.p + K.rho * t * e;
+        // flux
+        double qs_b[NQ];
+        double usb = gF[8] + gF[6] * (q[6] + ps);
+#pragma unroll
+        for (int k = 0; k < NQ; k++) {
+            qs_b[k] = gF[k] * us;
+            if (k != 6) usb += gF[k] * q[k];
+        }
+        const double psb = gF[2] + gF[6] * us;
+        // star state
+        double *qbK = kl ? qb_L : qb_R;
+        double rhoKb = 0.0, unKb = 0.0, utKb = 0.0, pKb = 0.0, Ssb = usb, tb = 0.0;
+        const double chib = qs_b[0] * K.q[0] + qs_b[1] * K.q[1] + qs_b[2] * K.rho * Ss + qs_b[3] * K.rho * K.ut +
+                            qs_b[4] * K.q[4] + qs_b[5] * K.q[5] + qs_b[6] * gv;
+        qbK[0] += qs_b[0] * chi;
+        qbK[1] += qs_b[1] * chi;
+        qbK[4] += qs_b[4] * chi;
+        qbK[5] += qs_b[5] * chi;
+        rhoKb += qs_b[2] * chi * Ss + qs_b[3] * chi * K.ut;
+        Ssb += qs_b[2] * chi * K.rho;
+        utKb += qs_b[3] * chi * K.rho;
+        const double gb = qs_b[6] * chi;
+        qbK[6] += gb;
+        const double eb1 = gb * fv, fb = gb * e;
+        rhoKb += fb * Ss;
+        Ssb += fb * K.rho;
+        pKb += fb / t;
+        tb -= fb * K.p / (t * t);
+        Ssb += eb1;
+        unKb -= eb1;
+        qbK[7] += qs_b[7];
+        // ps = pK + rhoK t e
+        pKb += psb;
+        rhoKb += psb * t * e;
+        tb += psb * K.rho * e;
+        const double eb2 = psb * K.rho * t;
+        Ssb += eb2;
+        unKb -= eb2;
+        // chi = t / d2, d2 = SK - Ss, t = SK - unK
+        const double d1b = chib / d2, d2b = -chib * chi / d2;
+        tb += d1b;
+        double SKb = d2b + tb;
+        Ssb -= d2b;
+        unKb -= tb;
+        // Ss = num / den
+        const double numb = Ssb / den, denb = -Ssb * Ss / den;
+        double SLb = 0.0, SRb = 0.0;
+        pRb += numb;
+        pLb -= numb;
+        rhoLb += numb * L.un * (SL - L.un) + denb * (SL - L.un);
+        unLb += numb * L.rho * (SL - 2.0 * L.un) - denb * L.rho;
+        SLb += numb * L.rho * L.un + denb * L.rho;
+        rhoRb -= numb * R.un * (SR - R.un) + denb * (SR - R.un);
+        unRb -= numb * R.rho * (SR - 2.0 * R.un) - denb * R.rho;
+        SRb -= numb * R.rho * R.un + denb * R.rho;
+        if (kl) SLb += SKb;
+        else SRb += SKb;
+        if (kl) { rhoLb += rhoKb; unLb += unKb; pLb += pKb; }
+        else { rhoRb += rhoKb; unRb += unKb; pRb += pKb; }
+        // Davis bounds: the operand each of S_L, S_R took
+        if (slR) { unRb += SLb; cRb -= SLb; }
+        else { unLb += SLb; cLb -= SLb; }
+        if (srR) { unRb += SRb; cRb += SRb; }
+        else { unLb += SRb; cLb += SRb; }
+        face_rev(p, L, qb_L, unLb, kl ? utKb : 0.0, pLb, cLb, rhoLb, wlb);
+        face_rev(p, R, qb_R, unRb, kl ? 0.0 : utKb, pRb, cRb, rhoRb, wrb);
+        return us;
     }
-    DFace<7> L, R;
-    d_face_state(p, a, L);
-    d_face_state(p, b, R);
-    Dn<7> F[9];
-    d_hllc(L, R, F);
-#pragma unroll
-    for (int j = 0; j < 7; j++) {
-        double s = 0.0;
-#pragma unroll
-        for (int o = 0; o < 9; o++) s += gF[o] * F[o].d[j];
-        wbar[j] = s;
-    }
-    return F[8].v;  // u* of the face
 }
 
 template <int AXIS>
@@ -667,8 +767,7 @@ __global__ void __launch_bounds__(128) k_adj_sweep_face(const DevParams p, const
             gF[8] = dtdx * (rR - rL);
         }
         double wlb[7], wrb[7];
-        fw[28 * (size_t)nf + fid] = face_pass(p, wl, wr, 0, gF, wlb);
-        face_pass(p, wl, wr, 1, gF, wrb);
+        fw[28 * (size_t)nf + fid] = face_reverse(p, wl, wr, gF, wlb, wrb);
         // transposed reconstruction
         double Wb[4][7];
 #pragma unroll
@@ -1036,25 +1135,37 @@ __global__ void __launch_bounds__(256) k_adj_heat_q(const DevParams p, const dou
     }
 }
 
-// one reverse predictor sweep: vprev = v^{m-1}
+// one reverse predictor sweep: vprev = v^{m-1}; y = vbar^m / (1 + tau b_m)
+// and z = V y are formed on the fly at the cell and its neighbours
 __global__ void __launch_bounds__(256) k_adj_heat_lim(const DevParams p, const double *V, const double *L,
                                                       const double *Ia, const double *vprev, const double *vbi,
                                                       double *vbo, double *T0b, double *Vb, double *Lb, double *Iab,
-                                                      double *z, double tau, double bm, double rden, int phase)
+                                                      double tau, double bm, double rden)
 {
     const int n = p.n;
-    if (phase == 0) {
-        // z = V y, y = vbar^m / (1 + tau b_m)
-        GRID_LOOP(c, n) z[c] = V[c] * (rden * vbi[c]);
-        return;
-    }
     GRID_LOOP(c, n)
     {
-        const double y = rden * vbi[c];
-        vbo[c] = tau * bm * y + tau * lap_v(p, c, z, L);
+        const double y = rden * vbi[c], zc = V[c] * y, Lc = L[c], vc = vprev[c];
+        double lz = 0.0, lv = 0.0, fl = 0.0;
+        for (int ax = 0; ax < 2; ax++) {
+            int cm, cp;
+            axis_nb(p, ax, c, cm, cp);
+            const double ih2 = ax == 0 ? p.idx2 : p.idy2;
+            for (int sd = 0; sd < 2; sd++) {
+                const int nb = sd == 0 ? cm : cp;
+                if (nb < 0) continue;
+                const double Lf = 0.5 * (L[nb] + Lc);
+                const double zn = V[nb] * (rden * vbi[nb]);
+                const double dv = vprev[nb] - vc;
+                lz += Lf * (zn - zc) * ih2;
+                lv += Lf * dv * ih2;
+                fl += (zc - zn) * dv * ih2;
+            }
+        }
+        vbo[c] = tau * bm * y + tau * lz;
         T0b[c] += y;
-        Vb[c] += tau * y * (lap_v(p, c, vprev, L) + Ia[c]);
-        Lb[c] += 0.5 * tau * face_lam_adj(p, c, z, vprev);
+        Vb[c] += tau * y * (lv + Ia[c]);
+        Lb[c] += 0.5 * tau * fl;
         Iab[c] += tau * V[c] * y;
     }
 }
@@ -1243,8 +1354,8 @@ cudaError_t adj_visc(const DevParams &p, int axis, const double *Uin, const doub
     return cudaGetLastError();
 }
 
-// planes of the heat adjoint: T0, T0b, V, L, Ia, qb, vb x2, Lb, Iab, Vb, Tb, ab, z
-constexpr int HEAT_WORK_PLANES = 14;
+// planes of the heat adjoint: T0, T0b, V, L, Ia, qb, vb x2, Lb, Iab, Vb, Tb, ab
+constexpr int HEAT_WORK_PLANES = 13;
 
 // Reverse of one heat-conduction stage (Algorithm 1, N outer iterations).
 // hist: per iteration it, 2 P_it planes (T_it, a_it, v^1..v^{M_it}); Ms[it] =
@@ -1256,7 +1367,7 @@ cudaError_t adj_heat(const DevParams &p, const double *Uin, const double *hist, 
     const size_t n = (size_t)p.n;
     double *T0 = work, *T0b = work + n, *V = work + 2 * n, *L = work + 3 * n, *Ia = work + 4 * n;
     double *qb = work + 5 * n, *vbA = work + 6 * n, *vbB = work + 7 * n, *Lb = work + 8 * n, *Iab = work + 9 * n;
-    double *Vb = work + 10 * n, *Tb = work + 11 * n, *ab = work + 12 * n, *z = work + 13 * n;
+    double *Vb = work + 10 * n, *Tb = work + 11 * n, *ab = work + 12 * n;
     const int gb = grid_for(p.n, 256);
     cudaError_t e;
     k_adj_heat_prep<<<gb, 256, 0, s>>>(p, Uin, T0, T0b);
@@ -1284,8 +1395,7 @@ cudaError_t adj_heat(const DevParams &p, const double *Uin, const double *hist, 
         double *vi = vbA, *vo = vbB;
         for (int m = M; m >= 1; m--) {
             const double bm = bs[boff[it] + m - 1], rden = 1.0 / (1.0 + tau * bm);
-            k_adj_heat_lim<<<gb, 256, 0, s>>>(p, V, L, Ia, v_of(m - 1), vi, vo, T0b, Vb, Lb, Iab, z, tau, bm, rden, 0);
-            k_adj_heat_lim<<<gb, 256, 0, s>>>(p, V, L, Ia, v_of(m - 1), vi, vo, T0b, Vb, Lb, Iab, z, tau, bm, rden, 1);
+            k_adj_heat_lim<<<gb, 256, 0, s>>>(p, V, L, Ia, v_of(m - 1), vi, vo, T0b, Vb, Lb, Iab, tau, bm, rden);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             double *t = vi; vi = vo; vo = t;
         }
