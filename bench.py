@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk variant")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched configuration")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (dim_grad) measurement")
+    ap.add_argument("--only-adjoint", action="store_true",
+                    help="run only the gradient measurement and print its JSON object (profiling)")
+    ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the gradient problem (default 200)")
+    ap.add_argument("--adjoint-ckpt", type=int, default=None, help="checkpoint spacing (default 20)")
+    ap.add_argument("--batch-ninst", type=int, default=256, help="instances of the batched configuration")
     return ap.parse_args()
 
 
@@ -262,7 +267,7 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
                 launches=launches, hbm_frac=hbm_frac, hbm=hbm_obj, status_warmup=st0)
 
 
-def run_batched(dev, world=1, steps=10, warmup=3):
+def run_batched(dev, world=1, steps=10, warmup=3, ninst=256):
     """256 independent water/air problems of uneven sizes (FP32 bulk), one
     persistent launch per step replayed from a CUDA graph; the packed state
     (4.1 GB) is larger than the L2, so no flush is needed."""
@@ -271,7 +276,7 @@ def run_batched(dev, world=1, steps=10, warmup=3):
     from paper_2106_00282_gb300 import inputs as I
     from paper_2106_00282_gb300.api import Batch
 
-    params, grids, prims = I.batch(ninst=256, seed=4)
+    params, grids, prims = I.batch(ninst=ninst, seed=4)
     B = Batch(params, grids)
     U = B.from_primitive(B.pack_primitive(prims))
     del prims
@@ -301,7 +306,7 @@ def run_batched(dev, world=1, steps=10, warmup=3):
     return out
 
 
-def run_adjoint(dev, world=1):
+def run_adjoint(dev, world=1, steps=None, ckpt=None):
     """The gradient problem on the conduction disc (512^2, FP64, 200 steps,
     checkpoints every 20): time of the forward run alone (dim_step) and of
     dim_grad (forward with checkpoints + reverse sweep with recomputation),
@@ -313,7 +318,8 @@ def run_adjoint(dev, world=1):
     from paper_2106_00282_gb300.api import Solver
 
     wl = I.disc_gradient()
-    nsteps, ckpt = wl.steps, wl.meta["ckpt"]
+    nsteps = steps or wl.steps
+    ckpt = ckpt or wl.meta["ckpt"]
     s = Solver(wl.params, wl.nx, wl.ny, wl.dx, wl.dy)
     U0 = s.from_primitive(torch.from_numpy(wl.prim).to(dev))
     g = torch.randn(U0.shape, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(5))
@@ -373,10 +379,20 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
+    if args.only_adjoint:
+        from paper_2106_00282_gb300 import build as cuda_build
+
+        cuda_build.build()
+        ra = run_adjoint(dev, world, args.adjoint_steps, args.adjoint_ckpt)
+        if rank == 0:
+            print(json.dumps({"adjoint": ra}))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     r = run_ours(args, rank, world, dev)
     r32 = None if args.no_fp32 else run_ours(args, rank, world, dev, precision=1, with_e2e=False)
-    rb = None if args.no_batch else run_batched(dev, world)
-    ra = None if args.no_adjoint else run_adjoint(dev, world)
+    rb = None if args.no_batch else run_batched(dev, world, ninst=args.batch_ninst)
+    ra = None if args.no_adjoint else run_adjoint(dev, world, args.adjoint_steps, args.adjoint_ckpt)
     if rank == 0:
         wl = r["wl"]
         cpu = None
