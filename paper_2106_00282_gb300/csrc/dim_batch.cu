@@ -81,7 +81,7 @@ __device__ void stage_wave(const BatchDev &d)
             for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
             st |= check_state(p, q);
             double a2 = q[7], a1 = 1.0 - a2;
-            float p1 = (float)sg_p(p, 0, q[4], a1), p2 = (float)sg_p(p, 1, q[5], a2);
+            float p1 = (float)sg_p<true>(p, 0, q[4], a1), p2 = (float)sg_p<true>(p, 1, q[5], a2);
             float rho = (float)(q[0] + q[1]);
             float cs = sqrtf(((float)a1 * f.g[0] * (p1 + f.pinf[0]) + (float)a2 * f.g[1] * (p2 + f.pinf[1])) / rho);
             float sx = (fabsf((float)q[2] / rho) + cs) * (float)p.idx;
@@ -294,7 +294,7 @@ __device__ bool stage_visc(const BatchDev &d, int relax)
             q[5] += tau * (aF2[1] * W[1] - aF2[0] * W[0]) * ih -
                     tau * (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) * ih;
             if (relax) {
-                unsigned r = prelax(p, q);
+                unsigned r = prelax<true>(p, q);
                 if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
                 st |= r & DIM_ST_NAN;
             }
@@ -327,7 +327,7 @@ __device__ bool stage_heat(const BatchDev &d)
         unsigned st = 0;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
             double m1 = U[c], m2 = U[n + c], T, a2;
-            unsigned r = equilibrium(p, m1, m2, U[4 * n + c] + U[5 * n + c], T, a2);
+            unsigned r = equilibrium<true>(p, m1, m2, U[4 * n + c] + U[5 * n + c], T, a2);
             if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
             st |= r & DIM_ST_NAN;
             U[4 * n + c] = m1 * p.cv[0] * T + (1.0 - a2) * p.pinf[0];
@@ -401,7 +401,7 @@ __device__ bool stage_heat(const BatchDev &d)
             double q = (double)lapf(p, neighbours(p, c), c, vin, L, idx2, idy2) + (double)F[5 * (size_t)n + c];
             double m1 = U[c], m2 = U[n + c];
             double T, a2;
-            unsigned r = equilibrium(p, m1, m2, U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
+            unsigned r = equilibrium<true>(p, m1, m2, U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
             double Q[NQ];
             Q[0] = m1;
             Q[1] = m2;
@@ -438,7 +438,7 @@ __device__ void stage_trelax(const BatchDev &d)
 #pragma unroll
             for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
             double T, a;
-            unsigned r = equilibrium(p, q[0], q[1], q[4] + q[5], T, a);
+            unsigned r = equilibrium<true>(p, q[0], q[1], q[4] + q[5], T, a);
             q[4] = q[0] * p.cv[0] * T + (1.0 - a) * p.pinf[0];
             q[5] = q[1] * p.cv[1] * T + a * p.pinf[1];
             q[7] = a;

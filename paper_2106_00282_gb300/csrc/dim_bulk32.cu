@@ -37,7 +37,7 @@ __global__ void k_wave_max32(const DevParams p, const double *__restrict__ U, Sc
         for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
         st |= check_state(p, q);
         double a2 = q[7], a1 = 1.0 - a2;
-        float p1 = (float)sg_p(p, 0, q[4], a1), p2 = (float)sg_p(p, 1, q[5], a2);
+        float p1 = (float)sg_p<true>(p, 0, q[4], a1), p2 = (float)sg_p<true>(p, 1, q[5], a2);
         float rho = (float)(q[0] + q[1]);
         float cs = sqrtf(((float)a1 * f.g[0] * (p1 + f.pinf[0]) + (float)a2 * f.g[1] * (p2 + f.pinf[1])) / rho);
         if (p.nx > 1) {
@@ -71,14 +71,14 @@ __global__ void __launch_bounds__(256) k_heat32(const DevParams p, double *U, He
         double m1 = U[c], m2 = U[n + c], E1 = U[4 * n + c], E2 = U[5 * n + c], a2 = U[7 * n + c];
         double T;
         if (trelax_first) {
-            unsigned r = equilibrium(p, m1, m2, E1 + E2, T, a2);
+            unsigned r = equilibrium<true>(p, m1, m2, E1 + E2, T, a2);
             if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
             st |= r & DIM_ST_NAN;
             U[4 * n + c] = m1 * p.cv[0] * T + (1.0 - a2) * p.pinf[0];
             U[5 * n + c] = m2 * p.cv[1] * T + a2 * p.pinf[1];
             U[7 * n + c] = a2;
         } else {
-            T = mixture_T(p, m1, m2, E1, E2, a2);
+            T = mixture_T<true>(p, m1, m2, E1, E2, a2);
         }
         s.T0[c] = (float)T;
         float V, L;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_heat32(const DevParams p, double *U, He
                 double m1 = U[c], m2 = U[n + c];
                 double rhoe = U[4 * n + c] + U[5 * n + c] + tau * q;
                 double T, a2;
-                unsigned r = equilibrium(p, m1, m2, rhoe, T, a2);
+                unsigned r = equilibrium<true>(p, m1, m2, rhoe, T, a2);
                 double Q[NQ];
                 Q[0] = m1;
                 Q[1] = m2;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_heat32(const DevParams p, double *U, He
             for (int c = t0; c < n; c += nt) {
                 double q = (double)lapf(p, neighbours(p, c), c, vin, s.L, idx2, idy2) + (double)s.Ia[c];
                 double T, a2;
-                unsigned r = equilibrium(p, U[c], U[n + c], U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
+                unsigned r = equilibrium<true>(p, U[c], U[n + c], U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
                 if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
                 s.Ti[c] = (float)T;
                 s.Ai[c] = a2;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256) k_visc32(const DevParams p, double *U, Vi
         q[5] += tau * (aF2[1] * W[1] - aF2[0] * W[0]) * ih -
                 tau * (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) * ih;
         if (relax) {
-            unsigned r = prelax(p, q);
+            unsigned r = prelax<true>(p, q);
             if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
             st |= r & DIM_ST_NAN;
         }

@@ -173,7 +173,7 @@ __device__ __forceinline__ void sweep32_tile(const DevParams &p, const double *_
 #pragma unroll
         for (int k = 0; k < NQ; k++) sU[k * NL + li] = q[k];
         double a2 = q[7], a1 = 1.0 - a2;
-        double p1 = sg_p(p, 0, q[4], a1), p2 = sg_p(p, 1, q[5], a2);
+        double p1 = sg_p<true>(p, 0, q[4], a1), p2 = sg_p<true>(p, 1, q[5], a2);
         sP[li] = p1;
         sP[NL + li] = p2;
         float rho = (float)(q[0] + q[1]);
@@ -270,7 +270,7 @@ __device__ __forceinline__ void sweep32_tile(const DevParams &p, const double *_
         q[QN] = qo[2];
         q[QT] = qo[3];
         if (relax) {
-            unsigned s = prelax(p, q);
+            unsigned s = prelax<true>(p, q);
             if (s & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
             st |= s & DIM_ST_NAN;
         }
