@@ -195,6 +195,17 @@ int dim_step_sched(dim_ctx *c, double *U, int nsteps, double *sched, int replay)
 int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const double *dJ_dUT, double *dJ_dU0,
              double *dJ_dparams);
 
+/* Failure-detection self-test of the bounded waits: one thread waits, for at
+ * most `seconds` (0 < seconds <= 1) of SM clock, on a context word that nothing
+ * writes, through the same bounded-wait routine the grid barriers of the
+ * cooperative kernels use.  The wait runs out and the call returns DIM_ETIMEOUT
+ * (the status bit is cleared again); the context stays usable.  DIM_EINVAL for
+ * a null context or seconds outside (0, 1], DIM_ECUDA on a CUDA error.
+ * Synchronizes.  (Any call that reports DIM_ETIMEOUT through the status word
+ * also clears the grid-barrier counters, so later cooperative launches start
+ * from a consistent barrier.) */
+int dim_wait_selftest(dim_ctx *c, double seconds);
+
 /* Vector-Jacobian product of dim_from_primitive: primbar (DEVICE, 5 planes:
  * alpha_2, p, T, u, v) = (dU/dprim)^T Ubar at the primitive state prim (DEVICE,
  * 5 planes); Ubar DEVICE, 8 planes.  For chaining an initial-condition

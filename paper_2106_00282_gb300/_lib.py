@@ -28,7 +28,7 @@ SYMBOLS = ["dim_init", "dim_destroy", "dim_from_primitive", "dim_cfl_dt", "dim_s
            "dim_hllc_sweep", "dim_relax", "dim_cheb_parabolic", "dim_grad", "dim_status", "dim_profile",
            "dim_kernel_time", "dim_strerror", "dim_hllc_sweep_noalloc", "dim_batch_init", "dim_batch_destroy",
            "dim_batch_layout", "dim_batch_from_primitive", "dim_batch_step", "dim_batch_autotune",
-           "dim_batch_status", "dim_step_sched", "dim_from_primitive_vjp"]
+           "dim_batch_status", "dim_step_sched", "dim_from_primitive_vjp", "dim_wait_selftest"]
 
 
 class DimParams(C.Structure):
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
     L.dim_grad.argtypes = [vp, vp, i, i, vp, vp, pd]
     L.dim_step_sched.argtypes = [vp, vp, i, vp, i]
     L.dim_from_primitive_vjp.argtypes = [vp, vp, vp, vp]
+    L.dim_wait_selftest.argtypes = [vp, d]
     L.dim_status.argtypes = [vp, C.POINTER(u), i]
     L.dim_profile.argtypes = [vp, i, i]
     L.dim_kernel_time.argtypes = [vp, C.c_char_p, C.POINTER(i), pd]

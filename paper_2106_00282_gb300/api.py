@@ -108,6 +108,11 @@ class Solver:
         check(self.L.dim_status(self._ctx, C.byref(f), int(reset)), "dim_status")
         return f.value
 
+    def wait_selftest(self, seconds: float = 0.2) -> int:
+        """Failure-detection self-test of the bounded waits (dim_wait_selftest):
+        returns the DIM_* code, DIM_ETIMEOUT when the wait ran out as designed."""
+        return int(self.L.dim_wait_selftest(self._ctx, float(seconds)))
+
     def step_sched(self, U: torch.Tensor, nsteps: int, sched: torch.Tensor | None = None) -> torch.Tensor:
         """nsteps steps (FP64) in place.  sched None: the schedule (CFL maximum S
         and every LIM lambda_max, per step) is recorded and returned as a

@@ -335,6 +335,18 @@ static int step_once(dim_ctx *c, double *U)
     return DIM_OK;
 }
 
+// After a timed-out grid barrier the barrier counters may hold arrivals of
+// blocks that left: clear them so that the next cooperative launch starts
+// from a consistent barrier.
+static cudaError_t clear_barrier_if_timeout(dim_ctx *c, unsigned st)
+{
+    if (!(st & DIM_ST_TIMEOUT)) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(&c->sc->bar_count, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->sc->bar_gen, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e;
+}
+
 static int read_back(dim_ctx *c, double *dt_last)
 {
     unsigned long long bits = 0;
@@ -342,6 +354,7 @@ static int read_back(dim_ctx *c, double *dt_last)
     TRY(cudaMemcpyAsync(&bits, &c->sc->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
     TRY(cudaMemcpyAsync(&st, &c->sc->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
     TRY(cudaStreamSynchronize(c->stream));
+    TRY(clear_barrier_if_timeout(c, st));
     if (dt_last) {
         double smax;
         memcpy(&smax, &bits, sizeof(smax));
@@ -431,7 +444,25 @@ int dim_status(dim_ctx *c, unsigned *flags, int reset)
     TRY(cudaMemcpyAsync(flags, &c->sc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     if (reset) TRY(cudaMemsetAsync(&c->sc->status, 0, sizeof(unsigned), c->stream));
     TRY(cudaStreamSynchronize(c->stream));
+    TRY(clear_barrier_if_timeout(c, *flags));
     return DIM_OK;
+}
+
+int dim_wait_selftest(dim_ctx *c, double seconds)
+{
+    if (!c || !(seconds > 0.0) || seconds > 1.0) return DIM_EINVAL;
+    int khz = 0;
+    TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->device));
+    const long long limit = (long long)(seconds * 1e3 * (double)khz);
+    // a word of the context scalars that no kernel writes: the spare P slots
+    TRY(cudaMemsetAsync(&c->sc->P[11], 0, sizeof(int), c->stream));
+    TRY(dimk::launch_wait_selftest(c->sc, (const unsigned *)&c->sc->P[11], limit, c->stream));
+    unsigned st = 0;
+    TRY(cudaMemcpyAsync(&st, &c->sc->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    TRY(cudaMemsetAsync(&c->sc->status, 0, sizeof(unsigned), c->stream));
+    TRY(cudaStreamSynchronize(c->stream));
+    return (st & DIM_ST_TIMEOUT) ? DIM_ETIMEOUT : DIM_OK;
 }
 
 int dim_profile(dim_ctx *c, int enable, int reset)

@@ -14,6 +14,7 @@ cudaError_t launch_sweep(const DevParams &p, int axis, const double *Uin, double
 cudaError_t launch_from_primitive(const DevParams &p, const double *prim, double *U, Scalars *sc, cudaStream_t s);
 cudaError_t launch_wave_max(const DevParams &p, const double *U, Scalars *sc, cudaStream_t s);
 cudaError_t launch_relax(const DevParams &p, double *U, Scalars *sc, int which, int check, cudaStream_t s);
+cudaError_t launch_wait_selftest(Scalars *sc, const unsigned *word, long long limit, cudaStream_t s);
 cudaError_t launch_heat(const DevParams &p, double *U, const HeatScratch &s, Scalars *sc, double dt_host,
                         int trelax_first, int check, cudaStream_t st);
 cudaError_t launch_visc(const DevParams &p, int axis, double *U, const ViscScratch &s, Scalars *sc, double dt_host,

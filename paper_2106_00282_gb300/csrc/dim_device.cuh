@@ -384,6 +384,18 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *a)
     return v;
 }
 
+// Bounded wait while *word == value: false after limit SM clock cycles.
+constexpr long long kWaitLimit = 2000000000LL;  // ~1 s at 2 GHz
+__device__ __forceinline__ bool wait_while_equal(const unsigned *word, unsigned value, long long limit)
+{
+    const long long t0 = clock64();
+    while (ld_acquire_u32(word) == value) {
+        __nanosleep(40);
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
 __device__ __forceinline__ bool grid_barrier(Scalars *sc)
 {
     __shared__ int s_ok;
@@ -397,16 +409,9 @@ __device__ __forceinline__ bool grid_barrier(Scalars *sc)
             atomicExch(&sc->bar_count, 0u);
             __threadfence();
             atomicAdd(&sc->bar_gen, 1u);
-        } else {
-            long long t0 = clock64();
-            while (ld_acquire_u32(&sc->bar_gen) == gen) {
-                __nanosleep(40);
-                if (clock64() - t0 > 2000000000LL) {
-                    atomicOr(&sc->status, DIM_ST_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
+        } else if (!wait_while_equal(&sc->bar_gen, gen, kWaitLimit)) {
+            atomicOr(&sc->status, DIM_ST_TIMEOUT);
+            ok = 0;
         }
         __threadfence();
         s_ok = ok;

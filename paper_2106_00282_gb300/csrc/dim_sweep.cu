@@ -370,6 +370,21 @@ cudaError_t launch_from_primitive(const DevParams &p, const double *prim, double
     return cudaGetLastError();
 }
 
+// one thread waits, bounded, on a word nothing writes (the failure path of the
+// grid barriers' wait, exercised without stopping any other work)
+__global__ void k_wait_selftest(Scalars *sc, const unsigned *word, long long limit)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!wait_while_equal(word, ld_acquire_u32(word), limit)) atomicOr(&sc->status, DIM_ST_TIMEOUT);
+    }
+}
+
+cudaError_t launch_wait_selftest(Scalars *sc, const unsigned *word, long long limit, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(sc, word, limit);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wave_max(const DevParams &p, const double *U, Scalars *sc, cudaStream_t s)
 {
     k_wave_max<<<pw_grid(p.n), 256, 0, s>>>(p, U, sc);

@@ -63,3 +63,4 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dim_grad(None, None, 1, 1, None, None, None) == _lib.DIM_EINVAL
     assert lib.dim_step_sched(None, None, 1, None, 0) == _lib.DIM_EINVAL
     assert lib.dim_from_primitive_vjp(None, None, None, None) == _lib.DIM_EINVAL
+    assert lib.dim_wait_selftest(None, 0.1) == _lib.DIM_EINVAL

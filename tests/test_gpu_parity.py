@@ -246,6 +246,23 @@ def test_nonphysical_input_is_reported(torch_cuda, O, I, fault):
     assert s.status() & (_lib.ST_NONPHYS | _lib.ST_NAN) == 0
 
 
+def test_bounded_wait_expires_and_context_stays_usable(torch_cuda, O, I):
+    """Failure detection without a fault: the bounded wait of the grid barriers
+    runs out on a word nothing writes and is reported as DIM_ETIMEOUT; the
+    status word is clean afterwards and the context keeps stepping correctly."""
+    from paper_2106_00282_gb300 import _lib
+
+    wl = I.conduction_disc(48)
+    s, U, Uo = _init_both(torch_cuda, O, wl)
+    assert s.wait_selftest(0.2) == _lib.DIM_ETIMEOUT
+    assert s.status() == 0
+    assert s.wait_selftest(1.5) == _lib.DIM_EINVAL
+    s.step(U, 3)
+    Uo = O.step(wl.params, Uo, wl.dx, wl.dy, 3)[0]
+    assert_parity(_host(U), Uo, what="steps after the wait self-test")
+    s.close()
+
+
 @pytest.mark.parametrize("which", ["impact", "conduction"])
 def test_full_size_parity(torch_cuda, O, I, which):
     """At the benchmark sizes (1024 x 512 impact; 2048^2 conduction disc), in the
