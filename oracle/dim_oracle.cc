@@ -79,12 +79,16 @@ typedef struct {
     int limiter;  /* 0: first order, 1: minmod MUSCL, 2: Overbee on alpha_2 and alpha_k rho_k with minmod
                    * on u and p_k, 3: Overbee on alpha_2 only (the inconsistent combination of Sec. 4.1) */
     int bc[2];    /* per axis: 0 transmissive, 1 periodic */
-    int trelax;   /* 0: off (no T relaxation, no conduction), 1: equilibrium */
+    int trelax;   /* 0: off (no T relaxation, no conduction), 1: exact equilibrium, 2: the implicit midpoint
+                   * scheme of Sec. 3.4.1 with trelax_iters simple iterations */
     int n_outer;  /* outer iterations of Algorithm 1 */
     int p_policy; /* 0: P by formula, 1: fixed p_fixed, 2: clamp(formula, p_min, p_max) */
     int p_fixed, p_min, p_max;
     int precision; /* unused: the oracle is FP64 */
     double src[2]; /* external heat source intensities I_k, I_k = alpha_k I_k (Eq. I) */
+    int heat_alpha;   /* heat stage (T, alpha) update: 0 projection onto the equilibrium manifold,
+                       * 1 linear, T += tau V (L_h u_hat + I), alpha += tau U (L_h u_hat + I) */
+    int trelax_iters; /* simple iterations of the midpoint temperature relaxation (trelax 2) */
 } orc_params;
 }
 
@@ -204,6 +208,7 @@ struct prm {
     double cfl;
     int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
     R src[2];
+    int heat_alpha, trelax_iters;
 };
 
 /* dparams (may be NULL): tangents of (k0_1, k0_2, mu_1, mu_2, I_1, I_2) */
@@ -221,6 +226,7 @@ prm<double> make_prm<double>(const orc_params *P, const double *)
     q.k_exp = P->k_exp; q.T_ref = P->T_ref; q.cfl = P->cfl;
     q.limiter = P->limiter; q.trelax = P->trelax; q.n_outer = P->n_outer; q.p_policy = P->p_policy;
     q.p_fixed = P->p_fixed; q.p_min = P->p_min; q.p_max = P->p_max;
+    q.heat_alpha = P->heat_alpha; q.trelax_iters = P->trelax_iters;
     return q;
 }
 
@@ -238,6 +244,7 @@ static prm<DualT<B>> make_prm_dual(const orc_params *P, const double *dp)
     q.k_exp = P->k_exp; q.T_ref = P->T_ref; q.cfl = P->cfl;
     q.limiter = P->limiter; q.trelax = P->trelax; q.n_outer = P->n_outer; q.p_policy = P->p_policy;
     q.p_fixed = P->p_fixed; q.p_min = P->p_min; q.p_max = P->p_max;
+    q.heat_alpha = P->heat_alpha; q.trelax_iters = P->trelax_iters;
     return q;
 }
 template <>
@@ -252,6 +259,7 @@ prm<Cnt> make_prm<Cnt>(const orc_params *P, const double *)
     q.k_exp = P->k_exp; q.T_ref = P->T_ref; q.cfl = P->cfl;
     q.limiter = P->limiter; q.trelax = P->trelax; q.n_outer = P->n_outer; q.p_policy = P->p_policy;
     q.p_fixed = P->p_fixed; q.p_min = P->p_min; q.p_max = P->p_max;
+    q.heat_alpha = P->heat_alpha; q.trelax_iters = P->trelax_iters;
     return q;
 }
 
@@ -706,6 +714,49 @@ static R cell_T(const prm<R> *P, const R *U, int n, int c)
     return (U[4 * n + c] + U[5 * n + c] - a1 * P->pinf[0] - a2 * P->pinf[1]) / C;
 }
 
+/* The paper's own discretization of the relaxation ODEs (ht_eq2_TR),
+ * (ht_eq3_TR): Eqs. (ht_eq2_TR_dis), (ht_eq3_TR_dis), unknowns (T', a2'),
+ *   B2 C1 (T' - T1^0) + (B1 + B2) C2 (T' - T2^0) = 0,
+ *   C2 (T' - T2^0) + B2 (a2' - a2^0) = 0,
+ * B2 evaluated at the averages T_k^av = (T_k^0 + T')/2, a2^av = (a2^0 + a2')/2.
+ * B2 is Eq. (B2_2) with the sign that keeps dp1 = dp2 along the path (the
+ * printed form adds pinf_2 to the fraction; differentiating p1 = p2 at fixed
+ * m_k and fixed total energy subtracts it from pinf_2):
+ *   B2 = pinf_2 - [G1 C1 T1/a1^2 + G1 pinf_1/a1 + G2 C2 T2/a2^2 + G2 pinf_2/a2]
+ *                 / [G1/a1 + G2/a2],   G_k = g_k - 1 (Grueneisen, SG).
+ * The system is solved by simple iteration, a fixed number of times, from
+ * T' = Eq. (Taverage), a2' = a2^0.  Every iterate satisfies both equations for
+ * its B2, so the total energy C T' + pinf_1 - B1 a2' is conserved whatever the
+ * count; with pinf_1 = pinf_2 the temperature is Eq. (Taverage) exactly. */
+template <typename R>
+static unsigned trelax_midpoint(const prm<R> *P, R m1, R m2, R E1, R E2, R a20, R *T, R *a2)
+{
+    R C1 = m1 * P->cv[0], C2 = m2 * P->cv[1];
+    double G1 = P->gamma[0] - 1.0, G2 = P->gamma[1] - 1.0;
+    double B1 = P->pinf[0] - P->pinf[1];
+    /* phase temperatures before the stage: E_k = C_k T_k + a_k pinf_k */
+    R T10 = (E1 - (1.0 - a20) * P->pinf[0]) / C1;
+    R T20 = (E2 - a20 * P->pinf[1]) / C2;
+    R Tp = (C1 * T10 + C2 * T20) / (C1 + C2);
+    R ap = a20;
+    for (int it = 0; it < P->trelax_iters; it++) {
+        R T1a = 0.5 * (T10 + Tp), T2a = 0.5 * (T20 + Tp);
+        R a2a = 0.5 * (a20 + ap), a1a = 1.0 - a2a;
+        R num = G1 * C1 * T1a / (a1a * a1a) + G1 * P->pinf[0] / a1a + G2 * C2 * T2a / (a2a * a2a) +
+                G2 * P->pinf[1] / a2a;
+        R den = G1 / a1a + G2 / a2a;
+        R B2 = P->pinf[1] - num / den;
+        Tp = (B2 * C1 * T10 + (B1 + B2) * C2 * T20) / (B2 * C1 + (B1 + B2) * C2);
+        ap = a20 - C2 * (Tp - T20) / B2;
+    }
+    *T = Tp;
+    *a2 = ap;
+    unsigned st = 0;
+    if (!(ap > 0.0 && ap < 1.0 && Tp > 0.0)) st |= ORC_NONPHYS;
+    if (is_nan(ap) || is_nan(Tp)) st |= ORC_NAN;
+    return st;
+}
+
 template <typename R>
 static unsigned trelax_t(const prm<R> *P, int ncell, R *U)
 {
@@ -715,7 +766,10 @@ static unsigned trelax_t(const prm<R> *P, int ncell, R *U)
         R m1 = U[0 * n + c], m2 = U[1 * n + c];
         R rhoe = U[4 * n + c] + U[5 * n + c];
         R T, a2;
-        st |= equilibrium(P, m1, m2, rhoe, &T, &a2);
+        if (P->trelax == 2)
+            st |= trelax_midpoint(P, m1, m2, U[4 * n + c], U[5 * n + c], U[7 * n + c], &T, &a2);
+        else
+            st |= equilibrium(P, m1, m2, rhoe, &T, &a2);
         U[4 * n + c] = m1 * P->cv[0] * T + (1.0 - a2) * P->pinf[0];
         U[5 * n + c] = m2 * P->cv[1] * T + a2 * P->pinf[1];
         U[7 * n + c] = a2;
@@ -958,6 +1012,8 @@ static double lam_of(double computed, double *slot, int replay)
  * applies the last (explicit) sweep conservatively to the mixture energy:
  * rho E += tau L_h u_hat, rho e += tau L_h u_hat, followed by the projection
  * (T, alpha) = equilibrium(m1, m2, rho e) and E_k = C_k T + a_k pinf_k.
+ * With heat_alpha = 1 the projection is replaced by the linear update of
+ * Eqs. (ht_eq2_ht), (ht_eq3_ht) with the frozen V and U = -B1 V / K.
  * lam_io: NULL, or the 8 lambda_max slots of the schedule record. */
 template <typename R>
 static unsigned heat_t(const prm<R> *P, int nx, int ny, double dx, double dy, double tau, R *U, int *P_used,
@@ -977,6 +1033,8 @@ static unsigned heat_t(const prm<R> *P, int nx, int ny, double dx, double dy, do
     R *q = (R *)malloc(sizeof(R) * n);
     R *Ia = (R *)malloc(sizeof(R) * n); /* I1 + I2 = a1 I1 + a2 I2 (Eq. I) */
     R *f = (R *)malloc(sizeof(R) * n);  /* V (I1 + I2): the f of Eq. (LIM) */
+    R *Uc = (R *)malloc(sizeof(R) * n); /* U = d alpha / d(rho e) = -B1 V / K */
+    R *a0 = (R *)malloc(sizeof(R) * n);
     orc_op<R> o;
     op_init(&o, nx, ny, dx, dy, P->bc);
     for (int c = 0; c < n; c++) {
@@ -985,6 +1043,7 @@ static unsigned heat_t(const prm<R> *P, int nx, int ny, double dx, double dy, do
         rE0[c] = U[6 * n + c];
         Ti[c] = T0[c];
         ai[c] = U[7 * n + c];
+        a0[c] = ai[c];
     }
     int pmax_used = 0;
     int nout = P->n_outer < 1 ? 1 : P->n_outer;
@@ -998,6 +1057,7 @@ static unsigned heat_t(const prm<R> *P, int nx, int ny, double dx, double dy, do
             R r2 = (P->gamma[1] - 1.0) * C2 * T / (a2 * a2);
             R K = T * (r1 + r2);
             V[c] = 1.0 / (C1 + C2 + B1 * B1 / K);
+            if (P->heat_alpha == 1) Uc[c] = -(B1 * V[c]) / K;
             lam[c] = a1 * lambda_k(P, 0, T) + a2 * lambda_k(P, 1, T);
             Ia[c] = a1 * P->src[0] + a2 * P->src[1];
             f[c] = V[c] * Ia[c];
@@ -1014,11 +1074,21 @@ static unsigned heat_t(const prm<R> *P, int nx, int ny, double dx, double dy, do
         op_apply(&o, uh, q);
         /* the last sweep in conservative form: rho e gains tau (L_h u_hat + I1 + I2) */
         for (int c = 0; c < n; c++) q[c] = q[c] + Ia[c];
-        for (int c = 0; c < n; c++) {
-            R T, a2;
-            st |= equilibrium(P, U[0 * n + c], U[1 * n + c], re0[c] + tau * q[c], &T, &a2);
-            Ti[c] = T;
-            ai[c] = a2;
+        if (P->heat_alpha == 1) {
+            /* Eqs. (ht_eq2_ht), (ht_eq3_ht) over the step with the frozen V, U
+             * and the same q + I: T = T^n + tau V (q + I), alpha = alpha^n + tau U (q + I);
+             * the energy C T + pinf_1 - B1 alpha gains tau (q + I)(C V - B1 U) = tau (q + I) */
+            for (int c = 0; c < n; c++) {
+                Ti[c] = T0[c] + tau * V[c] * q[c];
+                ai[c] = a0[c] + tau * Uc[c] * q[c];
+            }
+        } else {
+            for (int c = 0; c < n; c++) {
+                R T, a2;
+                st |= equilibrium(P, U[0 * n + c], U[1 * n + c], re0[c] + tau * q[c], &T, &a2);
+                Ti[c] = T;
+                ai[c] = a2;
+            }
         }
     }
     for (int c = 0; c < n; c++) {
@@ -1030,6 +1100,7 @@ static unsigned heat_t(const prm<R> *P, int nx, int ny, double dx, double dy, do
     }
     if (P_used) *P_used = pmax_used;
     free(T0); free(re0); free(rE0); free(Ti); free(ai); free(V); free(lam); free(uh); free(q); free(Ia); free(f);
+    free(Uc); free(a0);
     free(o.lx); free(o.ly);
     return st;
 }
@@ -1157,7 +1228,7 @@ static int viscous_on(const prm<R> *P) { return P->mu[0] > 0.0 || P->mu[1] > 0.0
 template <typename R>
 static int heat_on(const prm<R> *P)
 {
-    return P->trelax == 1 && (P->k0[0] > 0.0 || P->k0[1] > 0.0 || P->src[0] > 0.0 || P->src[1] > 0.0);
+    return P->trelax >= 1 && (P->k0[0] > 0.0 || P->k0[1] > 0.0 || P->src[0] > 0.0 || P->src[1] > 0.0);
 }
 
 /* end-of-step admissibility: alpha_2 in (0,1), m_k > 0, p_k + pinf_k > 0 */
@@ -1206,7 +1277,7 @@ static unsigned step_t(const prm<R> *P, int nx, int ny, double dx, double dy, R 
             if (ny > 1) tr |= viscous_t(P, nx, ny, dx, dy, 1, dt, U, &pv, rec ? rec + 10 : NULL, replay);
             tr |= prelax_t(P, n, U);
         }
-        if (P->trelax == 1) {
+        if (P->trelax >= 1) {
             tr |= trelax_t(P, n, U);
             if (heat_on(P)) tr |= heat_t(P, nx, ny, dx, dy, dt, U, &ph, rec ? rec + 1 : NULL, replay);
         }

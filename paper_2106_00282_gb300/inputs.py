@@ -32,7 +32,8 @@ import numpy as np
 LIMITER_NONE, LIMITER_MINMOD, LIMITER_OVERBEE = 0, 1, 2
 LIMITER_OVERBEE_ALPHA_ONLY = 3  # the inconsistent combination (oracle only)
 BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
-TRELAX_OFF, TRELAX_EQUILIBRIUM = 0, 1
+TRELAX_OFF, TRELAX_EQUILIBRIUM, TRELAX_MIDPOINT = 0, 1, 2
+HEAT_ALPHA_PROJECTION, HEAT_ALPHA_LINEAR = 0, 1
 P_FORMULA, P_FIXED, P_CLAMP = 0, 1, 2
 PRECISION_FP64, PRECISION_FP32_BULK = 0, 1
 
@@ -61,6 +62,8 @@ class Params:
     p_max: int = 24
     precision: int = PRECISION_FP64  # read by the CUDA library only; the oracle is FP64
     src: tuple = (0.0, 0.0)          # external heat source intensities I_k (W/m^3 of phase k)
+    heat_alpha: int = HEAT_ALPHA_PROJECTION  # heat-stage (T, alpha) update
+    trelax_iters: int = 20           # simple iterations of the midpoint temperature relaxation
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
