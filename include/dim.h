@@ -57,6 +57,12 @@ extern "C" {
 #define DIM_BC_PERIODIC 1
 #define DIM_TRELAX_OFF 0         /* no temperature relaxation and no conduction */
 #define DIM_TRELAX_EQUILIBRIUM 1 /* exact p,T equilibrium, Sec. 3.4.1 */
+#define DIM_TRELAX_MIDPOINT 2    /* the implicit scheme of Eqs. ht_eq2_TR_dis, ht_eq3_TR_dis with B2 (Eq. B2_2,
+                                    sign that keeps dp1 = dp2) at the averages, trelax_iters simple iterations
+                                    from T' = Eq. Taverage, alpha' = alpha^0 (FP64 only) */
+#define DIM_HEAT_ALPHA_PROJECTION 0 /* heat stage: (T, alpha) = p,T equilibrium of the updated rho e */
+#define DIM_HEAT_ALPHA_LINEAR 1     /* heat stage: T += tau V (L_h u_hat + I), alpha += tau U (L_h u_hat + I) with
+                                       the frozen V, U of Eqs. ht_eq2_ht, ht_eq3_ht (FP64 only) */
 #define DIM_P_FORMULA 0          /* P = ceil(pi/4 sqrt(tau lambda_max + 1)), capped at p_max */
 #define DIM_P_FIXED 1            /* P = p_fixed */
 #define DIM_P_CLAMP 2            /* P = clamp(formula, p_min, p_max) */
@@ -91,6 +97,8 @@ typedef struct dim_params {
     int precision; /* DIM_PRECISION_FP64 or DIM_PRECISION_FP32_BULK */
     double src[2]; /* external heat source I_k >= 0 per unit volume of phase k: I_k = alpha_k I_k (Eq. I),
                       deposited in the heat-conduction stage */
+    int heat_alpha;   /* DIM_HEAT_ALPHA_PROJECTION or DIM_HEAT_ALPHA_LINEAR */
+    int trelax_iters; /* simple iterations of DIM_TRELAX_MIDPOINT, 1..1000 (read only in that mode) */
 } dim_params;
 
 typedef struct dim_ctx dim_ctx; /* opaque: parameters, grid, stream, scratch */
@@ -100,7 +108,9 @@ typedef struct dim_ctx dim_ctx; /* opaque: parameters, grid, stream, scratch */
  * cuda_stream is a cudaStream_t (NULL: legacy default stream).
  * Errors: DIM_EINVAL for non-positive sizes/spacings, a 1 x 1 grid (no axis,
  * hence no CFL time scale), gamma_k <= 1, Cv_k <= 0,
- * cfl <= 0, unknown flags, p_max outside [1, 64]; DIM_ECUDA on allocation
+ * cfl <= 0, unknown flags, p_max outside [1, 64], DIM_TRELAX_MIDPOINT with
+ * trelax_iters outside [1, 1000], DIM_TRELAX_MIDPOINT or DIM_HEAT_ALPHA_LINEAR
+ * with a precision other than FP64; DIM_ECUDA on allocation
  * failure.  The paper's parameters: Sec. 2 (EOS), Sec. 3 (scheme). */
 int dim_init(dim_ctx **out, const dim_params *p, int nx, int ny, double dx, double dy, void *cuda_stream);
 
@@ -190,7 +200,8 @@ int dim_step_sched(dim_ctx *c, double *U, int nsteps, double *sched, int replay)
  *    device memory ~ (nsteps/ckpt_every + ckpt_every + 10) states plus the
  *    Chebyshev iterates of one step, allocated on the first call and reused.
  * Synchronizes.  Errors: DIM_EINVAL (null pointers, nsteps < 0, ckpt_every < 1,
- * FP32-bulk precision), DIM_ENONPHYS / DIM_ENOROOT / DIM_ETIMEOUT when the
+ * FP32-bulk precision, DIM_TRELAX_MIDPOINT, DIM_HEAT_ALPHA_LINEAR: the adjoint
+ * differentiates the equilibrium projection), DIM_ENONPHYS / DIM_ENOROOT / DIM_ETIMEOUT when the
  * forward run meets them, DIM_ECUDA. */
 int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const double *dJ_dUT, double *dJ_dU0,
              double *dJ_dparams);

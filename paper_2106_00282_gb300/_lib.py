@@ -39,6 +39,7 @@ class DimParams(C.Structure):
         ("limiter", C.c_int), ("bc", C.c_int * 2), ("trelax", C.c_int), ("n_outer", C.c_int),
         ("p_policy", C.c_int), ("p_fixed", C.c_int), ("p_min", C.c_int), ("p_max", C.c_int),
         ("precision", C.c_int), ("src", C.c_double * 2),
+        ("heat_alpha", C.c_int), ("trelax_iters", C.c_int),
     ]
 
 
@@ -62,6 +63,8 @@ def make_params(p) -> DimParams:
     s.p_max = p.p_max
     s.precision = getattr(p, "precision", 0)
     s.src[:] = list(getattr(p, "src", (0.0, 0.0)))
+    s.heat_alpha = getattr(p, "heat_alpha", 0)
+    s.trelax_iters = getattr(p, "trelax_iters", 20)
     return s
 
 

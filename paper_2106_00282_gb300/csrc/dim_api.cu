@@ -24,7 +24,7 @@ static bool g_setup_done[64];
 static bool viscous_on(const dim_params &h) { return h.mu[0] > 0.0 || h.mu[1] > 0.0; }
 static bool heat_on(const dim_params &h)
 {
-    return h.trelax == DIM_TRELAX_EQUILIBRIUM &&
+    return h.trelax != DIM_TRELAX_OFF &&
            (h.k0[0] > 0.0 || h.k0[1] > 0.0 || h.src[0] > 0.0 || h.src[1] > 0.0);
 }
 
@@ -147,7 +147,14 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
     if (hp->limiter != DIM_LIMITER_NONE && hp->limiter != DIM_LIMITER_MINMOD && hp->limiter != DIM_LIMITER_OVERBEE)
         return DIM_EINVAL;
     if (!(hp->src[0] >= 0.0) || !(hp->src[1] >= 0.0)) return DIM_EINVAL;
-    if (hp->trelax != DIM_TRELAX_OFF && hp->trelax != DIM_TRELAX_EQUILIBRIUM) return DIM_EINVAL;
+    if (hp->trelax != DIM_TRELAX_OFF && hp->trelax != DIM_TRELAX_EQUILIBRIUM && hp->trelax != DIM_TRELAX_MIDPOINT)
+        return DIM_EINVAL;
+    if (hp->trelax == DIM_TRELAX_MIDPOINT && (hp->trelax_iters < 1 || hp->trelax_iters > 1000)) return DIM_EINVAL;
+    if (hp->heat_alpha != DIM_HEAT_ALPHA_PROJECTION && hp->heat_alpha != DIM_HEAT_ALPHA_LINEAR) return DIM_EINVAL;
+    // the paper's variants are FP64 kernels only
+    if ((hp->trelax == DIM_TRELAX_MIDPOINT || hp->heat_alpha == DIM_HEAT_ALPHA_LINEAR) &&
+        hp->precision != DIM_PRECISION_FP64)
+        return DIM_EINVAL;
     if (hp->n_outer < 1 || hp->n_outer > 8) return DIM_EINVAL;
     if (hp->p_policy < DIM_P_FORMULA || hp->p_policy > DIM_P_CLAMP) return DIM_EINVAL;
     if (hp->p_max < 1 || hp->p_max > dimk::PMAX) return DIM_EINVAL;
@@ -187,6 +194,8 @@ int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, 
     p.n = nx * ny;
     p.limiter = hp->limiter;
     p.trelax = hp->trelax;
+    p.trelax_iters = hp->trelax == DIM_TRELAX_MIDPOINT ? hp->trelax_iters : 0;
+    p.heat_alpha = hp->heat_alpha;
     p.n_outer = hp->n_outer;
     p.p_policy = hp->p_policy;
     p.p_fixed = hp->p_fixed;
@@ -302,7 +311,7 @@ static int step_once(dim_ctx *c, double *U)
 {
     const dim_params &h = c->hp;
     const DevParams &p = c->p;
-    const bool vis = viscous_on(h), heat = heat_on(h), trx = h.trelax == DIM_TRELAX_EQUILIBRIUM;
+    const bool vis = viscous_on(h), heat = heat_on(h), trx = h.trelax != DIM_TRELAX_OFF;
     const bool sx = p.nx > 1, sy = p.ny > 1;
     // the kernel that ends the step also checks the end-of-step state
     enum { LAST_SX, LAST_SY, LAST_VX, LAST_VY, LAST_TR, LAST_HEAT } last;

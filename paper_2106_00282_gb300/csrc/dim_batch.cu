@@ -681,7 +681,7 @@ int dim_batch_init(dim_batch **out, const dim_params *hp, int ninst, const int *
         return r;
     }
     b->viscous = hp->mu[0] > 0.0 || hp->mu[1] > 0.0;
-    b->trelax = hp->trelax == DIM_TRELAX_EQUILIBRIUM;
+    b->trelax = hp->trelax != DIM_TRELAX_OFF;  // FP32-bulk only: dim_host_params admits no variant
     b->heat = b->trelax && (hp->k0[0] > 0.0 || hp->k0[1] > 0.0 || hp->src[0] > 0.0 || hp->src[1] > 0.0);
     int dev = 0;
     bool ok = cudaGetDevice(&dev) == cudaSuccess &&

@@ -32,6 +32,8 @@ struct DevParams {
     double dx, dy, idx, idy, idx2, idy2;  // spacing, 1/h and 1/h^2
     int nx, ny, n;
     int limiter, bc[2], trelax, n_outer, p_policy, p_fixed, p_min, p_max;
+    int trelax_iters;  // simple iterations of DIM_TRELAX_MIDPOINT
+    int heat_alpha;    // DIM_HEAT_ALPHA_PROJECTION or DIM_HEAT_ALPHA_LINEAR
     int precision;  // DIM_PRECISION_FP64 or DIM_PRECISION_FP32_BULK
     double src[2];  // external heat source intensities I_k
     // 1: the Chebyshev lambda_max of every LIM solve is read from the context
@@ -311,6 +313,51 @@ __device__ __forceinline__ unsigned equilibrium(const DevParams &p, double m1, d
     return st;
 }
 
+// The implicit discretization of the relaxation ODEs, Eqs. ht_eq2_TR_dis and
+// ht_eq3_TR_dis, in the unknowns (T', a'):
+//   B2 C1 (T' - T1^0) + (B1 + B2) C2 (T' - T2^0) = 0,  C2 (T' - T2^0) + B2 (a' - a^0) = 0,
+// B2 from Eq. B2_2 at the averages T_k^av = (T_k^0 + T')/2, a^av = (a^0 + a')/2,
+// taken as pinf_2 minus the fraction (differentiating p1 = p2 at fixed m_k and
+// total energy fixes that sign; the printed form adds pinf_2).  p.trelax_iters
+// simple iterations from T' = Eq. Taverage, a' = a^0; each iterate conserves
+// C T' + pinf_1 - B1 a' exactly.
+__device__ __forceinline__ unsigned trelax_midpoint(const DevParams &p, double m1, double m2, double E1, double E2,
+                                                    double a0, double &T, double &a)
+{
+    const double C1 = m1 * p.cv[0], C2 = m2 * p.cv[1];
+    const double G1 = p.gm1[0], G2 = p.gm1[1];
+    const double B1 = p.pinf[0] - p.pinf[1];
+    // phase temperatures before the stage: E_k = C_k T_k + a_k pinf_k
+    const double T10 = (E1 - (1.0 - a0) * p.pinf[0]) / C1;
+    const double T20 = (E2 - a0 * p.pinf[1]) / C2;
+    double Tp = (C1 * T10 + C2 * T20) / (C1 + C2);
+    double ap = a0;
+    for (int it = 0; it < p.trelax_iters; it++) {
+        double T1a = 0.5 * (T10 + Tp), T2a = 0.5 * (T20 + Tp);
+        double a2a = 0.5 * (a0 + ap), a1a = 1.0 - a2a;
+        double num = G1 * C1 * T1a / (a1a * a1a) + G1 * p.pinf[0] / a1a + G2 * C2 * T2a / (a2a * a2a) +
+                     G2 * p.pinf[1] / a2a;
+        double den = G1 / a1a + G2 / a2a;
+        double B2 = p.pinf[1] - num / den;
+        Tp = (B2 * C1 * T10 + (B1 + B2) * C2 * T20) / (B2 * C1 + (B1 + B2) * C2);
+        ap = a0 - C2 * (Tp - T20) / B2;
+    }
+    T = Tp;
+    a = ap;
+    unsigned st = 0;
+    if (!(gt0_i(ap) && lt_i(ap, 1.0) && gt0_i(Tp))) st |= DIM_ST_NONPHYS;
+    if (nan_i(ap) || nan_i(Tp)) st |= DIM_ST_NAN;
+    return st;
+}
+
+// the temperature-relaxation stage of one cell: (T, a) from the phase energies
+__device__ __forceinline__ unsigned trelax_cell(const DevParams &p, double m1, double m2, double E1, double E2,
+                                                double a0, double &T, double &a)
+{
+    if (p.trelax == DIM_TRELAX_MIDPOINT) return trelax_midpoint(p, m1, m2, E1, E2, a0, T, a);
+    return equilibrium(p, m1, m2, E1 + E2, T, a);
+}
+
 // mixture temperature of a cell in thermal equilibrium (energy form of Eq. Taverage)
 template <bool FAST = false>
 __device__ __forceinline__ double mixture_T(const DevParams &p, double m1, double m2, double E1, double E2, double a2)
@@ -332,6 +379,19 @@ __device__ __forceinline__ void heat_coeffs(const DevParams &p, double m1, doubl
     double K = T * (r1 + r2);
     V = 1.0 / (C1 + C2 + B1 * B1 / K);
     Lam = a1 * cond(p, 0, T) + a2 * cond(p, 1, T);
+}
+
+// U = d alpha / d(rho e) = -B1 V / K on the equilibrium manifold at (T, a), for
+// the V that heat_coeffs gives there (Eq. ht_eq3_ht, linear update)
+__device__ __forceinline__ double heat_U(const DevParams &p, double m1, double m2, double T, double a2, double V)
+{
+    double a1 = 1.0 - a2;
+    double C1 = m1 * p.cv[0], C2 = m2 * p.cv[1];
+    double B1 = p.pinf[0] - p.pinf[1];
+    double r1 = p.gm1[0] * C1 * T / (a1 * a1);
+    double r2 = p.gm1[1] * C2 * T / (a2 * a2);
+    double K = T * (r1 + r2);
+    return -(B1 * V) / K;
 }
 
 // ---------------------------------------------------------------------------

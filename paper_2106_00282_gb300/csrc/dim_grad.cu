@@ -58,7 +58,7 @@ int stage_list(const dim_ctx *c, Stage *s)
     if (ctx_heat_on(c->hp)) {
         s[k++] = {ST_TRELAX, 0};
         s[k++] = {ST_HEAT, 0};
-    } else if (c->hp.trelax == DIM_TRELAX_EQUILIBRIUM) {
+    } else if (c->hp.trelax != DIM_TRELAX_OFF) {
         s[k++] = {ST_TRELAX, 0};
     }
     return k;
@@ -198,6 +198,8 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
 {
     if (!c || !U0 || !dJ_dUT || !dJ_dU0 || nsteps < 0 || ckpt_every < 1) return DIM_EINVAL;
     if (c->p.precision != DIM_PRECISION_FP64) return DIM_EINVAL;
+    // the reverse stages differentiate the equilibrium relaxation and projection
+    if (c->hp.trelax == DIM_TRELAX_MIDPOINT || c->hp.heat_alpha != DIM_HEAT_ALPHA_PROJECTION) return DIM_EINVAL;
     const DevParams &p = c->p;
     cudaStream_t s = c->stream;
     const size_t n = (size_t)p.n, n8 = 8 * n, sb = n8 * sizeof(double);

@@ -59,6 +59,10 @@ __device__ __forceinline__ double gersh(const DevParams &p, const Nb &nb, int c,
 // ---------------------------------------------------------------------------
 // heat conduction (Algorithm 1 with the LIM)
 // ---------------------------------------------------------------------------
+// VARIANTS: compiled with the paper's midpoint temperature relaxation and the
+// linear (T, alpha) update (chosen by p.trelax / p.heat_alpha); the default
+// instantiation holds only the equilibrium relaxation and projection.
+template <bool VARIANTS>
 __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, HeatScratch s,
                                               Scalars *sc, double dt_host, int trelax_first, int check)
 {
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
         double m1 = U[c], m2 = U[n + c], E1 = U[4 * n + c], E2 = U[5 * n + c], a2 = U[7 * n + c];
         double T;
         if (trelax_first) {
-            unsigned r = equilibrium(p, m1, m2, E1 + E2, T, a2);
+            unsigned r = VARIANTS ? trelax_cell(p, m1, m2, E1, E2, a2, T, a2) : equilibrium(p, m1, m2, E1 + E2, T, a2);
             if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
             st |= r & DIM_ST_NAN;
             U[4 * n + c] = m1 * p.cv[0] * T + (1.0 - a2) * p.pinf[0];
@@ -133,14 +137,27 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
         }
         hoff += 2 * (size_t)P;
         // D. last (explicit, b = 0) sweep in conservative form on the energy and
-        //    the projection onto the p,T-equilibrium manifold
+        //    the projection onto the p,T-equilibrium manifold (or the linear
+        //    update T = T^n + tau V q, a = a^n + tau U q of Eqs. ht_eq2_ht, ht_eq3_ht
+        //    with the V, U this iteration froze)
+        const bool linear = VARIANTS && p.heat_alpha == DIM_HEAT_ALPHA_LINEAR;
         if (it == nout - 1) {
             for (int c = t0; c < n; c += nt) {
                 double q = lap(p, neighbours(p, c), c, vin, s.L) + s.Ia[c];
                 double m1 = U[c], m2 = U[n + c];
                 double rhoe = U[4 * n + c] + U[5 * n + c] + tau * q;
                 double T, a2;
-                unsigned r = equilibrium(p, m1, m2, rhoe, T, a2);
+                unsigned r = 0;
+                if (linear) {
+                    const double Tit = it == 0 ? s.T0[c] : s.Ti[c], ait = it == 0 ? U[7 * n + c] : s.Ai[c];
+                    const double Uc = heat_U(p, m1, m2, Tit, ait, s.V[c]);
+                    T = s.T0[c] + tau * s.V[c] * q;
+                    a2 = U[7 * n + c] + tau * Uc * q;
+                    if (!(gt0_i(a2) && lt_i(a2, 1.0) && gt0_i(T))) r |= DIM_ST_NONPHYS;
+                    if (nan_i(a2) || nan_i(T)) r |= DIM_ST_NAN;
+                } else {
+                    r = equilibrium(p, m1, m2, rhoe, T, a2);
+                }
                 double Q[NQ];
                 Q[0] = m1;
                 Q[1] = m2;
@@ -161,8 +178,16 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             for (int c = t0; c < n; c += nt) {
                 double q = lap(p, neighbours(p, c), c, vin, s.L) + s.Ia[c];
                 double T, a2;
-                unsigned r = equilibrium(p, U[c], U[n + c], U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
-                if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+                if (linear) {
+                    const double Tit = it == 0 ? s.T0[c] : s.Ti[c], ait = it == 0 ? U[7 * n + c] : s.Ai[c];
+                    const double Uc = heat_U(p, U[c], U[n + c], Tit, ait, s.V[c]);
+                    T = s.T0[c] + tau * s.V[c] * q;
+                    a2 = U[7 * n + c] + tau * Uc * q;
+                } else {
+                    unsigned r = equilibrium(p, U[c], U[n + c], U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
+                    if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+                }
+                // every thread reads and writes only its own cells here
                 s.Ti[c] = T;
                 s.Ai[c] = a2;
             }
@@ -325,14 +350,17 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static int g_heat_blocks = 0, g_visc_blocks[2] = {0, 0};
+static int g_heat_blocks[2] = {0, 0}, g_visc_blocks[2] = {0, 0};
 
 cudaError_t parabolic_setup(int nsm)
 {
     int b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heat, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heat<false>, 256, 0);
     if (e != cudaSuccess) return e;
-    g_heat_blocks = b * nsm;
+    g_heat_blocks[0] = b * nsm;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heat<true>, 256, 0);
+    if (e != cudaSuccess) return e;
+    g_heat_blocks[1] = b * nsm;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_visc<0>, 256, 0);
     if (e != cudaSuccess) return e;
     g_visc_blocks[0] = b * nsm;
@@ -355,8 +383,9 @@ cudaError_t launch_heat(const DevParams &p, double *U, const HeatScratch &s, Sca
     HeatScratch ss = s;
     void *args[] = {(void *)&pp, (void *)&U, (void *)&ss, (void *)&sc, (void *)&dt_host, (void *)&trelax_first,
                     (void *)&check};
-    return cudaLaunchCooperativeKernel((const void *)k_heat, dim3(coop_grid(g_heat_blocks, p.n)), dim3(256), args, 0,
-                                       st);
+    const int var = p.trelax == DIM_TRELAX_MIDPOINT || p.heat_alpha == DIM_HEAT_ALPHA_LINEAR;
+    const void *f = var ? (const void *)k_heat<true> : (const void *)k_heat<false>;
+    return cudaLaunchCooperativeKernel(f, dim3(coop_grid(g_heat_blocks[var], p.n)), dim3(256), args, 0, st);
 }
 
 cudaError_t launch_visc(const DevParams &p, int axis, double *U, const ViscScratch &s, Scalars *sc, double dt_host,

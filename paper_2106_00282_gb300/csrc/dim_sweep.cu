@@ -316,7 +316,7 @@ __global__ void k_relax(const DevParams p, double *__restrict__ U, Scalars *sc, 
             U[7 * n + c] = q[7];
         } else {
             double T, a;
-            s = equilibrium(p, q[0], q[1], q[4] + q[5], T, a);
+            s = trelax_cell(p, q[0], q[1], q[4], q[5], q[7], T, a);
             q[4] = q[0] * p.cv[0] * T + (1.0 - a) * p.pinf[0];
             q[5] = q[1] * p.cv[1] * T + a * p.pinf[1];
             q[7] = a;

@@ -55,6 +55,14 @@ def test_init_rejects_bad_arguments(lib):
         (good.replace(p_policy=1, p_fixed=0), 10, 1, 1e-3, 1e-3),
         (good.replace(n_outer=0), 10, 1, 1e-3, 1e-3),
         (good.replace(bc=(0, 5)), 10, 1, 1e-3, 1e-3),
+        (good.replace(trelax=3), 10, 1, 1e-3, 1e-3),
+        (good.replace(trelax=inputs.TRELAX_MIDPOINT, trelax_iters=0), 10, 1, 1e-3, 1e-3),
+        (good.replace(trelax=inputs.TRELAX_MIDPOINT, trelax_iters=1001), 10, 1, 1e-3, 1e-3),
+        (good.replace(heat_alpha=2), 10, 1, 1e-3, 1e-3),
+        # the paper's variants are FP64 kernels only
+        (good.replace(trelax=inputs.TRELAX_MIDPOINT, precision=inputs.PRECISION_FP32_BULK), 10, 1, 1e-3, 1e-3),
+        (good.replace(heat_alpha=inputs.HEAT_ALPHA_LINEAR, precision=inputs.PRECISION_FP32_BULK), 10, 1, 1e-3,
+         1e-3),
     ]
     for p, nx, ny, dx, dy in cases:
         s = _lib.make_params(p)

@@ -185,6 +185,25 @@ def test_checkpoint_spacing_does_not_change_the_gradient(torch_cuda, I):
     s.close()
 
 
+def test_gradient_rejects_the_paper_variants(torch_cuda, I):
+    """The reverse stages differentiate the exact-equilibrium relaxation and
+    projection; the midpoint relaxation and the linear heat update are
+    refused with DIM_EINVAL, and the context stays usable."""
+    from paper_2106_00282_gb300 import _lib
+
+    torch = torch_cuda
+    for kw in (dict(trelax=I.TRELAX_MIDPOINT, trelax_iters=5), dict(heat_alpha=I.HEAT_ALPHA_LINEAR)):
+        wl = I.smooth_mixture(20, 12, seed=8)
+        wl.params = wl.params.replace(**kw)
+        s = _solver(wl)
+        U0 = s.from_primitive(_dev(torch, wl.prim))
+        with pytest.raises(_lib.DimError) as e:
+            s.grad(U0, 2, torch.ones_like(U0))
+        assert e.value.code == _lib.DIM_EINVAL
+        s.step(U0, 2)
+        s.close()
+
+
 def test_schedule_record_and_replay(torch_cuda, O, I):
     """Recording returns the same state as dim_step; replaying the record on the
     initial state reproduces it; the record equals the oracle's bit for bit."""

@@ -92,7 +92,8 @@ def test_relaxations(torch_cuda, O, I):
     from test_oracle_relax import _nonequilibrium_state
     from paper_2106_00282_gb300 import _lib
 
-    for params in (I.impact(8, 8).params, I.shock_tube().params):
+    mid = dict(trelax=I.TRELAX_MIDPOINT, trelax_iters=7)
+    for params in (I.impact(8, 8).params, I.shock_tube().params, I.impact(8, 8).params.replace(**mid)):
         U0 = _nonequilibrium_state(I, params, 5000, 21, dT=0.3, dp=0.3, dE=1e-3)
         wl = I.Workload("r", 5000, 1, 1.0, 1.0, params, None)
         s = _solver(torch_cuda, wl)
@@ -100,14 +101,20 @@ def test_relaxations(torch_cuda, O, I):
             U = _dev(torch_cuda, U0)
             s.relax(U, which)
             Uo, st = fn(params, U0)
-            assert_parity(_host(U), Uo, 1e-12, f"relax {which}")
+            assert_parity(_host(U), Uo, 1e-12, f"relax {which} trelax mode {params.trelax}")
 
 
-@pytest.mark.parametrize("case", ["disc", "mixture", "periodic", "outer2", "fixedP"])
+@pytest.mark.parametrize("case", ["disc", "mixture", "periodic", "outer2", "fixedP", "linear", "linear_outer3"])
 def test_heat_stage(torch_cuda, O, I, case):
     from paper_2106_00282_gb300 import _lib
 
-    if case == "disc":
+    if case == "linear":
+        wl = I.conduction_disc(n=131, p_min=4, p_max=12)
+        wl.params = wl.params.replace(heat_alpha=I.HEAT_ALPHA_LINEAR)
+    elif case == "linear_outer3":
+        wl = I.conduction_disc(n=72, p_min=5, p_max=12, k_exp=2.5)
+        wl.params = wl.params.replace(heat_alpha=I.HEAT_ALPHA_LINEAR, n_outer=3)
+    elif case == "disc":
         wl = I.conduction_disc(n=131, p_min=4, p_max=12)
     elif case == "mixture":
         wl = I.mixture_shock(n=301)
@@ -120,7 +127,8 @@ def test_heat_stage(torch_cuda, O, I, case):
     else:
         wl = I.shock_tube(n=517)
     s, U, Uo = _init_both(torch_cuda, O, wl)
-    tau = {"disc": 2e-5, "mixture": 1e-6, "periodic": 4e-5, "outer2": 2e-5, "fixedP": 2e-6}[case]
+    tau = {"disc": 2e-5, "mixture": 1e-6, "periodic": 4e-5, "outer2": 2e-5, "fixedP": 2e-6, "linear": 2e-5,
+           "linear_outer3": 2e-5}[case]
     P = s.cheb_parabolic(U, _lib.PARABOLIC_HEAT, tau)
     Uo, st, Po = O.heat(wl.params, Uo, wl.dx, wl.dy, tau)
     assert P == Po
@@ -164,6 +172,13 @@ CASES = {
     "overbee_shock": lambda I: I.shock_tube(n=400, limiter=I.LIMITER_OVERBEE),
     "heat_source": lambda I: _with(I.shock_tube(n=400), src=(1e12, 1e10)),
     "spitzer_like": lambda I: I.conduction_disc(n=96, k_exp=2.5),
+    # the paper's own temperature relaxation (implicit midpoint, simple iteration)
+    # and the linear (T, alpha) update of the heat stage
+    "midpoint_trelax_shock": lambda I: _with(I.shock_tube(n=400), trelax=I.TRELAX_MIDPOINT, trelax_iters=20),
+    "midpoint_trelax_disc_3it": lambda I: _with(I.conduction_disc(n=96), trelax=I.TRELAX_MIDPOINT, trelax_iters=3),
+    "linear_heat_disc": lambda I: _with(I.conduction_disc(n=96), heat_alpha=I.HEAT_ALPHA_LINEAR),
+    "linear_heat_outer2_source": lambda I: _with(I.conduction_disc(n=72, p_min=5, p_max=12),
+                                                 heat_alpha=I.HEAT_ALPHA_LINEAR, n_outer=2, src=(1e9, 1e7)),
 }
 
 
