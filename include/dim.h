@@ -196,9 +196,14 @@ int dim_step_sched(dim_ctx *c, double *U, int nsteps, double *sched, int replay)
  *    dJ_dU0 may alias dJ_dUT; U0 is not modified.
  *  - dJ_dparams: HOST array of DIM_GRAD_NPARAMS doubles, or NULL.
  *  - ckpt_every >= 1: the forward states are kept every ckpt_every steps and
- *    each segment is recomputed from its checkpoint in the reverse sweep;
- *    device memory ~ (nsteps/ckpt_every + ckpt_every + 10) states plus the
- *    Chebyshev iterates of one step, allocated on the first call and reused.
+ *    each segment is replayed once from its checkpoint in the reverse sweep,
+ *    keeping its stage states and Chebyshev iterates: device memory ~
+ *    nsteps/ckpt_every + ckpt_every x (stages per step, <= 9) states plus
+ *    ckpt_every steps' iterates, allocated on the first call and reused.  If
+ *    that exceeds half of the free device memory (or the environment variable
+ *    DIM_GRAD_KEEP_SEGMENT is "0"), each step is replayed a second time instead
+ *    and ~ (nsteps/ckpt_every + ckpt_every + 10) states plus one step's iterates
+ *    suffice.  Both forms give the same gradient bit for bit.
  * Synchronizes.  Errors: DIM_EINVAL (null pointers, nsteps < 0, ckpt_every < 1,
  * FP32-bulk precision, DIM_TRELAX_MIDPOINT, DIM_HEAT_ALPHA_LINEAR: the adjoint
  * differentiates the equilibrium projection), DIM_ENONPHYS / DIM_ENOROOT / DIM_ETIMEOUT when the

@@ -3,12 +3,14 @@
 //
 // dim_grad: a forward pass records the schedule of every step (CFL maximum S,
 // every LIM lambda_max) and keeps the state every ckpt_every steps.  The
-// reverse pass walks the segments backwards: it recomputes the segment's
-// states from its checkpoint, then, step by step from the last, re-runs the
-// step stage by stage with the recorded schedule (the forward kernels, same
-// arithmetic as dim_step, so the same states), keeping each stage's input and
-// every Chebyshev iterate, and applies the stages' adjoint kernels in reverse
-// order (dim_adjoint.cu).
+// reverse pass walks the segments backwards: it replays the segment from its
+// checkpoint stage by stage with the recorded schedule (the forward kernels,
+// same arithmetic as dim_step, so the same states), keeping every stage's
+// input and every Chebyshev iterate of the segment, then applies the stages'
+// adjoint kernels in reverse order (dim_adjoint.cu).  When a segment's stage
+// states do not fit in half of the free device memory, it keeps only the
+// segment's step states and replays each step a second time, stage by stage,
+// just before reversing it.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -129,9 +131,9 @@ static cudaError_t replay_begin(dim_ctx *c, const double *rec)
 }
 
 // One replayed step.  stg == nullptr: X is advanced in place.  Otherwise X is
-// only read: stg[k] (k = 0..nst) receives the input of stage k (stg[0] = X)
-// and stg[nst] the step's result; hist_* (may be null) receive the Chebyshev
-// iterates.
+// only read: stg[k] (k = 0..nst) receives the input of stage k (stg[0] = X;
+// X may be stg itself) and stg[nst] the step's result; hist_* (may be null)
+// receive the Chebyshev iterates.
 static int run_step(dim_ctx *c, const double *rec, double *X, double *stg, double *hist_h, double *hist_v0,
                     double *hist_v1)
 {
@@ -142,7 +144,7 @@ static int run_step(dim_ctx *c, const double *rec, double *X, double *stg, doubl
     const size_t sb = sizeof(double) * 8 * (size_t)c->p.n, n8 = 8 * (size_t)c->p.n;
     cudaStream_t s = c->stream;
     TRY(replay_begin(c, rec));
-    if (stg) TRY(cudaMemcpyAsync(stg, X, sb, cudaMemcpyDeviceToDevice, s));
+    if (stg && stg != X) TRY(cudaMemcpyAsync(stg, X, sb, cudaMemcpyDeviceToDevice, s));
     for (int k = 0; k < nst; k++) {
         double *in = stg ? stg + k * n8 : X;
         double *out = stg ? stg + (k + 1) * n8 : X;
@@ -217,8 +219,6 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
     TRY(ensure(w, GW_SMALL, 8 + (size_t)DIM_SCHED * (nsteps > 0 ? nsteps : 1)));
     double *pbar = w->buf[GW_SMALL], *sched = w->buf[GW_SMALL] + 8;
     TRY(ensure(w, GW_CK, n8 * (nck > 0 ? nck : 1)));
-    TRY(ensure(w, GW_SEG, n8 * (size_t)K));
-    TRY(ensure(w, GW_STG, n8 * (size_t)(nst + 1)));
     TRY(ensure(w, GW_G, 2 * n8));
     const int wp = dimk::adj_visc_work_planes() > dimk::adj_heat_work_planes() ? dimk::adj_visc_work_planes()
                                                                                : dimk::adj_heat_work_planes();
@@ -227,8 +227,10 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
     const size_t nwork = n * (size_t)wp > nfmax * dimk::adj_face_planes() ? n * (size_t)wp
                                                                           : nfmax * dimk::adj_face_planes();
     TRY(ensure(w, GW_WORK, nwork));
-    double *ck = w->buf[GW_CK], *seg = w->buf[GW_SEG], *stg = w->buf[GW_STG];
+    double *ck = w->buf[GW_CK];
     double *G = w->buf[GW_G], *G2 = w->buf[GW_G] + n8, *work = w->buf[GW_WORK];
+    TRY(ensure(w, GW_SEG, n8));
+    double *seg = w->buf[GW_SEG];
 
     // forward pass: record the schedule, keep the checkpoints
     TRY(cudaMemcpyAsync(seg, U0, sb, cudaMemcpyDeviceToDevice, s));
@@ -266,11 +268,33 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
         if (st[k].kind == ST_HEAT) heat = true;
         if (st[k].kind == ST_VISC) visc[st[k].axis] = true;
     }
-    TRY(ensure(w, GW_HH, heat ? n * hh : 1));
-    TRY(ensure(w, GW_HVX, visc[0] ? n * hv[0] : 1));
-    TRY(ensure(w, GW_HVY, visc[1] ? n * hv[1] : 1));
-    double *hist_h = heat ? w->buf[GW_HH] : nullptr;
-    double *hist_v[2] = {visc[0] ? w->buf[GW_HVX] : nullptr, visc[1] ? w->buf[GW_HVY] : nullptr};
+    if (!heat) hh = 0;
+    if (!visc[0]) hv[0] = 0;
+    if (!visc[1]) hv[1] = 0;
+    // Segment storage: when one segment's stage states (K nst + 1 states, the
+    // output of each step being the input of the next) and Chebyshev iterates
+    // fit in half of the free device memory, the reverse pass replays each
+    // segment once, keeping everything; otherwise it keeps the segment's step
+    // states only and replays each step a second time, stage by stage.
+    const size_t per_step_hist = n * (hh + hv[0] + hv[1]);
+    size_t fr = 0, tot = 0;
+    TRY(cudaMemGetInfo(&fr, &tot));
+    const size_t seg_doubles = (size_t)K * ((size_t)nst * n8 + per_step_hist) + n8;
+    const size_t have = w->cap[GW_STG] + w->cap[GW_HH] + w->cap[GW_HVX] + w->cap[GW_HVY] + w->cap[GW_SEG];
+    const char *force = getenv("DIM_GRAD_KEEP_SEGMENT");  // "0": always the two-replay form
+    const bool keep = !(force && force[0] == '0') && seg_doubles * sizeof(double) < (fr + have * sizeof(double)) / 2;
+    const size_t Ks = keep ? (size_t)K : 1;  // steps whose stage states and iterates are kept
+    if (keep) {
+        TRY(ensure(w, GW_STG, (size_t)K * nst * n8 + n8));
+    } else {
+        TRY(ensure(w, GW_SEG, n8 * (size_t)K));
+        TRY(ensure(w, GW_STG, n8 * (size_t)(nst + 1)));
+    }
+    seg = w->buf[GW_SEG];
+    double *stg = w->buf[GW_STG];
+    TRY(ensure(w, GW_HH, Ks * n * hh));
+    TRY(ensure(w, GW_HVX, Ks * n * hv[0]));
+    TRY(ensure(w, GW_HVY, Ks * n * hv[1]));
 
     // reverse pass
     TRY(cudaMemcpyAsync(G, dJ_dUT, sb, cudaMemcpyDeviceToDevice, s));
@@ -279,26 +303,46 @@ int dim_grad(dim_ctx *c, const double *U0, int nsteps, int ckpt_every, const dou
     pf.frozen = 1;
     std::vector<double> b;
     std::vector<int> Ms;
+    // Chebyshev iterates of step t of the current segment (slot 0 when only one step is kept)
+    auto hist_of = [&](int buf, size_t planes, int slot) -> double * {
+        return planes ? w->buf[buf] + (size_t)slot * n * planes : nullptr;
+    };
     for (int sg = nck - 1; sg >= 0; sg--) {
         const int t0 = sg * K, t1 = t0 + K < nsteps ? t0 + K : nsteps;
-        TRY(cudaMemcpyAsync(seg, ck + (size_t)sg * n8, sb, cudaMemcpyDeviceToDevice, s));
-        for (int t = t0; t + 1 < t1; t++) {
-            double *nx = seg + (size_t)(t - t0 + 1) * n8;
-            TRY(cudaMemcpyAsync(nx, seg + (size_t)(t - t0) * n8, sb, cudaMemcpyDeviceToDevice, s));
-            int r = run_step(c, sched + (size_t)DIM_SCHED * t, nx, nullptr, nullptr, nullptr, nullptr);
-            if (r != DIM_OK) return r;
+        if (keep) {
+            // replay the segment once, keeping every stage state and iterate
+            TRY(cudaMemcpyAsync(stg, ck + (size_t)sg * n8, sb, cudaMemcpyDeviceToDevice, s));
+            for (int t = t0; t < t1; t++) {
+                const int j = t - t0;
+                double *sj = stg + (size_t)j * nst * n8;
+                int r = run_step(c, sched + (size_t)DIM_SCHED * t, sj, sj, hist_of(GW_HH, hh, j),
+                                 hist_of(GW_HVX, hv[0], j), hist_of(GW_HVY, hv[1], j));
+                if (r != DIM_OK) return r;
+            }
+        } else {
+            TRY(cudaMemcpyAsync(seg, ck + (size_t)sg * n8, sb, cudaMemcpyDeviceToDevice, s));
+            for (int t = t0; t + 1 < t1; t++) {
+                double *nx = seg + (size_t)(t - t0 + 1) * n8;
+                TRY(cudaMemcpyAsync(nx, seg + (size_t)(t - t0) * n8, sb, cudaMemcpyDeviceToDevice, s));
+                int r = run_step(c, sched + (size_t)DIM_SCHED * t, nx, nullptr, nullptr, nullptr, nullptr);
+                if (r != DIM_OK) return r;
+            }
         }
         for (int t = t1 - 1; t >= t0; t--) {
             const double *r = rec.data() + (size_t)DIM_SCHED * t;
             const double tau = p.cfl / r[0];
-            // the step's stage inputs and Chebyshev iterates
-            {
+            const int slot = keep ? t - t0 : 0;
+            double *hist_h = hist_of(GW_HH, hh, slot);
+            double *hist_v[2] = {hist_of(GW_HVX, hv[0], slot), hist_of(GW_HVY, hv[1], slot)};
+            const double *sg_stg = keep ? stg + (size_t)slot * nst * n8 : stg;
+            if (!keep) {
+                // the step's stage inputs and Chebyshev iterates
                 int rr = run_step(c, sched + (size_t)DIM_SCHED * t, seg + (size_t)(t - t0) * n8, stg, hist_h,
                                   hist_v[0], hist_v[1]);
                 if (rr != DIM_OK) return rr;
             }
             for (int k = nst - 1; k >= 0; k--) {
-                const double *in = stg + (size_t)k * n8;
+                const double *in = sg_stg + (size_t)k * n8;
                 switch (st[k].kind) {
                 case ST_PRELAX: TRY(dimk::adj_prelax(pf, in, G, s)); break;
                 case ST_TRELAX: TRY(dimk::adj_trelax(pf, in, G, s)); break;

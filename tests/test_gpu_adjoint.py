@@ -185,6 +185,27 @@ def test_checkpoint_spacing_does_not_change_the_gradient(torch_cuda, I):
     s.close()
 
 
+@pytest.mark.parametrize("case", ["smooth_2d_periodic", "smooth_2d_transmissive_overbee_nouter2", "shock_tube_20"])
+def test_segment_storage_forms_agree(torch_cuda, I, case, monkeypatch):
+    """Keeping a segment's stage states and Chebyshev iterates (one replay per
+    segment) and keeping its step states only (a second, stage-by-stage replay
+    of each step) give the same gradient bit for bit, for checkpoint spacings
+    that divide the run and that do not."""
+    torch = torch_cuda
+    wl, nsteps = _small_case(I, case)
+    nsteps += 3
+    s = _solver(wl)
+    U0 = s.from_primitive(_dev(torch, wl.prim))
+    g = _dev(torch, _seed_adjoint(U0.cpu().numpy(), 31))
+    for k in (1, 3, nsteps):
+        monkeypatch.delenv("DIM_GRAD_KEEP_SEGMENT", raising=False)
+        a = s.grad(U0, nsteps, g, k)
+        monkeypatch.setenv("DIM_GRAD_KEEP_SEGMENT", "0")
+        b = s.grad(U0, nsteps, g, k)
+        assert torch.equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (case, k)
+    s.close()
+
+
 def test_gradient_rejects_the_paper_variants(torch_cuda, I):
     """The reverse stages differentiate the exact-equilibrium relaxation and
     projection; the midpoint relaxation and the linear heat update are
