@@ -449,7 +449,10 @@ __global__ void __launch_bounds__(256) k_adj_trelax(const DevParams p, const dou
 // cell (ghost positions mapped as in the forward), the transposed Jacobian of
 // the conversion q -> W, the identity of the update and the cell's own
 // R(U_i)(u*_{i+1/2} - u*_{i-1/2}) term.
+// k_adj_sweep_prims first stores every cell's primitives W (line-local order)
+// once, so that the face kernel does not convert each cell four times.
 constexpr int FACE_ADJ_PLANES = 29;  // 4 x 7 primitive adjoints + u*
+constexpr int FACE_WORK_PLANES = FACE_ADJ_PLANES + 7;  // + the primitives W
 
 template <int AXIS>
 __device__ __forceinline__ void line_cell(const DevParams &p, int l, int pos, int &c)
@@ -687,7 +690,24 @@ __device__ __forceinline__ double face_reverse(const DevParams &p, const double 
 }
 
 template <int AXIS>
-__global__ void __launch_bounds__(128) k_adj_sweep_face(const DevParams p, const double *Uin, const double *Gout,
+__global__ void __launch_bounds__(256) k_adj_sweep_prims(const DevParams p, const double *Uin, double *Wp)
+{
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    const int gmap[NQ] = {0, 1, QN, QT, 4, 5, 6, 7};
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        double q[NQ], w[7];
+#pragma unroll
+        for (int j = 0; j < NQ; j++) q[j] = Uin[gmap[j] * n + c];
+        prims_v(p, q, w);
+#pragma unroll
+        for (int j = 0; j < 7; j++) Wp[(size_t)j * n + c] = w[j];
+    }
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(128) k_adj_sweep_face(const DevParams p, const double *Wp, const double *Gout,
                                                         double *fw, double dtdx)
 {
     constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
@@ -705,10 +725,8 @@ __global__ void __launch_bounds__(128) k_adj_sweep_face(const DevParams p, const
         for (int k = 0; k < 4; k++) {
             int c;
             line_cell<AXIS>(p, l, line_map(f - 2 + k, len, bc), c);
-            double q[NQ];
 #pragma unroll
-            for (int j = 0; j < NQ; j++) q[j] = Uin[gmap[j] * n + c];
-            prims_v(p, q, W[k]);
+            for (int j = 0; j < 7; j++) W[k][j] = Wp[(size_t)j * n + c];
         }
         // reconstruction (values and limiter choices as in the forward)
         double wl[7], wr[7];
@@ -1299,17 +1317,20 @@ cudaError_t adj_sweep(const DevParams &p, int axis, const double *Uin, const dou
 {
     const int len = axis == 0 ? p.nx : p.ny, nlines = axis == 0 ? p.ny : p.nx;
     const int nf = (len + 1) * nlines;
+    double *Wp = fw + (size_t)FACE_ADJ_PLANES * nf;  // 7 planes of n <= nf cells
     if (axis == 0) {
-        k_adj_sweep_face<0><<<grid_for(nf, 128), 128, 0, s>>>(p, Uin, Gout, fw, dtdx);
+        k_adj_sweep_prims<0><<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, Wp);
+        k_adj_sweep_face<0><<<grid_for(nf, 128), 128, 0, s>>>(p, Wp, Gout, fw, dtdx);
         k_adj_sweep_cell<0><<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, Gout, fw, Gin, dtdx);
     } else {
-        k_adj_sweep_face<1><<<grid_for(nf, 128), 128, 0, s>>>(p, Uin, Gout, fw, dtdx);
+        k_adj_sweep_prims<1><<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, Wp);
+        k_adj_sweep_face<1><<<grid_for(nf, 128), 128, 0, s>>>(p, Wp, Gout, fw, dtdx);
         k_adj_sweep_cell<1><<<grid_for(p.n, 256), 256, 0, s>>>(p, Uin, Gout, fw, Gin, dtdx);
     }
     return cudaGetLastError();
 }
 
-int adj_face_planes() { return FACE_ADJ_PLANES; }
+int adj_face_planes() { return FACE_WORK_PLANES; }
 
 // planes of the viscous adjoint: 11 work planes W[0..10] (V, mu, u0, w0, ub x2,
 // wb x2, u0b, w0b, Vb) + ab, mub = 13

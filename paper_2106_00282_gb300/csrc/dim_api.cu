@@ -69,14 +69,16 @@ static dimk::HeatScratch heat_scratch(dim_ctx *c)
 {
     size_t n = (size_t)c->p.n;
     double *S = c->S;
-    return dimk::HeatScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n, nullptr};
+    return dimk::HeatScratch{S,         S + n,     S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n,
+                             S + 6 * n, S + 7 * n, nullptr,   S + 8 * n, S + 9 * n};
 }
 
 static dimk::ViscScratch visc_scratch(dim_ctx *c)
 {
     size_t n = (size_t)c->p.n;
     double *S = c->S;
-    return dimk::ViscScratch{S, S + n, S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n, S + 6 * n, S + 7 * n, nullptr};
+    return dimk::ViscScratch{S,         S + n,     S + 2 * n, S + 3 * n, S + 4 * n,  S + 5 * n,
+                             S + 6 * n, S + 7 * n, nullptr,   S + 8 * n, S + 9 * n, S + 10 * n};
 }
 
 static bool fp32(const dim_ctx *c) { return c->p.precision == DIM_PRECISION_FP32_BULK; }
@@ -237,7 +239,7 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
         g_setup_done[dev] = true;
     }
     size_t plane = sizeof(double) * (size_t)p.n;
-    if (cudaMalloc(&c->U2, 8 * plane) != cudaSuccess || cudaMalloc(&c->S, 8 * plane) != cudaSuccess ||
+    if (cudaMalloc(&c->U2, 8 * plane) != cudaSuccess || cudaMalloc(&c->S, dimk::SCRATCH_PLANES * plane) != cudaSuccess ||
         cudaMalloc(&c->sc, sizeof(Scalars)) != cudaSuccess || cudaMemset(c->sc, 0, sizeof(Scalars)) != cudaSuccess ||
         cudaMalloc(&c->beta, sizeof(double) * dimk::PMAX * dimk::PMAX) != cudaSuccess) {
         dim_destroy(c);

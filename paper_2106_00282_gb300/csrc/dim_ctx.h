@@ -51,7 +51,7 @@ struct dim_ctx {
     DevParams p;
     cudaStream_t stream;
     double *U2;   // 8 planes: out-of-place target of the sweeps
-    double *S;    // 8 scratch planes for the parabolic stages
+    double *S;    // dimk::SCRATCH_PLANES scratch planes for the parabolic stages
     double *Uh;   // 8 planes: device copy of a host state (dim_step_host), lazily allocated
     double *beta; // Chebyshev roots table (PMAX x PMAX)
     Scalars *sc;

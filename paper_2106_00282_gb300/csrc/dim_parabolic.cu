@@ -20,22 +20,34 @@ namespace dimk {
 
 
 // (L_h v)_c = Fx_{+} - Fx_{-} + Fy_{+} - Fy_{-}, F = Lam_f (v_R - v_L) / h^2,
-// Lam_f = mean of the two cells (Eq. qk_dis in flux-difference form)
-__device__ __forceinline__ double lap(const DevParams &p, const Nb &nb, int c, const double *v, const double *L)
+// Lam_f = mean of the two cells (Eq. qk_dis in flux-difference form), read from
+// the face planes Lfx, Lfy (the face after each cell; the face before a cell is
+// the face after its predecessor)
+__device__ __forceinline__ double lap(const DevParams &p, const Nb &nb, int c, const double *v, const double *Lfx,
+                                      const double *Lfy)
 {
     double r = 0.0;
-    double vc = v[c], Lc = L[c];
+    double vc = v[c];
     if (p.nx > 1) {
-        double fl = nb.xm >= 0 ? 0.5 * (L[nb.xm] + Lc) * (vc - v[nb.xm]) * p.idx2 : 0.0;
-        double fr = nb.xp >= 0 ? 0.5 * (Lc + L[nb.xp]) * (v[nb.xp] - vc) * p.idx2 : 0.0;
+        double fl = nb.xm >= 0 ? Lfx[nb.xm] * (vc - v[nb.xm]) * p.idx2 : 0.0;
+        double fr = nb.xp >= 0 ? Lfx[c] * (v[nb.xp] - vc) * p.idx2 : 0.0;
         r += fr - fl;
     }
     if (p.ny > 1) {
-        double fl = nb.ym >= 0 ? 0.5 * (L[nb.ym] + Lc) * (vc - v[nb.ym]) * p.idy2 : 0.0;
-        double fr = nb.yp >= 0 ? 0.5 * (Lc + L[nb.yp]) * (v[nb.yp] - vc) * p.idy2 : 0.0;
+        double fl = nb.ym >= 0 ? Lfy[nb.ym] * (vc - v[nb.ym]) * p.idy2 : 0.0;
+        double fr = nb.yp >= 0 ? Lfy[c] * (v[nb.yp] - vc) * p.idy2 : 0.0;
         r += fr - fl;
     }
     return r;
+}
+
+// the face means 0.5 (Lam_c + Lam_next) after cell c along x and y (unused at a wall)
+__device__ __forceinline__ void face_means(const DevParams &p, const Nb &nb, int c, const double *L, double *Lfx,
+                                           double *Lfy)
+{
+    const double Lc = L[c];
+    if (p.nx > 1 && nb.xp >= 0) Lfx[c] = 0.5 * (Lc + L[nb.xp]);
+    if (p.ny > 1 && nb.yp >= 0) Lfy[c] = 0.5 * (Lc + L[nb.yp]);
 }
 
 // Gershgorin row bound 2 V_c sum_f Lam_f / h_f^2 of A = -V L_h
@@ -100,11 +112,16 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
     size_t hoff = 0;  // history planes used by the earlier outer iterations
     for (int it = 0; it < nout; it++) {
         if (!grid_barrier(sc)) return;
-        // B. lambda_max (Gershgorin) of this iteration's frozen operator
-        if (!p.frozen) {
+        // B. face means of Lam and lambda_max (Gershgorin) of this iteration's
+        //    frozen operator
+        {
             double lm = 0.0;
-            for (int c = t0; c < n; c += nt) lm = fmax(lm, gersh(p, neighbours(p, c), c, s.V, s.L));
-            block_max_to(&sc->lam[it], lm);
+            for (int c = t0; c < n; c += nt) {
+                const Nb nb = neighbours(p, c);
+                face_means(p, nb, c, s.L, s.Lfx, s.Lfy);
+                if (!p.frozen) lm = fmax(lm, gersh(p, nb, c, s.V, s.L));
+            }
+            if (!p.frozen) block_max_to(&sc->lam[it], lm);
         }
         if (!grid_barrier(sc)) return;
         double lam = read_acc(&sc->lam[it]);
@@ -129,7 +146,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             const double bm = s_b[m - 1];
             const double rden = 1.0 / (1.0 + tau * bm);
             for (int c = t0; c < n; c += nt) {
-                double Lv = lap(p, neighbours(p, c), c, vin, s.L);
+                double Lv = lap(p, neighbours(p, c), c, vin, s.Lfx, s.Lfy);
                 vout[c] = (s.T0[c] + tau * bm * vin[c] + tau * s.V[c] * Lv + tau * (s.V[c] * s.Ia[c])) * rden;
             }
             if (!grid_barrier(sc)) return;
@@ -143,7 +160,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
         const bool linear = VARIANTS && p.heat_alpha == DIM_HEAT_ALPHA_LINEAR;
         if (it == nout - 1) {
             for (int c = t0; c < n; c += nt) {
-                double q = lap(p, neighbours(p, c), c, vin, s.L) + s.Ia[c];
+                double q = lap(p, neighbours(p, c), c, vin, s.Lfx, s.Lfy) + s.Ia[c];
                 double m1 = U[c], m2 = U[n + c];
                 double rhoe = U[4 * n + c] + U[5 * n + c] + tau * q;
                 double T, a2;
@@ -176,7 +193,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             }
         } else {
             for (int c = t0; c < n; c += nt) {
-                double q = lap(p, neighbours(p, c), c, vin, s.L) + s.Ia[c];
+                double q = lap(p, neighbours(p, c), c, vin, s.Lfx, s.Lfy) + s.Ia[c];
                 double T, a2;
                 if (linear) {
                     const double Tit = it == 0 ? s.T0[c] : s.Ti[c], ait = it == 0 ? U[7 * n + c] : s.Ai[c];
@@ -232,29 +249,36 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
     const double ih = AXIS == 0 ? 1.0 / p.dx : 1.0 / p.dy;
     unsigned st = 0;
 
-    // A. velocities, V = 1/rho, alpha_2 snapshot (read by the face means)
+    // mixture viscosity of a cell from alpha_2 (U is not written before phase D)
+    auto mu_of = [&](int c) {
+        double a2 = U[7 * n + c];
+        return (1.0 - a2) * p.mu[0] + a2 * p.mu[1];
+    };
+    // A. velocities, V = 1/rho, alpha_2 snapshot; face coefficients 4/3 mu_f
+    //    and mu_f (two-cell means) at the face after each cell
     for (int c = t0; c < n; c += nt) {
         double rho = U[c] + U[n + c];
         s.V[c] = 1.0 / rho;
         s.A2[c] = U[7 * n + c];
         s.u0[c] = U[QN * n + c] / rho;
         s.w0[c] = U[QT * n + c] / rho;
+        int cm, cp;
+        visc_nb<AXIS>(p, c, cm, cp);
+        if (cp >= 0) {
+            const double mc = mu_of(c), mr = mu_of(cp);
+            s.LN[c] = 0.5 * (4.0 / 3.0 * mc + 4.0 / 3.0 * mr);
+            s.LM[c] = 0.5 * (mc + mr);
+        }
     }
     if (!grid_barrier(sc)) return;
-    // mixture viscosity of a cell from the alpha snapshot
-    auto mu_of = [&](int c) {
-        double a2 = s.A2[c];
-        return (1.0 - a2) * p.mu[0] + a2 * p.mu[1];
-    };
     // B. lambda_max with the normal coefficient 4/3 mu (bounds the tangential one too)
     if (!p.frozen) {
         double lm = 0.0;
         for (int c = t0; c < n; c += nt) {
             int cm, cp;
             visc_nb<AXIS>(p, c, cm, cp);
-            double lc = 4.0 / 3.0 * mu_of(c);
-            double fl = cm >= 0 ? 0.5 * (4.0 / 3.0 * mu_of(cm) + lc) : 0.0;
-            double fr = cp >= 0 ? 0.5 * (lc + 4.0 / 3.0 * mu_of(cp)) : 0.0;
+            double fl = cm >= 0 ? s.LN[cm] : 0.0;
+            double fr = cp >= 0 ? s.LN[c] : 0.0;
             lm = fmax(lm, 2.0 * s.V[c] * ((fl + fr) * ih2));
         }
         block_max_to(&sc->lam[SLOT], lm);
@@ -280,14 +304,11 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
         for (int c = t0; c < n; c += nt) {
             int cm, cp;
             visc_nb<AXIS>(p, c, cm, cp);
-            double mc = mu_of(c);
-            double mm = cm >= 0 ? 0.5 * (mu_of(cm) + mc) : 0.0;
-            double mp = cp >= 0 ? 0.5 * (mc + mu_of(cp)) : 0.0;
-            double lnm = cm >= 0 ? 0.5 * (4.0 / 3.0 * mu_of(cm) + 4.0 / 3.0 * mc) : 0.0;
-            double lnp = cp >= 0 ? 0.5 * (4.0 / 3.0 * mc + 4.0 / 3.0 * mu_of(cp)) : 0.0;
             double uc = uin[c], wc = win[c];
-            double Lu = (cp >= 0 ? lnp * (uin[cp] - uc) * ih2 : 0.0) - (cm >= 0 ? lnm * (uc - uin[cm]) * ih2 : 0.0);
-            double Lw = (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.0) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.0);
+            double Lu = (cp >= 0 ? s.LN[c] * (uin[cp] - uc) * ih2 : 0.0) -
+                        (cm >= 0 ? s.LN[cm] * (uc - uin[cm]) * ih2 : 0.0);
+            double Lw = (cp >= 0 ? s.LM[c] * (win[cp] - wc) * ih2 : 0.0) -
+                        (cm >= 0 ? s.LM[cm] * (wc - win[cm]) * ih2 : 0.0);
             uo[c] = (s.u0[c] + tau * bm * uc + tau * s.V[c] * Lu) * rden;
             wo[c] = (s.w0[c] + tau * bm * wc + tau * s.V[c] * Lw) * rden;
         }
@@ -295,42 +316,54 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
         uin = uo;
         win = wo;
     }
-    // D. conservative last sweep and energies
+    // D1. the face values of the conservative last sweep, once per face (the
+    //     face after cell c, between c and its successor)
+    const size_t fn = (size_t)n;
     for (int c = t0; c < n; c += nt) {
         int cm, cp;
         visc_nb<AXIS>(p, c, cm, cp);
-        double mc = mu_of(c);
-        double Fn[2], Ft[2], W[2], aF1[2], aF2[2];
-        for (int sd = 0; sd < 2; sd++) {
-            int cl = sd == 0 ? cm : c, cr = sd == 0 ? c : cp;
-            if ((sd == 0 ? cm : cp) < 0) {
-                Fn[sd] = Ft[sd] = W[sd] = 0.0;
-                aF1[sd] = aF2[sd] = 0.0;
-                continue;
-            }
-            double ml = sd == 0 ? mu_of(cm) : mc, mr = sd == 0 ? mc : mu_of(cp);
-            double lnf = 0.5 * (4.0 / 3.0 * ml + 4.0 / 3.0 * mr);
-            double lmf = 0.5 * (ml + mr);
-            Fn[sd] = lnf * (uin[cr] - uin[cl]) * ih;
-            Ft[sd] = lmf * (win[cr] - win[cl]) * ih;
-            double ubar = 0.5 * (uin[cl] + uin[cr]);
-            double wbar = 0.5 * (win[cl] + win[cr]);
-            W[sd] = ubar * Fn[sd] + wbar * Ft[sd];
-            double a2l = s.A2[cl], a2r = s.A2[cr];
-            aF2[sd] = 0.5 * (a2l + a2r);
-            aF1[sd] = 0.5 * ((1.0 - a2l) + (1.0 - a2r));
+        if (cp < 0) continue;
+        const int cl = c, cr = cp;
+        double Fn = s.LN[c] * (uin[cr] - uin[cl]) * ih;
+        double Ft = s.LM[c] * (win[cr] - win[cl]) * ih;
+        double ubar = 0.5 * (uin[cl] + uin[cr]);
+        double wbar = 0.5 * (win[cl] + win[cr]);
+        double W = ubar * Fn + wbar * Ft;
+        double a2l = s.A2[cl], a2r = s.A2[cr];
+        double aF2 = 0.5 * (a2l + a2r);
+        double aF1 = 0.5 * ((1.0 - a2l) + (1.0 - a2r));
+        s.F[VF_FN * fn + c] = Fn;
+        s.F[VF_FT * fn + c] = Ft;
+        s.F[VF_W * fn + c] = W;
+        s.F[VF_A1W * fn + c] = aF1 * W;
+        s.F[VF_A1FN * fn + c] = aF1 * Fn;
+        s.F[VF_A1FT * fn + c] = aF1 * Ft;
+        s.F[VF_A2W * fn + c] = aF2 * W;
+        s.F[VF_A2FN * fn + c] = aF2 * Fn;
+        s.F[VF_A2FT * fn + c] = aF2 * Ft;
+    }
+    if (!grid_barrier(sc)) return;
+    // D2. conservative update and energies of each cell from its two faces
+    for (int c = t0; c < n; c += nt) {
+        int cm, cp;
+        visc_nb<AXIS>(p, c, cm, cp);
+        double f[2][VF_N];
+#pragma unroll
+        for (int k = 0; k < VF_N; k++) {
+            f[0][k] = cm >= 0 ? s.F[k * fn + cm] : 0.0;
+            f[1][k] = cp >= 0 ? s.F[k * fn + c] : 0.0;
         }
         double uh = uin[c], wh = win[c];
         double q[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
-        q[QN] = q[QN] + tau * (Fn[1] - Fn[0]) * ih;
-        q[QT] = q[QT] + tau * (Ft[1] - Ft[0]) * ih;
-        q[6] = q[6] + tau * (W[1] - W[0]) * ih;
-        q[4] = q[4] + tau * (aF1[1] * W[1] - aF1[0] * W[0]) * ih -
-               tau * (uh * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + wh * (aF1[1] * Ft[1] - aF1[0] * Ft[0])) * ih;
-        q[5] = q[5] + tau * (aF2[1] * W[1] - aF2[0] * W[0]) * ih -
-               tau * (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) * ih;
+        q[QN] = q[QN] + tau * (f[1][VF_FN] - f[0][VF_FN]) * ih;
+        q[QT] = q[QT] + tau * (f[1][VF_FT] - f[0][VF_FT]) * ih;
+        q[6] = q[6] + tau * (f[1][VF_W] - f[0][VF_W]) * ih;
+        q[4] = q[4] + tau * (f[1][VF_A1W] - f[0][VF_A1W]) * ih -
+               tau * (uh * (f[1][VF_A1FN] - f[0][VF_A1FN]) + wh * (f[1][VF_A1FT] - f[0][VF_A1FT])) * ih;
+        q[5] = q[5] + tau * (f[1][VF_A2W] - f[0][VF_A2W]) * ih -
+               tau * (uh * (f[1][VF_A2FN] - f[0][VF_A2FN]) + wh * (f[1][VF_A2FT] - f[0][VF_A2FT])) * ih;
         if (relax) {
             unsigned r = prelax(p, q);
             if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
