@@ -372,23 +372,25 @@ __global__ void __launch_bounds__(256) k_adj_prelax(const DevParams p, const dou
         const double rhoe = rE - ke;
         const double Nn = rhoe - (a1n * c1 + a2n * c2), Dd = a1n * i1 + a2n * i2;
         const double p2 = Nn / Dd;
-        // reverse
+        // reverse (shared reciprocals: the adjoint needs no bit-compatibility)
         const double G4 = G[4 * n + c], G5 = G[5 * n + c], G7 = G[7 * n + c];
         const double p2b = G4 * a1n * i1 + G5 * a2n * i2;
         double a1nb = G4 * (p2 + ek1) * i1;
         double a2nb = G5 * (p2 + ek2) * i2 + G7;
-        const double Nb = p2b / Dd, Db = -p2b * p2 / Dd;
+        const double rD = 1.0 / Dd, rr = 1.0 / rho, rY = 1.0 / Ya;
+        const double Nb = p2b * rD, Db = -p2b * p2 * rD;
         const double rhoeb = Nb;
         a1nb += -Nb * c1 + Db * i1;
         a2nb += -Nb * c2 + Db * i2;
         a2nb -= a1nb;
         const double rEb = rhoeb;
-        const double mub = -rhoeb * mu / rho, mvb = -rhoeb * mv / rho;
-        const double rhob = rhoeb * ke / rho;
-        const double Xb = a2nb / Ya, Yb = -a2nb * a2n / Ya;
+        const double mub = -rhoeb * mu * rr, mvb = -rhoeb * mv * rr;
+        const double rhob = rhoeb * ke * rr;
+        const double Xb = a2nb * rY, Yb = -a2nb * a2n * rY;
         double ak2b = Xb, bk2b = Xb * pr;
         const double prb = Xb * bk2 + Yb * g2;
-        const double Ab = -prb * pr * pr / sq, Bb = -prb * pr / sq, Cb = -prb / sq;
+        const double w = prb / sq;
+        const double Ab = -w * pr * pr, Bb = -w * pr, Cb = -w;
         double bk1b = -Ab * g2;
         bk2b += -Ab * g1;
         double ak1b = -Bb * g2;
@@ -536,8 +538,9 @@ __device__ __forceinline__ void face_rev(const DevParams &p, const FaceV &s, con
     utb += qb[6] * s.rho * s.ut;
     // c = sqrt(X / rho)
     const double c2b = cb / (2.0 * s.c);
-    const double Xb = c2b / s.rho;
-    rhob -= c2b * (s.X / s.rho) / s.rho;
+    const double ir = 1.0 / s.rho;
+    const double Xb = c2b * ir;
+    rhob -= c2b * (s.X * ir) * ir;
     a1b += Xb * s.A1;
     a2b += Xb * s.A2;
     p1b += Xb * s.a1 * p.g[0];
@@ -645,8 +648,9 @@ __device__ __forceinline__ double face_reverse(const DevParams &p, const double 
         const double eb1 = gb * fv, fb = gb * e;
         rhoKb += fb * Ss;
         Ssb += fb * K.rho;
-        pKb += fb / t;
-        tb -= fb * K.p / (t * t);
+        const double it = 1.0 / t;
+        pKb += fb * it;
+        tb -= fb * K.p * it * it;
         Ssb += eb1;
         unKb -= eb1;
         qbK[7] += qs_b[7];
@@ -658,13 +662,15 @@ __device__ __forceinline__ double face_reverse(const DevParams &p, const double 
         Ssb += eb2;
         unKb -= eb2;
         // chi = t / d2, d2 = SK - Ss, t = SK - unK
-        const double d1b = chib / d2, d2b = -chib * chi / d2;
+        const double id2 = 1.0 / d2;
+        const double d1b = chib * id2, d2b = -chib * chi * id2;
         tb += d1b;
         double SKb = d2b + tb;
         Ssb -= d2b;
         unKb -= tb;
         // Ss = num / den
-        const double numb = Ssb / den, denb = -Ssb * Ss / den;
+        const double iden = 1.0 / den;
+        const double numb = Ssb * iden, denb = -Ssb * Ss * iden;
         double SLb = 0.0, SRb = 0.0;
         pRb += numb;
         pLb -= numb;
@@ -902,23 +908,40 @@ __global__ void __launch_bounds__(256) k_adj_visc_prep(const DevParams p, const 
 // the contribution of face (l, r) to J through the conservative last sweep:
 // S = sum over s in {l (+), r (-)} of sign_s tau/h [G_s^n Fn + G_s^t Ft +
 //     G_s^E W + (G_s^E1 aF1 + G_s^E2 aF2)(W - uh_s Fn - wh_s Ft)]
-// with inputs x = (uh_l, uh_r, wh_l, wh_r, a_l, a_r, mu_l, mu_r)
-// (ih = 1/h; the factor tau/h of the update is folded into Gl, Gr by the caller)
-__device__ __forceinline__ Dn<8> visc_face_J(const double *x, const double *Gl, const double *Gr, double ih)
+// with inputs x = (uh_l, uh_r, wh_l, wh_r, a_l, a_r, mu_l, mu_r); xb = dS/dx
+// by the hand-written reverse (ih = 1/h; the factor tau/h of the update is
+// folded into Gl, Gr by the caller)
+__device__ __forceinline__ void visc_face_J(const double *x, const double *Gl, const double *Gr, double ih,
+                                            double *xb)
 {
-    Dn<8> ul = dseed<8>(x[0], 0), ur = dseed<8>(x[1], 1), wl = dseed<8>(x[2], 2), wr = dseed<8>(x[3], 3);
-    Dn<8> al = dseed<8>(x[4], 4), ar = dseed<8>(x[5], 5), ml = dseed<8>(x[6], 6), mr = dseed<8>(x[7], 7);
-    Dn<8> lnf = 0.5 * (4.0 / 3.0 * ml + 4.0 / 3.0 * mr);
-    Dn<8> lmf = 0.5 * (ml + mr);
-    Dn<8> Fn = lnf * (ur - ul) * ih;
-    Dn<8> Ft = lmf * (wr - wl) * ih;
-    Dn<8> W = 0.5 * (ul + ur) * Fn + 0.5 * (wl + wr) * Ft;
-    Dn<8> aF2 = 0.5 * (al + ar);
-    Dn<8> aF1 = 0.5 * ((1.0 - al) + (1.0 - ar));
+    const double ul = x[0], ur = x[1], wl = x[2], wr = x[3], al = x[4], ar = x[5], ml = x[6], mr = x[7];
+    // forward values
+    const double lnf = 0.5 * (4.0 / 3.0 * ml + 4.0 / 3.0 * mr);
+    const double lmf = 0.5 * (ml + mr);
+    const double Fn = lnf * (ur - ul) * ih;
+    const double Ft = lmf * (wr - wl) * ih;
+    const double um = 0.5 * (ul + ur), wm = 0.5 * (wl + wr);
+    const double W = um * Fn + wm * Ft;
+    const double aF2 = 0.5 * (al + ar);
+    const double aF1 = 0.5 * ((1.0 - al) + (1.0 - ar));
     // Gl/Gr: (G^n, G^t, G^E, G^E1, G^E2) of the two cells, each already times tau/h
-    Dn<8> Sl = Gl[0] * Fn + Gl[1] * Ft + Gl[2] * W + (Gl[3] * aF1 + Gl[4] * aF2) * (W - ul * Fn - wl * Ft);
-    Dn<8> Sr = Gr[0] * Fn + Gr[1] * Ft + Gr[2] * W + (Gr[3] * aF1 + Gr[4] * aF2) * (W - ur * Fn - wr * Ft);
-    return Sl - Sr;
+    const double Kl = Gl[3] * aF1 + Gl[4] * aF2, Kr = Gr[3] * aF1 + Gr[4] * aF2;
+    const double Dl = W - ul * Fn - wl * Ft, Dr = W - ur * Fn - wr * Ft;
+    // reverse of S = Sl - Sr
+    const double Dlb = Kl, Drb = -Kr;
+    const double Wb = Gl[2] - Gr[2] + Dlb + Drb;
+    const double Fnb = Gl[0] - Gr[0] - Dlb * ul - Drb * ur + Wb * um;
+    const double Ftb = Gl[1] - Gr[1] - Dlb * wl - Drb * wr + Wb * wm;
+    const double aF1b = Dl * Gl[3] - Dr * Gr[3], aF2b = Dl * Gl[4] - Dr * Gr[4];
+    const double umb = Wb * Fn, wmb = Wb * Ft;
+    const double fu = Fnb * lnf * ih, fw = Ftb * lmf * ih;
+    xb[0] = -Dlb * Fn + 0.5 * umb - fu;
+    xb[1] = -Drb * Fn + 0.5 * umb + fu;
+    xb[2] = -Dlb * Ft + 0.5 * wmb - fw;
+    xb[3] = -Drb * Ft + 0.5 * wmb + fw;
+    xb[4] = xb[5] = 0.5 * aF2b - 0.5 * aF1b;
+    const double lnfb = Fnb * (ur - ul) * ih, lmfb = Ftb * (wr - wl) * ih;
+    xb[6] = xb[7] = lnfb * (0.5 * (4.0 / 3.0)) + 0.5 * lmfb;
 }
 
 template <int AXIS>
@@ -945,13 +968,14 @@ __global__ void __launch_bounds__(128) k_adj_visc_final(const DevParams p, const
                             tih * G[5 * n + l]};
             double Gr[5] = {tih * G[QN * n + r], tih * G[QT * n + r], tih * G[6 * n + r], tih * G[4 * n + r],
                             tih * G[5 * n + r]};
-            Dn<8> S = visc_face_J(x, Gl, Gr, ih);
+            double xb[8];
+            visc_face_J(x, Gl, Gr, ih, xb);
             // this cell is r of the minus face, l of the plus face
             const int o = sd == 0 ? 1 : 0;
-            su += S.d[0 + o];
-            sw += S.d[2 + o];
-            sa += S.d[4 + o];
-            sm += S.d[6 + o];
+            su += xb[0 + o];
+            sw += xb[2 + o];
+            sa += xb[4 + o];
+            sm += xb[6 + o];
         }
 #pragma unroll
         for (int k = 0; k < NQ; k++) Gin[k * n + c] = G[k * n + c];
