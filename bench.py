@@ -350,6 +350,26 @@ def run_adjoint(dev, world=1, steps=None, ckpt=None):
             "params_grad": [float(x) for x in gp]}
 
 
+def host_cpu():
+    """nproc and the CPU model of the host (from /proc/cpuinfo; Arm cores by implementer and part)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for line in info.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+        if model is None:
+            imp = [l.split(":", 1)[1].strip() for l in info.splitlines() if l.startswith("CPU implementer")]
+            part = [l.split(":", 1)[1].strip() for l in info.splitlines() if l.startswith("CPU part")]
+            if imp and part:
+                model = f"Arm implementer {imp[0]} part {part[0]}"
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def oracle_rate(wl, budget_s=10.0, max_steps=1000):
     """FP64 oracle (single-threaded C) on the same workload: steps until the budget."""
     from oracle import oracle as O
@@ -402,7 +422,8 @@ def main():
             rate, nst, el = oracle_rate(I.bench_workload(args.workload))
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{nst} oracle steps of the full {wl.nx}x{wl.ny} grid from the initial state "
-                             f"({el:.1f} s, single-threaded C, -O2 -ffp-contract=off)"}
+                             f"({el:.1f} s, single-threaded C, -O2 -ffp-contract=off)",
+                   "host": host_cpu()}
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -451,7 +472,8 @@ def main_reference(args, rank, world):
             "config": workload_desc(wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full oracle steps of the {wl.nx}x{wl.ny} grid after "
-                                       f"{max(3, args.warmup)} warm-up steps"},
+                                       f"{max(3, args.warmup)} warm-up steps",
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
