@@ -69,8 +69,9 @@ static dimk::HeatScratch heat_scratch(dim_ctx *c)
 {
     size_t n = (size_t)c->p.n;
     double *S = c->S;
-    return dimk::HeatScratch{S,         S + n,     S + 2 * n, S + 3 * n, S + 4 * n, S + 5 * n,
-                             S + 6 * n, S + 7 * n, nullptr,   S + 8 * n, S + 9 * n};
+    return dimk::HeatScratch{S,         S + n,     S + 2 * n, S + 3 * n,  S + 4 * n,  S + 5 * n,
+                             S + 6 * n, S + 7 * n, nullptr,   S + 8 * n,  S + 9 * n,  S + 10 * n,
+                             S + 11 * n};
 }
 
 static dimk::ViscScratch visc_scratch(dim_ctx *c)
@@ -78,7 +79,8 @@ static dimk::ViscScratch visc_scratch(dim_ctx *c)
     size_t n = (size_t)c->p.n;
     double *S = c->S;
     return dimk::ViscScratch{S,         S + n,     S + 2 * n, S + 3 * n, S + 4 * n,  S + 5 * n,
-                             S + 6 * n, S + 7 * n, nullptr,   S + 8 * n, S + 9 * n, S + 10 * n};
+                             S + 6 * n, S + 7 * n, nullptr,   S + 8 * n, S + 9 * n, S + 10 * n,
+                             S + (10 + dimk::VF_N) * n};
 }
 
 static bool fp32(const dim_ctx *c) { return c->p.precision == DIM_PRECISION_FP32_BULK; }

@@ -65,6 +65,7 @@ struct HeatScratch {
     double *T0, *V, *L, *va, *vb, *Ti, *Ai, *Ia;  // Ia = a1 I1 + a2 I2 (external source)
     double *hist;
     double *Lfx, *Lfy;  // face means of Lam at the face after each cell along x, y
+    double *tV, *tf;    // tau V and tau (V Ia) of each cell (the LIM sweeps' coefficients)
 };
 // planes of the viscous stage's per-face values, stored at the face after each cell
 enum { VF_FN, VF_FT, VF_W, VF_A1W, VF_A1FN, VF_A1FT, VF_A2W, VF_A2FN, VF_A2FT, VF_N };
@@ -73,8 +74,9 @@ struct ViscScratch {
     double *hist;
     double *LN, *LM;  // face coefficients 4/3 mu_f and mu_f
     double *F;        // VF_N face planes of the conservative last sweep
+    double *tV;       // tau V of each cell
 };
-constexpr int SCRATCH_PLANES = 8 + 2 + VF_N;  // parabolic scratch of a context
+constexpr int SCRATCH_PLANES = 8 + 2 + VF_N + 1;  // parabolic scratch of a context
 
 __device__ __forceinline__ double dmax_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
 

@@ -106,7 +106,10 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
         heat_coeffs(p, m1, m2, T, a2, V, L);
         s.V[c] = V;
         s.L[c] = L;
-        s.Ia[c] = (1.0 - a2) * p.src[0] + a2 * p.src[1];
+        const double Ia = (1.0 - a2) * p.src[0] + a2 * p.src[1];
+        s.Ia[c] = Ia;
+        s.tV[c] = tau * V;
+        s.tf[c] = tau * (V * Ia);
     }
 
     size_t hoff = 0;  // history planes used by the earlier outer iterations
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
             const double rden = 1.0 / (1.0 + tau * bm);
             for (int c = t0; c < n; c += nt) {
                 double Lv = lap(p, neighbours(p, c), c, vin, s.Lfx, s.Lfy);
-                vout[c] = (s.T0[c] + tau * bm * vin[c] + tau * s.V[c] * Lv + tau * (s.V[c] * s.Ia[c])) * rden;
+                vout[c] = (s.T0[c] + tau * bm * vin[c] + s.tV[c] * Lv + s.tf[c]) * rden;
             }
             if (!grid_barrier(sc)) return;
             vin = vout;
@@ -214,7 +217,10 @@ __global__ void __launch_bounds__(256) k_heat(const DevParams p, double *U, Heat
                 heat_coeffs(p, U[c], U[n + c], s.Ti[c], s.Ai[c], V, L);
                 s.V[c] = V;
                 s.L[c] = L;
-                s.Ia[c] = (1.0 - s.Ai[c]) * p.src[0] + s.Ai[c] * p.src[1];
+                const double Ia = (1.0 - s.Ai[c]) * p.src[0] + s.Ai[c] * p.src[1];
+                s.Ia[c] = Ia;
+                s.tV[c] = tau * V;
+                s.tf[c] = tau * (V * Ia);
             }
         }
     }
@@ -258,7 +264,9 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
     //    and mu_f (two-cell means) at the face after each cell
     for (int c = t0; c < n; c += nt) {
         double rho = U[c] + U[n + c];
-        s.V[c] = 1.0 / rho;
+        const double V = 1.0 / rho;
+        s.V[c] = V;
+        s.tV[c] = tau * V;
         s.A2[c] = U[7 * n + c];
         s.u0[c] = U[QN * n + c] / rho;
         s.w0[c] = U[QT * n + c] / rho;
@@ -309,8 +317,8 @@ __global__ void __launch_bounds__(256) k_visc(const DevParams p, double *U, Visc
                         (cm >= 0 ? s.LN[cm] * (uc - uin[cm]) * ih2 : 0.0);
             double Lw = (cp >= 0 ? s.LM[c] * (win[cp] - wc) * ih2 : 0.0) -
                         (cm >= 0 ? s.LM[cm] * (wc - win[cm]) * ih2 : 0.0);
-            uo[c] = (s.u0[c] + tau * bm * uc + tau * s.V[c] * Lu) * rden;
-            wo[c] = (s.w0[c] + tau * bm * wc + tau * s.V[c] * Lw) * rden;
+            uo[c] = (s.u0[c] + tau * bm * uc + s.tV[c] * Lu) * rden;
+            wo[c] = (s.w0[c] + tau * bm * wc + s.tV[c] * Lw) * rden;
         }
         if (!grid_barrier(sc)) return;
         uin = uo;
