@@ -551,15 +551,19 @@ static void line_update(const prm<R> *P, int n, double dtdx, const R *ext, R *ou
         hllc(&sl, &sr, F + NQ * f, us + f);
     }
     /* Godunov update with the non-conservative term R(U_i^n)(u*_{i+1/2} - u*_{i-1/2}),
-     * R = [0 0 0 0 a1p1 a2p2 0 -a2] (Sec. 3.1) */
+     * R = [0 0 0 0 a1p1 a2p2 0 -a2] (Sec. 3.1): only the phase-energy and
+     * volume-fraction rows carry it */
     for (int i = 0; i < n; i++) {
         const R *q = ext + NQ * (i + 2);
         const R *w = W + 7 * (i + 2);
         R a2 = w[0], a1 = 1.0 - a2;
         R Rv[NQ] = {R(0.0), R(0.0), R(0.0), R(0.0), a1 * w[5], a2 * w[6], R(0.0), -a2};
         R du = us[i + 1] - us[i];
-        for (int k = 0; k < NQ; k++)
-            out[NQ * i + k] = q[k] - dtdx * (F[NQ * (i + 1) + k] - F[NQ * i + k]) - dtdx * Rv[k] * du;
+        for (int k = 0; k < NQ; k++) {
+            R v = q[k] - dtdx * (F[NQ * (i + 1) + k] - F[NQ * i + k]);
+            if (k == 4 || k == 5 || k == 7) v = v - dtdx * Rv[k] * du;
+            out[NQ * i + k] = v;
+        }
     }
     free(W); free(S); free(F); free(us);
 }

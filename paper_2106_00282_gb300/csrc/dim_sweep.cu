@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(TN *TL) k_sweep(const DevParams p, const doubl
     double *sU = smem;         // [8][NL]
     double *sW = sU + NQ * NL;  // [7][NL]
     double *sF = sW + 7 * NL;   // [9][NF]
+    double *sS = sF + 9 * NF;   // [7][NL] limited slopes (twice minmod for Overbee on alpha_2, m1, m2)
     const int n = p.n;
     const int len = AXIS == 0 ? p.nx : p.ny;
     const int ntr = AXIS == 0 ? p.ny : p.nx;
@@ -165,6 +166,27 @@ __global__ void __launch_bounds__(TN *TL) k_sweep(const DevParams p, const doubl
     }
     __syncthreads();
 
+    // 1b. the limited slope of every cell with both neighbours in the tile, once
+    //     per cell (each is used by the faces on both sides)
+    const bool lim = p.limiter != DIM_LIMITER_NONE, ob = p.limiter == DIM_LIMITER_OVERBEE;
+    if (lim) {
+        for (int li = threadIdx.x; li < NL; li += blockDim.x) {
+            int e, l;
+            if (AXIS == 0) { l = li / NE; e = li - l * NE; }
+            else { e = li / TL; l = li - e * TL; }
+            if (e < 1 || e > NE - 2) continue;
+            const int im = cidx(e - 1, l), ip = cidx(e + 1, l);
+#pragma unroll
+            for (int k = 0; k < 7; k++) {
+                const double *Wk = sW + k * NL;
+                double sl = minmod(Wk[li] - Wk[im], Wk[ip] - Wk[li]);
+                if (ob && k <= 2) sl = 2.0 * sl;  // Overbee on alpha_2, m1, m2: twice the minmod slope
+                sS[k * NL + li] = sl;
+            }
+        }
+        __syncthreads();
+    }
+
     // 2. face fluxes: face f of line l lies between cells e = f+1 and e = f+2
     for (int fi = threadIdx.x; fi < NF; fi += blockDim.x) {
         int f, l;
@@ -172,20 +194,12 @@ __global__ void __launch_bounds__(TN *TL) k_sweep(const DevParams p, const doubl
         else { f = fi / TL; l = fi - f * TL; }
         const int iL = cidx(f + 1, l), iR = cidx(f + 2, l);
         double wl[7], wr[7];
-        if (p.limiter != DIM_LIMITER_NONE) {
-            const int iLL = cidx(f, l), iRR = cidx(f + 3, l);
-            const bool ob = p.limiter == DIM_LIMITER_OVERBEE;
+        if (lim) {
 #pragma unroll
             for (int k = 0; k < 7; k++) {
                 const double *Wk = sW + k * NL;
-                double sl = minmod(Wk[iL] - Wk[iLL], Wk[iR] - Wk[iL]);
-                double sr = minmod(Wk[iR] - Wk[iL], Wk[iRR] - Wk[iR]);
-                if (ob && k <= 2) {  // Overbee on alpha_2, m1, m2: twice the minmod slope
-                    sl = 2.0 * sl;
-                    sr = 2.0 * sr;
-                }
-                wl[k] = Wk[iL] + 0.5 * sl;
-                wr[k] = Wk[iR] - 0.5 * sr;
+                wl[k] = Wk[iL] + 0.5 * sS[k * NL + iL];
+                wr[k] = Wk[iR] - 0.5 * sS[k * NL + iR];
             }
         } else {
 #pragma unroll
@@ -220,8 +234,10 @@ __global__ void __launch_bounds__(TN *TL) k_sweep(const DevParams p, const doubl
         double du = sF[8 * NF + fp] - sF[8 * NF + fm];
         double qo[NQ];
 #pragma unroll
-        for (int k = 0; k < NQ; k++)
-            qo[k] = sU[k * NL + ci] - dtdx * (sF[k * NF + fp] - sF[k * NF + fm]) - dtdx * Rv[k] * du;
+        for (int k = 0; k < NQ; k++) {
+            qo[k] = sU[k * NL + ci] - dtdx * (sF[k * NF + fp] - sF[k * NF + fm]);
+            if (k == 4 || k == 5 || k == 7) qo[k] = qo[k] - dtdx * Rv[k] * du;  // the rows R is nonzero in
+        }
         // back to the global plane order
         double q[NQ] = {qo[0], qo[1], 0.0, 0.0, qo[4], qo[5], qo[6], qo[7]};
         q[QN] = qo[2];
@@ -336,7 +352,7 @@ __global__ void k_relax(const DevParams p, double *__restrict__ U, Scalars *sc, 
 constexpr int SX_TN = 128, SX_TL = 1;
 constexpr int SY_TN = 32, SY_TL = 8;
 
-static size_t sweep_smem(int TN, int TL) { return sizeof(double) * ((TN + 4) * TL * (NQ + 7) + (TN + 1) * TL * 9); }
+static size_t sweep_smem(int TN, int TL) { return sizeof(double) * ((TN + 4) * TL * (NQ + 7 + 7) + (TN + 1) * TL * 9); }
 
 cudaError_t sweep_setup()
 {

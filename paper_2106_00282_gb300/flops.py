@@ -8,7 +8,7 @@ the limit of a large grid (ghost cells of the sweeps and boundary faces
 excluded).  tests/test_flops.py checks every entry below against that count.
 
 per cell                                   1D      2D
-  sweep, one axis (no limiter / minmod / Overbee)   201 / 215 / 218
+  sweep, one axis (no limiter / minmod / Overbee)   186 / 200 / 203
   pressure relaxation (Sec. 3.3)                    62
   temperature relaxation (Sec. 3.4.1)               36
   CFL maximum                              21      24
@@ -23,7 +23,7 @@ viscous kernel of the last axis ends with the pressure relaxation.
 """
 from __future__ import annotations
 
-SWEEP = {0: 201, 1: 215, 2: 218}   # by limiter: none, minmod, Overbee
+SWEEP = {0: 186, 1: 200, 2: 203}   # by limiter: none, minmod, Overbee
 PRELAX = 62
 TRELAX = 36
 WAVE = {1: 21, 2: 24}              # by number of active axes
