@@ -349,8 +349,17 @@ __global__ void k_relax(const DevParams p, double *__restrict__ U, Scalars *sc, 
 // ---------------------------------------------------------------------------
 // host-side launchers (called from dim_api.cu)
 // ---------------------------------------------------------------------------
-constexpr int SX_TN = 128, SX_TL = 1;
-constexpr int SY_TN = 32, SY_TL = 8;
+// tile shapes (cells along the sweep x lines); a build may override them
+#ifndef DIM_SX_TN
+#define DIM_SX_TN 256
+#define DIM_SX_TL 1
+#endif
+#ifndef DIM_SY_TN
+#define DIM_SY_TN 32
+#define DIM_SY_TL 8
+#endif
+constexpr int SX_TN = DIM_SX_TN, SX_TL = DIM_SX_TL;
+constexpr int SY_TN = DIM_SY_TN, SY_TL = DIM_SY_TL;
 
 static size_t sweep_smem(int TN, int TL) { return sizeof(double) * ((TN + 4) * TL * (NQ + 7 + 7) + (TN + 1) * TL * 9); }
 
