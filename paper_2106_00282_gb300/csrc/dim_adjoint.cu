@@ -1177,34 +1177,66 @@ __global__ void __launch_bounds__(256) k_adj_heat_q(const DevParams p, const dou
     }
 }
 
-// one reverse predictor sweep: vprev = v^{m-1}; y = vbar^m / (1 + tau b_m)
-// and z = V y are formed on the fly at the cell and its neighbours
-__global__ void __launch_bounds__(256) k_adj_heat_lim(const DevParams p, const double *V, const double *L,
-                                                      const double *Ia, const double *vprev, const double *vbi,
-                                                      double *vbo, double *T0b, double *Vb, double *Lb, double *Iab,
-                                                      double tau, double bm, double rden)
+// face coefficients of the frozen operator times 1/h^2: Lx[c] = (Lam_c +
+// Lam_{c+x})/2 / dx^2 at the face after c (0 at a wall), Ly likewise
+__global__ void __launch_bounds__(256) k_adj_heat_faces(const DevParams p, const double *L, double *Lx, double *Ly)
 {
     const int n = p.n;
     GRID_LOOP(c, n)
     {
-        const double y = rden * vbi[c], zc = V[c] * y, Lc = L[c], vc = vprev[c];
+        int cm, cp;
+        axis_nb(p, 0, c, cm, cp);
+        Lx[c] = cp >= 0 ? 0.5 * (L[c] + L[cp]) * p.idx2 : 0.0;
+        axis_nb(p, 1, c, cm, cp);
+        Ly[c] = cp >= 0 ? 0.5 * (L[c] + L[cp]) * p.idy2 : 0.0;
+    }
+}
+
+// z = V (vbar / (1 + tau b)) of the first reverse sweep
+__global__ void __launch_bounds__(256) k_adj_heat_z(const DevParams p, const double *V, const double *vb, double *z,
+                                                    double rden)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n) z[c] = V[c] * (rden * vb[c]);
+}
+
+// one reverse predictor sweep: vprev = v^{m-1}; y = vbar^m / (1 + tau b_m),
+// z = V y (formed by the previous sweep for every cell); writes vbar^{m-1} and
+// the next sweep's z (rden_next = 1/(1 + tau b_{m-1}))
+__global__ void __launch_bounds__(256) k_adj_heat_lim(const DevParams p, const double *V, const double *Lx,
+                                                      const double *Ly, const double *Ia, const double *vprev,
+                                                      const double *vbi, const double *z, double *vbo, double *znext,
+                                                      double *T0b, double *Vb, double *Lb, double *Iab, double tau,
+                                                      double bm, double rden, double rden_next)
+{
+    const int n = p.n;
+    GRID_LOOP(c, n)
+    {
+        const double y = rden * vbi[c], zc = z[c], vc = vprev[c];
         double lz = 0.0, lv = 0.0, fl = 0.0;
         for (int ax = 0; ax < 2; ax++) {
             int cm, cp;
             axis_nb(p, ax, c, cm, cp);
+            const double *Lf = ax == 0 ? Lx : Ly;
             const double ih2 = ax == 0 ? p.idx2 : p.idy2;
-            for (int sd = 0; sd < 2; sd++) {
-                const int nb = sd == 0 ? cm : cp;
-                if (nb < 0) continue;
-                const double Lf = 0.5 * (L[nb] + Lc);
-                const double zn = V[nb] * (rden * vbi[nb]);
-                const double dv = vprev[nb] - vc;
-                lz += Lf * (zn - zc) * ih2;
-                lv += Lf * dv * ih2;
-                fl += (zc - zn) * dv * ih2;
+            double fa = 0.0;
+            if (cm >= 0) {
+                const double f = Lf[cm], dz = z[cm] - zc, dv = vprev[cm] - vc;
+                lz += f * dz;
+                lv += f * dv;
+                fa -= dz * dv;
             }
+            if (cp >= 0) {
+                const double f = Lf[c], dz = z[cp] - zc, dv = vprev[cp] - vc;
+                lz += f * dz;
+                lv += f * dv;
+                fa -= dz * dv;
+            }
+            fl += fa * ih2;
         }
-        vbo[c] = tau * bm * y + tau * lz;
+        const double vb = tau * bm * y + tau * lz;
+        vbo[c] = vb;
+        znext[c] = V[c] * (rden_next * vb);
         T0b[c] += y;
         Vb[c] += tau * y * (lv + Ia[c]);
         Lb[c] += 0.5 * tau * fl;
@@ -1400,7 +1432,7 @@ cudaError_t adj_visc(const DevParams &p, int axis, const double *Uin, const doub
 }
 
 // planes of the heat adjoint: T0, T0b, V, L, Ia, qb, vb x2, Lb, Iab, Vb, Tb, ab
-constexpr int HEAT_WORK_PLANES = 13;
+constexpr int HEAT_WORK_PLANES = 17;
 
 // Reverse of one heat-conduction stage (Algorithm 1, N outer iterations).
 // hist: per iteration it, 2 P_it planes (T_it, a_it, v^1..v^{M_it}); Ms[it] =
@@ -1413,6 +1445,7 @@ cudaError_t adj_heat(const DevParams &p, const double *Uin, const double *hist, 
     double *T0 = work, *T0b = work + n, *V = work + 2 * n, *L = work + 3 * n, *Ia = work + 4 * n;
     double *qb = work + 5 * n, *vbA = work + 6 * n, *vbB = work + 7 * n, *Lb = work + 8 * n, *Iab = work + 9 * n;
     double *Vb = work + 10 * n, *Tb = work + 11 * n, *ab = work + 12 * n;
+    double *Lx = work + 13 * n, *Ly = work + 14 * n, *zA = work + 15 * n, *zB = work + 16 * n;
     const int gb = grid_for(p.n, 256);
     cudaError_t e;
     k_adj_heat_prep<<<gb, 256, 0, s>>>(p, Uin, T0, T0b);
@@ -1437,12 +1470,21 @@ cudaError_t adj_heat(const DevParams &p, const double *Uin, const double *hist, 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_adj_heat_q<<<gb, 256, 0, s>>>(p, qb, v_of(M), L, vbA, Lb, Iab, Vb);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        double *vi = vbA, *vo = vbB;
+        double *vi = vbA, *vo = vbB, *zi = zA, *zo = zB;
+        auto rden_of = [&](int m) { return 1.0 / (1.0 + tau * bs[boff[it] + m - 1]); };
+        if (M >= 1) {
+            k_adj_heat_faces<<<gb, 256, 0, s>>>(p, L, Lx, Ly);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_adj_heat_z<<<gb, 256, 0, s>>>(p, V, vi, zi, rden_of(M));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         for (int m = M; m >= 1; m--) {
-            const double bm = bs[boff[it] + m - 1], rden = 1.0 / (1.0 + tau * bm);
-            k_adj_heat_lim<<<gb, 256, 0, s>>>(p, V, L, Ia, v_of(m - 1), vi, vo, T0b, Vb, Lb, Iab, tau, bm, rden);
+            const double bm = bs[boff[it] + m - 1], rden = rden_of(m), rnext = m > 1 ? rden_of(m - 1) : 0.0;
+            k_adj_heat_lim<<<gb, 256, 0, s>>>(p, V, Lx, Ly, Ia, v_of(m - 1), vi, zi, vo, zo, T0b, Vb, Lb, Iab, tau,
+                                              bm, rden, rnext);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             double *t = vi; vi = vo; vo = t;
+            t = zi; zi = zo; zo = t;
         }
         k_adj_heat_coef<<<gb, 256, 0, s>>>(p, Uin, Tit, ait, Vb, Lb, Iab, vi, T0b, Tb, ab, Gin, pbar, it == 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
