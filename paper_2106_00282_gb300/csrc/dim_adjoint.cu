@@ -218,31 +218,10 @@ __device__ __forceinline__ double law_ratio(const DevParams &p, double T)
 // the stage formulas in dual arithmetic (same operation order as the forward)
 // ---------------------------------------------------------------------------
 template <int N>
-__device__ __forceinline__ Dn<N> d_sgp(const DevParams &p, int k, const Dn<N> &Ek, const Dn<N> &ak)
-{
-    return p.gm1[k] * Ek / ak - p.gpinf[k];
-}
-template <int N>
 __device__ __forceinline__ Dn<N> d_sgE(const DevParams &p, int k, const Dn<N> &pr, const Dn<N> &ak)
 {
     return ak * (pr + p.gpinf[k]) * p.inv_gm1[k];
 }
-// line-local conserved (m1, m2, rho u_n, rho u_t, E1, E2, rho E, alpha_2) ->
-// primitive (alpha_2, m1, m2, u_n, u_t, p1, p2)
-template <int N>
-__device__ __forceinline__ void d_prims(const DevParams &p, const Dn<N> *q, Dn<N> *w)
-{
-    Dn<N> a2 = q[7], a1 = 1.0 - a2;
-    Dn<N> rho = q[0] + q[1];
-    w[0] = a2;
-    w[1] = q[0];
-    w[2] = q[1];
-    w[3] = q[2] / rho;
-    w[4] = q[3] / rho;
-    w[5] = d_sgp(p, 0, q[4], a1);
-    w[6] = d_sgp(p, 1, q[5], a2);
-}
-
 // p,T equilibrium at fixed (m1, m2, rho e) (Sec. 3.4.1 / 3.4.2)
 template <int N>
 __device__ __forceinline__ void d_equilibrium(const DevParams &p, const Dn<N> &m1, const Dn<N> &m2, const Dn<N> &rhoe,
@@ -859,18 +838,24 @@ __global__ void __launch_bounds__(256) k_adj_sweep_cell(const DevParams p, const
             q[k] = Uin[gmap[k] * n + c];
             lam[k] = Gout[gmap[k] * n + c];
         }
-        // transposed Jacobian of q -> W (line-local order)
-        Dn<8> qd[NQ], W[7];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) qd[k] = dseed<8>(q[k], k);
-        d_prims(p, qd, W);
+        // transposed Jacobian of q -> W (line-local order), by hand:
+        // W = (a2, m1, m2, q2/rho, q3/rho, (g1-1) E1/a1 - g1 pinf1, (g2-1) E2/a2 - g2 pinf2)
         double acc[NQ];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) {
-            double s = lam[k];
-#pragma unroll
-            for (int j = 0; j < 7; j++) s += Wb[j] * W[j].d[k];
-            acc[k] = s;
+        {
+            const double a2 = q[7], a1 = 1.0 - a2, ir = 1.0 / (q[0] + q[1]);
+            const double ia1 = 1.0 / a1, ia2 = 1.0 / a2;
+            const double u = q[2] * ir, v = q[3] * ir;
+            const double rhob = -(Wb[3] * u + Wb[4] * v) * ir;
+            const double e1 = Wb[5] * p.gm1[0] * ia1, e2 = Wb[6] * p.gm1[1] * ia2;
+            acc[0] = lam[0] + Wb[1] + rhob;
+            acc[1] = lam[1] + Wb[2] + rhob;
+            acc[2] = lam[2] + Wb[3] * ir;
+            acc[3] = lam[3] + Wb[4] * ir;
+            acc[4] = lam[4] + e1;
+            acc[5] = lam[5] + e2;
+            acc[6] = lam[6];
+            // d p1/d a2 = +(g1-1) E1/a1^2 (a1 = 1 - a2), d p2/d a2 = -(g2-1) E2/a2^2
+            acc[7] = lam[7] + Wb[0] + e1 * q[4] * ia1 - e2 * q[5] * ia2;
         }
         // R(U_i) (u*_{i+1/2} - u*_{i-1/2}): R.lam = lam4 a1 p1 + lam5 a2 p2 - lam7 a2,
         // a_k p_k = (g_k-1) E_k - a_k g_k pinf_k
