@@ -106,8 +106,9 @@ typedef struct dim_ctx dim_ctx; /* opaque: parameters, grid, stream, scratch */
 /* Create a context for an nx x ny grid of spacing (dx, dy) and allocate its
  * scratch.  A 1D problem is ny = 1 (or nx = 1); an axis of extent 1 is inactive.
  * cuda_stream is a cudaStream_t (NULL: legacy default stream).
- * Errors: DIM_EINVAL for non-positive sizes/spacings, a 1 x 1 grid (no axis,
- * hence no CFL time scale), gamma_k <= 1, Cv_k <= 0,
+ * Errors: DIM_EINVAL for non-positive sizes/spacings, nx * ny above 2^27 cells
+ * (134,217,728: the 32-bit cell-plane indexing of the kernels), a 1 x 1 grid
+ * (no axis, hence no CFL time scale), gamma_k <= 1, Cv_k <= 0,
  * cfl <= 0, unknown flags, p_max outside [1, 64], DIM_TRELAX_MIDPOINT with
  * trelax_iters outside [1, 1000], DIM_TRELAX_MIDPOINT or DIM_HEAT_ALPHA_LINEAR
  * with a precision other than FP64; DIM_ECUDA on allocation

@@ -46,6 +46,7 @@ def test_init_rejects_bad_arguments(lib):
     ctx = C.c_void_p()
     cases = [
         (good, 0, 1, 1e-3, 1e-3),
+        (good, 16385, 8192, 1e-3, 1e-3),  # above 2^27 cells
         (good, 1, 1, 1e-3, 1e-3),
         (good, 10, 1, -1.0, 1e-3),
         (good.replace(gamma=(1.0, 1.4)), 10, 1, 1e-3, 1e-3),

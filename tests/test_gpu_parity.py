@@ -289,3 +289,35 @@ def test_full_size_parity(torch_cuda, O, I, which):
     s.step(U, nst)
     Uo, st, dto, ph = O.step(wl.params, Uo, wl.dx, wl.dy, nst)
     assert_parity(_host(U), Uo, TOL, which)
+
+
+def test_maximum_grid(torch_cuda, O, I):
+    """The largest grid dim_init accepts (2^27 cells: 16384 x 8192), holding the
+    water/air shock tube along x in every row (heat conduction on).  Every row is
+    then the same problem with the same time step and Chebyshev parameters, so
+    after two steps every row must equal, bit for bit, the oracle's run of the
+    same rows on a 16384 x 3 grid -- a check of the kernels' indexing and tiling
+    at the size limit."""
+    torch = torch_cuda
+    from paper_2106_00282_gb300.api import Solver
+
+    nx, ny = 16384, 8192
+    wl = I.shock_tube(n=nx)
+    h = wl.dx
+    prim_row = torch.from_numpy(np.ascontiguousarray(wl.prim.reshape(5, 1, nx)))
+    s = Solver(wl.params, nx, ny, h, h)
+    U = s.from_primitive(prim_row.cuda().expand(5, ny, nx).contiguous())
+    s.step(U, 2)
+    # three rows: the middle one has both y faces, as the interior rows of the
+    # large grid, so the Gershgorin bound (hence the Chebyshev schedule) agrees
+    Uo = O.from_primitive(wl.params, np.ascontiguousarray(np.repeat(wl.prim.reshape(5, 1, nx), 3, axis=1)))
+    Uo, st, dto, ph = O.step(wl.params, Uo, h, h, 2)
+    assert st & 3 == 0
+    assert np.array_equal(Uo[:, 0], Uo[:, 1]) and np.array_equal(Uo[:, 2], Uo[:, 1])
+    row = torch.from_numpy(np.ascontiguousarray(Uo[:, 1:2, :])).cuda()
+    same = (U == row).reshape(8, -1).all(dim=1)
+    print(f"[parity] maximum grid {nx}x{ny}: rows equal to the oracle per field {same.tolist()}")
+    assert bool(same.all())
+    s.close()
+    del U
+    torch.cuda.empty_cache()
