@@ -4,17 +4,19 @@
 // Chebyshev lambda_max, hence P and b_m) and its value-decided branches
 // (limiter operand, Davis bounds, HLLC wave region) held fixed:
 //
-//  * pointwise stages (pressure relaxation Sec. 3.3, temperature relaxation
-//    Sec. 3.4.1, the equilibrium projection and the conduction coefficients
-//    of Sec. 3.4.2): the local Jacobian of the cell map is formed by
-//    forward-mode dual numbers over the cell's inputs and its transpose is
-//    applied to the cell's adjoint;
+//  * pointwise stages: the pressure relaxation (Sec. 3.3) and the p,T
+//    equilibrium (temperature relaxation, Sec. 3.4.1, and the projection of
+//    Sec. 3.4.2) are reversed by hand, the admissible roots through their
+//    implicit derivatives; the conduction coefficients of Sec. 3.4.2 form
+//    their local Jacobian with forward-mode dual numbers and apply its
+//    transpose;
 //  * the hyperbolic sweep (Sec. 3.1, 3.6): the update of cell i is
 //    U_i - dt/h (F_{i+1/2} - F_{i-1/2}) - dt/h R(U_i)(u*_{i+1/2} - u*_{i-1/2});
 //    the adjoint of face f's outputs (F, u*) is dt/h times the difference of
-//    its two cells' adjoints (and of R.adjoint for u*), and every cell gathers
-//    the transposed Jacobian of each face whose four-cell stencil contains it,
-//    evaluated with that cell's eight inputs seeded;
+//    its two cells' adjoints (and of R.adjoint for u*); each face reverses its
+//    HLLC flux and reconstruction by hand into the adjoints of its four
+//    stencil cells' primitives, and every cell gathers those and applies the
+//    transposed primitive Jacobian;
 //  * the LIM solves (Sec. 3.2, Eqs. LIM, LIM_last): the sweeps
 //    v^m = (v^0 + tau b_m v^{m-1} + tau V (L v^{m-1} + f)) / (1 + tau b_m) are
 //    linear in v for frozen coefficients and L_h is symmetric, so the reverse
@@ -222,24 +224,6 @@ __device__ __forceinline__ Dn<N> d_sgE(const DevParams &p, int k, const Dn<N> &p
 {
     return ak * (pr + p.gpinf[k]) * p.inv_gm1[k];
 }
-// p,T equilibrium at fixed (m1, m2, rho e) (Sec. 3.4.1 / 3.4.2)
-template <int N>
-__device__ __forceinline__ void d_equilibrium(const DevParams &p, const Dn<N> &m1, const Dn<N> &m2, const Dn<N> &rhoe,
-                                              Dn<N> &T, Dn<N> &a)
-{
-    Dn<N> C1 = m1 * p.cv[0], C2 = m2 * p.cv[1], C = C1 + C2;
-    Dn<N> G1C1 = p.gm1[0] * C1, G2C2 = p.gm1[1] * C2, G = G1C1 + G2C2;
-    const double B1 = p.pinf[0] - p.pinf[1];
-    Dn<N> E = rhoe - p.pinf[0];
-    Dn<N> qa = B1 * (G + C);
-    Dn<N> qb = E * G - B1 * G2C2 - C * B1;
-    Dn<N> qc = -E * G2C2;
-    Dn<N> disc = qb * qb - 4.0 * qa * qc;
-    if (disc.v < 0.0) disc = dcst<N>(0.0);
-    Dn<N> sq = dsqrt(disc);
-    a = qb.v > 0.0 ? (-2.0 * qc) / (qb + sq) : (sq - qb) / (2.0 * qa);
-    T = (E + B1 * a) / C;
-}
 
 // conduction coefficients V = 1/(C + B1^2/K), Lam = sum_k a_k lambda_k(T)
 // (Sec. 3.4.2) and the source a1 I1 + a2 I2 (Eq. I) at (m1, m2, T, a2)
@@ -314,6 +298,62 @@ __device__ __forceinline__ void add_param(double *pbar, int k, double v)
 
 #define GRID_LOOP(c, n) for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (n); c += gridDim.x * blockDim.x)
 
+
+// ---------------------------------------------------------------------------
+// the p,T equilibrium (Sec. 3.4.1 / 3.4.2) and its reverse by the implicit
+// derivative of the admissible root: qa a^2 + qb a + qc = 0 gives
+// da = -(a^2 dqa + a dqb + dqc) / (2 qa a + qb); T = (E + B1 a) / C
+// ---------------------------------------------------------------------------
+struct EqState {
+    double C, G, G2C2, E, qa, qb, B1, a, T;
+};
+
+// forward values in the operation order of the forward kernels' equilibrium()
+__device__ __forceinline__ EqState eq_fwd(const DevParams &p, double m1, double m2, double rhoe)
+{
+    EqState q;
+    const double C1 = m1 * p.cv[0], C2 = m2 * p.cv[1];
+    q.C = C1 + C2;
+    const double G1C1 = p.gm1[0] * C1;
+    q.G2C2 = p.gm1[1] * C2;
+    q.G = G1C1 + q.G2C2;
+    q.B1 = p.pinf[0] - p.pinf[1];
+    q.E = rhoe - p.pinf[0];
+    q.qa = q.B1 * (q.G + q.C);
+    q.qb = q.E * q.G - q.B1 * q.G2C2 - q.C * q.B1;
+    const double qc = -q.E * q.G2C2;
+    double disc = q.qb * q.qb - 4.0 * q.qa * qc;
+    if (disc < 0.0) disc = 0.0;
+    const double sq = sqrt(disc);
+    q.a = q.qb > 0.0 ? (-2.0 * qc) / (q.qb + sq) : (sq - q.qb) / (2.0 * q.qa);
+    q.T = (q.E + q.B1 * q.a) / q.C;
+    return q;
+}
+
+// adjoints (Tb, ab) of (T, a) -> adjoints of (m1, m2, rho e)
+__device__ __forceinline__ void eq_rev(const DevParams &p, const EqState &q, double Tb, double ab, double &m1b,
+                                       double &m2b, double &reb)
+{
+    const double iC = 1.0 / q.C;
+    double Eb = Tb * iC;
+    ab += Tb * q.B1 * iC;
+    double Cb = -Tb * q.T * iC;
+    const double w = ab / (2.0 * q.qa * q.a + q.qb);
+    const double qab = -w * q.a * q.a, qbb = -w * q.a, qcb = -w;
+    double Gb = q.B1 * qab;
+    Cb += q.B1 * qab;
+    Eb += q.G * qbb;
+    Gb += q.E * qbb;
+    double G2C2b = -q.B1 * qbb;
+    Cb -= q.B1 * qbb;
+    Eb -= q.G2C2 * qcb;
+    G2C2b -= q.E * qcb;
+    G2C2b += Gb;
+    const double C1b = p.gm1[0] * Gb + Cb, C2b = p.gm1[1] * G2C2b + Cb;
+    m1b = p.cv[0] * C1b;
+    m2b = p.cv[1] * C2b;
+    reb = Eb;
+}
 
 // ---------------------------------------------------------------------------
 // pointwise stages: Gin = J^T G in place (G: 8 planes)
@@ -396,21 +436,18 @@ __global__ void __launch_bounds__(256) k_adj_trelax(const DevParams p, const dou
     const int n = p.n;
     GRID_LOOP(c, n)
     {
-        // inputs m1, m2, E1, E2
-        Dn<4> m1 = dseed<4>(Uin[c], 0), m2 = dseed<4>(Uin[n + c], 1);
-        Dn<4> E1 = dseed<4>(Uin[4 * n + c], 2), E2 = dseed<4>(Uin[5 * n + c], 3);
-        Dn<4> T, a;
-        d_equilibrium(p, m1, m2, E1 + E2, T, a);
-        Dn<4> o4 = m1 * p.cv[0] * T + (1.0 - a) * p.pinf[0];
-        Dn<4> o5 = m2 * p.cv[1] * T + a * p.pinf[1];
+        // inputs m1, m2, E1, E2; outputs E_k = m_k Cv_k T + a_k pinf_k and alpha_2 = a
+        const double m1 = Uin[c], m2 = Uin[n + c];
+        const EqState q = eq_fwd(p, m1, m2, Uin[4 * n + c] + Uin[5 * n + c]);
         const double g4 = G[4 * n + c], g5 = G[5 * n + c], g7 = G[7 * n + c];
-        double r[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) r[k] = g4 * o4.d[k] + g5 * o5.d[k] + g7 * a.d[k];
-        G[c] += r[0];
-        G[n + c] += r[1];
-        G[4 * n + c] = r[2];
-        G[5 * n + c] = r[3];
+        const double Tb = g4 * m1 * p.cv[0] + g5 * m2 * p.cv[1];
+        const double ab = -g4 * p.pinf[0] + g5 * p.pinf[1] + g7;
+        double m1b, m2b, reb;
+        eq_rev(p, q, Tb, ab, m1b, m2b, reb);
+        G[c] += g4 * p.cv[0] * q.T + m1b;
+        G[n + c] += g5 * p.cv[1] * q.T + m2b;
+        G[4 * n + c] = reb;
+        G[5 * n + c] = reb;
         G[7 * n + c] = 0.0;  // alpha_2 is replaced by the equilibrium value
     }
 }
@@ -422,7 +459,7 @@ __global__ void __launch_bounds__(256) k_adj_trelax(const DevParams p, const dou
 // reconstructed primitives wl (cell f-1) and wr (cell f): 14 values.
 // k_adj_sweep_face, per face: the adjoint of the face outputs
 // gbar = dt/h (adj_R - adj_L) [and dt/h (R.adj_R - R.adj_L) for u*], the
-// transposed HLLC Jacobian with respect to (wl, wr) by two 7-wide dual passes,
+// hand-written reverse of the HLLC flux with respect to (wl, wr),
 // then the transposed reconstruction (slopes: the minmod operand chosen, times
 // 1 or 2 for Overbee) -> the adjoint of the primitives W of the 4 stencil
 // cells, stored per face (28 values) with the face's u*.
@@ -1116,17 +1153,14 @@ __global__ void __launch_bounds__(256) k_adj_heat_eq(const DevParams p, const do
     {
         const double m1v = Uin[c], m2v = Uin[n + c];
         const double q = lap_v(p, c, vM, L) + Ia[c];
-        Dn<3> m1 = dseed<3>(m1v, 0), m2 = dseed<3>(m2v, 1);
-        Dn<3> re = dseed<3>(Uin[4 * n + c] + Uin[5 * n + c] + tau * q, 2);
-        Dn<3> T, a;
-        d_equilibrium(p, m1, m2, re, T, a);
+        const EqState eq = eq_fwd(p, m1v, m2v, Uin[4 * n + c] + Uin[5 * n + c] + tau * q);
         double tb, abr, g0 = 0.0, g1 = 0.0, qbc = 0.0;
         if (last) {
             const double g4 = G[4 * n + c], g5 = G[5 * n + c];
             tb = g4 * m1v * p.cv[0] + g5 * m2v * p.cv[1];
             abr = -g4 * p.pinf[0] + g5 * p.pinf[1] + G[7 * n + c];
-            g0 = g4 * p.cv[0] * T.v;
-            g1 = g5 * p.cv[1] * T.v;
+            g0 = g4 * p.cv[0] * eq.T;
+            g1 = g5 * p.cv[1] * eq.T;
             qbc = tau * G[6 * n + c];
 #pragma unroll
             for (int k = 0; k < 4; k++) Gin[k * n + c] = G[k * n + c];
@@ -1138,9 +1172,10 @@ __global__ void __launch_bounds__(256) k_adj_heat_eq(const DevParams p, const do
             tb = Tb[c];
             abr = ab[c];
         }
-        const double rb = tb * T.d[2] + abr * a.d[2];
-        Gin[c] += g0 + tb * T.d[0] + abr * a.d[0];
-        Gin[n + c] += g1 + tb * T.d[1] + abr * a.d[1];
+        double m1b, m2b, rb;
+        eq_rev(p, eq, tb, abr, m1b, m2b, rb);
+        Gin[c] += g0 + m1b;
+        Gin[n + c] += g1 + m2b;
         // rho e0 = E1 + E2
         Gin[4 * n + c] += rb;
         Gin[5 * n + c] += rb;
