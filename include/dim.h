@@ -142,8 +142,11 @@ int dim_cfl_dt(dim_ctx *c, const double *U, double *dt);
 int dim_step(dim_ctx *c, double *U, int nsteps, double *dt_last);
 
 /* The same nsteps split steps on a HOST state U_host (8 planes as above, any
- * alignment): copies it to a context-owned device buffer, steps, copies it
- * back; synchronizes; returns the status like dim_step with dt_last. */
+ * alignment; page-locked memory lets the copies run asynchronously): copies it
+ * to a context-owned device buffer, steps, copies it back -- the masses and
+ * momenta of the last step on a second stream as soon as they are final,
+ * overlapping the remaining stages; synchronizes; returns the status like
+ * dim_step with dt_last. */
 int dim_step_host(dim_ctx *c, double *U_host, int nsteps, double *dt_last);
 
 /* One hyperbolic sweep along axis (0 = x, 1 = y) with time step dt (> 0),

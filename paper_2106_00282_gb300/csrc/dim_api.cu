@@ -271,6 +271,12 @@ void dim_destroy(dim_ctx *c)
     cudaFree(c->U2);
     cudaFree(c->S);
     cudaFree(c->Uh);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+        cudaEventDestroy(c->ev_mass);
+        cudaEventDestroy(c->ev_mom);
+    }
     cudaFree(c->sc);
     cudaFree(c->beta);
     for (int i = 0; i < c->caprec; i++) {
@@ -310,8 +316,16 @@ static int status_to_code(unsigned st)
     return DIM_OK;
 }
 
-// one split step on U (device); stages in the order of Sec. 3
-static int step_once(dim_ctx *c, double *U)
+// Where the planes of the state are final within a step: the masses m1, m2
+// (planes 0, 1) after the last sweep, the momenta (planes 2, 3) after the last
+// viscous stage (else the last sweep); the later stages write planes 4-7 only.
+struct StepMarks {
+    double *mass_buf, *mom_buf;  // the buffer holding the final planes at that point
+};
+
+// one split step on U (device); stages in the order of Sec. 3.  mk (may be
+// null): record c->ev_mass and c->ev_mom on the stream at the points above
+static int step_once(dim_ctx *c, double *U, StepMarks *mk = nullptr)
 {
     const dim_params &h = c->hp;
     const DevParams &p = c->p;
@@ -335,9 +349,17 @@ static int step_once(dim_ctx *c, double *U)
         TIMED(c, K_SWEEP_Y, run_sweep(c, 1, cur, oth, 0.0, 1, last == LAST_SY));
         double *t = cur; cur = oth; oth = t;
     }
+    if (mk) {
+        TRY(cudaEventRecord(c->ev_mass, c->stream));
+        mk->mass_buf = cur;
+    }
     if (vis) {
         if (sx) TIMED(c, K_VISC_X, run_visc(c, 0, cur, 0.0, !sy, last == LAST_VX));
         if (sy) TIMED(c, K_VISC_Y, run_visc(c, 1, cur, 0.0, 1, last == LAST_VY));
+    }
+    if (mk) {
+        TRY(cudaEventRecord(c->ev_mom, c->stream));
+        mk->mom_buf = cur;
     }
     if (heat) {
         TIMED(c, K_HEAT, run_heat(c, cur, 0.0, 1, 1));
@@ -390,14 +412,37 @@ int dim_step(dim_ctx *c, double *U, int nsteps, double *dt_last)
 int dim_step_host(dim_ctx *c, double *U_host, int nsteps, double *dt_last)
 {
     if (!c || !U_host || nsteps < 0) return DIM_EINVAL;
-    size_t bytes = sizeof(double) * 8 * (size_t)c->p.n;
+    const size_t n = (size_t)c->p.n, bytes = sizeof(double) * 8 * n, two = sizeof(double) * 2 * n;
     if (!c->Uh && cudaMalloc(&c->Uh, bytes) != cudaSuccess) return DIM_ECUDA;
-    TRY(cudaMemcpyAsync(c->Uh, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
-    for (int s = 0; s < nsteps; s++) {
-        int r = step_once(c, c->Uh);
-        if (r != DIM_OK) return r;
+    if (!c->side) {
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+            c->side = nullptr;
+            return DIM_ECUDA;
+        }
+        if (cudaEventCreateWithFlags(&c->ev_mass, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_mom, cudaEventDisableTiming) != cudaSuccess)
+            return DIM_ECUDA;
     }
-    TRY(cudaMemcpyAsync(U_host, c->Uh, bytes, cudaMemcpyDeviceToHost, c->stream));
+    TRY(cudaMemcpyAsync(c->Uh, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (nsteps == 0) {
+        TRY(cudaMemcpyAsync(U_host, c->Uh, bytes, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        for (int s = 0; s + 1 < nsteps; s++) {
+            int r = step_once(c, c->Uh);
+            if (r != DIM_OK) return r;
+        }
+        // the last step: planes 0-3 go back to the host on the side stream as
+        // soon as they are final, overlapping the remaining stages
+        StepMarks mk;
+        int r = step_once(c, c->Uh, &mk);
+        if (r != DIM_OK) return r;
+        TRY(cudaStreamWaitEvent(c->side, c->ev_mass, 0));
+        TRY(cudaMemcpyAsync(U_host, mk.mass_buf, two, cudaMemcpyDeviceToHost, c->side));
+        TRY(cudaStreamWaitEvent(c->side, c->ev_mom, 0));
+        TRY(cudaMemcpyAsync(U_host + 2 * n, mk.mom_buf + 2 * n, two, cudaMemcpyDeviceToHost, c->side));
+        TRY(cudaMemcpyAsync(U_host + 4 * n, c->Uh + 4 * n, 2 * two, cudaMemcpyDeviceToHost, c->stream));
+        TRY(cudaStreamSynchronize(c->side));
+    }
     double dtl = 0.0;
     int r = read_back(c, &dtl);
     if (dt_last) *dt_last = dtl;

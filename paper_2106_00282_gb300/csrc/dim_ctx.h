@@ -53,6 +53,11 @@ struct dim_ctx {
     double *U2;   // 8 planes: out-of-place target of the sweeps
     double *S;    // dimk::SCRATCH_PLANES scratch planes for the parabolic stages
     double *Uh;   // 8 planes: device copy of a host state (dim_step_host), lazily allocated
+    // dim_step_host: a second stream that copies the planes a step has finished
+    // (masses after the sweeps, momenta after the viscous stage) back to the
+    // host while the later stages run; events marking those points (lazily created)
+    cudaStream_t side;
+    cudaEvent_t ev_mass, ev_mom;
     double *beta; // Chebyshev roots table (PMAX x PMAX)
     Scalars *sc;
     int device;

@@ -226,15 +226,24 @@ def test_two_cells(torch_cuda, O, I):
         assert_parity(_host(U), Uo, TOL, f"{nx}x{ny}")
 
 
-def test_host_entry_point(torch_cuda, O, I):
-    """dim_step_host (host buffers, copies inside) equals the device path."""
-    wl = I.impact(120, 60)
+@pytest.mark.parametrize("case", ["impact", "shock_tube_1d", "pvt_no_viscosity", "pageable"])
+def test_host_entry_point(torch_cuda, O, I, case):
+    """dim_step_host (host buffers, copies inside; the masses and momenta of the
+    last step copied back on a second stream while the later stages run) equals
+    the device path: 2D with viscosity, 1D (the state ends in the sweep
+    buffer), no viscous stage, a pageable host buffer; 0, 1 and 5 steps."""
+    wl = {"impact": lambda: I.impact(120, 60), "shock_tube_1d": lambda: I.shock_tube(n=300),
+          "pvt_no_viscosity": lambda: I.pvt_translation(n=150, k=(0.6, 0.026)),
+          "pageable": lambda: I.impact(64, 40)}[case]()
     s, U, Uo = _init_both(torch_cuda, O, wl)
-    Uh = _host(U).copy()
-    Ut = torch_cuda.from_numpy(Uh).pin_memory()
-    s.step_host(Ut, 5)
-    s.step(U, 5)
-    assert np.array_equal(Ut.numpy(), _host(U))
+    for nst in (0, 1, 5):
+        Uh = _host(U).copy()
+        Ut = torch_cuda.from_numpy(Uh)
+        if case != "pageable":
+            Ut = Ut.pin_memory()
+        s.step_host(Ut, nst)
+        s.step(U, nst)
+        assert np.array_equal(Ut.numpy(), _host(U)), (case, nst)
 
 
 @pytest.mark.parametrize("fault", ["alpha_above_one", "negative_mass", "nan_energy"])
