@@ -1,11 +1,16 @@
 """Benchmark of the split time step (HLLC sweeps + relaxations + Chebyshev
 parabolic stages) of the two-temperature diffuse-interface model.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload impact]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload conduction_disc]
 
 One step = one full split step over the workload grid (CFL reduction, x and y
 hyperbolic sweeps with pressure relaxation, viscous steps, temperature
 relaxation and heat conduction).  Prints one JSON line on rank 0.
+
+The headline workload is the 2048 x 2048 conduction-dominated interface (hot
+air disc in cold water, nonlinear conductivity, 16-32 Chebyshev passes per
+heat solve), FP64; the FP32-bulk form of the same grid, the 1024 x 512 impact,
+the batched configuration and the gradient problem are reported beside it.
 
 Timing: W untimed warm-up steps, then K steps timed one by one with CUDA events
 on the solver's stream, a 256 MiB buffer write between steps flushing the L2
@@ -18,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -33,8 +39,9 @@ METRIC = "cell-updates/s per full split step (HLLC+Chebyshev) and % of HBM roofl
 UNIT = "cell-updates/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-# FP64 rate of a GB300 (152 SMs x 2070 MHz x 4 FP64 FLOP/clk/SM, the nominal 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 1.25
+# nominal FP64 rate of a GB300 (152 SMs x 2070 MHz x 4 FP64 FLOP/clk/SM), context only: the
+# roofline is quoted against the FP64 rate measured in the same run (measure_rates)
+FP64_NOMINAL_TFLOPS = 1.26
 
 
 def parse():
@@ -43,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="impact")
+    ap.add_argument("--workload", default="conduction_disc")
+    ap.add_argument("--no-impact", action="store_true", help="skip the 1024x512 impact figures")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk variant")
@@ -57,15 +66,26 @@ def parse():
     return ap.parse_args()
 
 
-def workload_desc(wl):
+WORKLOAD_TEXT = {
+    "impact": "2D multiphase impact: solid projectile at 500 m/s on a solid slab in air, heat conduction "
+              "and viscosity on",
+    "conduction_disc": "2D conduction-dominated interface: hot air disc (3000 K, r 0.2, seeded sinusoidal "
+                       "interface perturbation, modes 4-16) in water at 300 K, 1e5 Pa, conductivity "
+                       "k0 (T/300)^2, viscosity on, P = clamp(formula, 8, 16) Chebyshev parameters",
+    "shock_tube": "1D water/air shock tube, P = 4",
+}
+
+
+def workload_desc(wl, precision="fp64"):
+    state = 64.0 * wl.nx * wl.ny / 1e6
+    l2 = (f"flushed between timed steps (256 MiB buffer write); state {state:.1f} MB "
+          + ("> L2 (129 MB)" if state > 129 else "< L2 (129 MB)"))
     return {
-        "workload": f"{wl.name} {wl.nx}x{wl.ny} FP64 (2D multiphase impact: solid projectile at 500 m/s on a "
-                    f"solid slab in air, heat conduction and viscosity on)" if wl.name == "impact" else
-        f"{wl.name} {wl.nx}x{wl.ny} FP64",
+        "workload": f"{wl.name} {wl.nx}x{wl.ny} {precision.upper()} ({WORKLOAD_TEXT.get(wl.name, wl.name)})",
         "cells": wl.nx * wl.ny,
         "grid": [wl.nx, wl.ny],
-        "precision": "fp64",
-        "l2": "flushed between timed steps (256 MiB buffer write); state 33.6 MB < L2",
+        "precision": precision,
+        "l2": l2,
     }
 
 
@@ -111,9 +131,11 @@ def clocks_sampler_stop(p):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def kernel_hash():
+def kernel_hash(precision=0):
     h = hashlib.sha256()
-    for fn in ("dim_device.cuh", "dim_sweep.cu", "dim_parabolic.cu"):
+    files = ("dim_device.cuh", "dim_sweep.cu", "dim_parabolic.cu") if precision == 0 else \
+        ("dim_device.cuh", "dim_bulk32.cuh", "dim_bulk32.cu")
+    for fn in files:
         with open(os.path.join(ROOT, "paper_2106_00282_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -127,13 +149,74 @@ def measured_peak():
         return {}
 
 
-def flops_per_cell(kernel: str, wl) -> float:
+def flops_per_cell(kernel: str, wl, P: int = 1) -> float:
     """Algorithmic FP64 operations per cell of one launch (+ - * / sqrt each
-    one, as the plain FP64 statement of the stage performs them)."""
+    one, as the plain FP64 statement of the stage performs them) with P
+    Chebyshev parameters."""
     from paper_2106_00282_gb300 import flops
 
     ndim = 2 if wl.nx > 1 and wl.ny > 1 else 1
-    return flops.per_cell(kernel, wl.params, ndim=ndim)
+    return flops.per_cell(kernel, wl.params, P=P, ndim=ndim)
+
+
+def cheb_P(params, tau: float, lam: float, viscous: bool) -> int:
+    """The Chebyshev parameter count the kernels take for time step tau and
+    spectral bound lam (the same IEEE operations): ceil(pi/4 sqrt(tau lam + 1)),
+    then the heat solve's policy (fixed / clamped) or, for the viscous solve,
+    the cap p_max."""
+    pf = int(math.ceil(math.pi / 4.0 * math.sqrt(tau * lam + 1.0)))
+    if viscous:
+        return min(pf, params.p_max)
+    if params.p_policy == 1:
+        return params.p_fixed
+    P = pf
+    if params.p_policy == 2 and P < params.p_min:
+        P = params.p_min
+    return min(P, params.p_max)
+
+
+def launch_P(params, sched) -> dict:
+    """Per step, the P of each LIM solve, from a schedule record (rows of
+    DIM_SCHED doubles: CFL maximum S, heat lambda_max per outer iteration,
+    viscous lambda_max along x and y)."""
+    out = {"heat": [], "viscous_x": [], "viscous_y": []}
+    for row in sched:
+        tau = params.cfl / row[0]
+        out["heat"].append([cheb_P(params, tau, lam, False) for lam in row[1:9] if lam > 0.0])
+        out["viscous_x"].append(cheb_P(params, tau, row[9], True) if row[9] > 0.0 else 0)
+        out["viscous_y"].append(cheb_P(params, tau, row[10], True) if row[10] > 0.0 else 0)
+    return out
+
+
+def measure_rates(dev) -> dict:
+    """Arithmetic rates of this GPU measured now (dim_probe_rate: dependency
+    chains of one operation in every thread, 8 blocks of 256 threads per SM,
+    CUDA events; best of three after one warm-up): FP64 FMA and FP32 FMA in
+    TFLOP/s, FP64 add/multiply without contraction in TFLOP/s, IEEE FP64
+    division and square root and the FP32-bulk kernels' division in G/s."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2106_00282_gb300 import _lib
+
+    L = _lib.load()
+    stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    kinds = {"dfma_tflops": (_lib.PROBE_DFMA, 4000, 1e12), "daddmul_tflops": (_lib.PROBE_DADDMUL, 4000, 1e12),
+             "ddiv_gops": (_lib.PROBE_DDIV, 1000, 1e9), "dsqrt_gops": (_lib.PROBE_DSQRT, 1000, 1e9),
+             "ffma_tflops": (_lib.PROBE_FFMA, 100000, 1e12), "fastdiv_gops": (_lib.PROBE_FASTDIV, 1000, 1e9)}
+    out = {}
+    for name, (kind, iters, scale) in kinds.items():
+        best = 0.0
+        for rep in range(4):
+            ms, ops = C.c_double(), C.c_double()
+            _lib.check(L.dim_probe_rate(kind, 0, iters, stream, C.byref(ms), C.byref(ops)), "dim_probe_rate")
+            if rep:
+                best = max(best, ops.value / (ms.value * 1e-3) / scale)
+        out[name] = best
+    out["method"] = ("dim_probe_rate: 8 independent dependency chains per thread, 8 blocks x 256 threads per SM, "
+                     "CUDA events, best of 3 after a warm-up")
+    return out
 
 
 def aggregate(ms_local: float, units_per_rank: float, world: int, dev):
@@ -149,7 +232,10 @@ def aggregate(ms_local: float, units_per_rank: float, world: int, dev):
     return ms_max, world * units_per_rank / (ms_max / 1e3)
 
 
-def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
+def run_ours(args, rank, world, dev, precision=0, with_e2e=True, workload=None, steps=None, rates=None):
+    """K timed split steps of one workload in one precision; per-kernel device
+    times over the timed region; the roofline of the dominant kernel; the
+    end-to-end rate through dim_step_host."""
     import torch
 
     from paper_2106_00282_gb300 import build as cuda_build, inputs as I
@@ -159,7 +245,8 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
         cuda_build.build()
     if world > 1:
         torch.distributed.barrier()
-    wl = I.bench_workload(args.workload)
+    name = workload or args.workload
+    wl = I.bench_workload(name)
     wl.params = wl.params.replace(precision=precision)
     ncell = wl.nx * wl.ny
     s = Solver(wl.params, wl.nx, wl.ny, wl.dx, wl.dy)
@@ -167,10 +254,11 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
     U = U0.clone()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     W = max(3, args.warmup)
-    K = args.steps
+    K = steps or args.steps
     s.step(U, W)
     torch.cuda.synchronize()
     st0 = s.status(reset=True)
+    Ustart = U.clone() if precision == 0 else None
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     sampler = clocks_sampler_start(torch.cuda.current_device()) if rank == 0 else None
@@ -195,33 +283,51 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
     if st & 3:
         raise RuntimeError(f"inadmissible state during the timed steps (status {st})")
 
-    # per-kernel device times over the timed region
+    # per-kernel device times over the timed region (CUDA events on the solver stream)
     kern = {}
     launches = 0
-    for name in ("wave_max", "sweep_x", "sweep_y", "viscous_x", "viscous_y", "heat", "relax", "copy"):
-        nl, kms = s.kernel_time(name)
+    for kn in ("wave_max", "sweep_x", "sweep_y", "viscous_x", "viscous_y", "heat", "relax", "copy"):
+        nl, kms = s.kernel_time(kn)
         if nl:
-            kern[name] = {"launches": nl, "ms": kms, "avg_us": 1e3 * kms / nl}
-            if name != "copy":
+            kern[kn] = {"launches": nl, "ms": kms, "avg_us": 1e3 * kms / nl}
+            if kn != "copy":
                 launches += nl
     dom = max((k for k in kern if k != "copy"), key=lambda k: kern[k]["ms"])
-    peaks = measured_peak()
-    fpc = flops_per_cell(dom, wl)
-    achieved = fpc * ncell / (kern[dom]["avg_us"] * 1e-6) / 1e12
-    traffic = None
-    try:
-        with open(TRAFFIC) as f:
-            tr = json.load(f)
-        e = tr.get(args.workload, {}).get(dom)
-        if e and e.get("kernel_hash") == kernel_hash():
-            traffic = e["bytes_per_launch"]
-    except Exception:
-        pass
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
-                "flops_per_cell": fpc, "peak_source": "nominal FP64 rate (152 SMs x 2070 MHz x 4 FLOP/clk/SM)",
-                "kernels": kern}
-    hbm = peaks.get("hbm_gbs")
+
+    roofline = None
+    Ps = None
+    if precision == 0:
+        # the Chebyshev parameter counts of the timed steps: the same K steps
+        # replayed from the state the timed region started from, recording the
+        # schedule (bit-identical to the timed run); P follows from (dt, lambda_max)
+        sched = s.step_sched(Ustart, K).cpu().numpy()
+        del Ustart
+        Ps = launch_P(wl.params, sched)
+        if dom == "heat":
+            fl_launch = [sum(flops_per_cell("heat", wl, P) for P in row) for row in Ps["heat"]]
+        elif dom in ("viscous_x", "viscous_y"):
+            fl_launch = [flops_per_cell(dom, wl, P) for P in Ps[dom]]
+        else:
+            fl_launch = [flops_per_cell(dom, wl)] * kern[dom]["launches"]
+        fpc = sum(fl_launch) / len(fl_launch)  # per cell, average over the timed launches
+        achieved = fpc * ncell / (kern[dom]["avg_us"] * 1e-6) / 1e12
+        peak = rates["dfma_tflops"] if rates else FP64_NOMINAL_TFLOPS
+        traffic = None
+        try:
+            with open(TRAFFIC) as f:
+                e = json.load(f).get(name, {}).get(dom)
+            if e and e.get("kernel_hash") == kernel_hash(precision):
+                traffic = e["bytes_per_launch"]
+        except Exception:
+            pass
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic, "kernel": dom, "flops_per_cell": fpc,
+                    "peak_source": ("measured in this run: FP64 FMA chains (dim_probe_rate), "
+                                    f"nominal {FP64_NOMINAL_TFLOPS}") if rates else
+                    "nominal FP64 rate (152 SMs x 2070 MHz x 4 FLOP/clk/SM)",
+                    "frac_of_fma_free_rate": (achieved / rates["daddmul_tflops"]) if rates else None,
+                    "kernels": kern}
+    hbm = measured_peak().get("hbm_gbs")
     alg_bytes = 128.0 * ncell  # the 8-plane FP64 state read and written once per step
     step_us = 1e3 * ms_max / K
     hbm_frac = (alg_bytes / (step_us * 1e-6) / 1e9) / hbm if hbm else None
@@ -230,12 +336,12 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
     dram_step = 0.0
     try:
         with open(TRAFFIC) as f:
-            trw = json.load(f).get(args.workload, {})
-        for name, v in kern.items():
-            if name == "copy":
+            trw = json.load(f).get(name if precision == 0 else name + "_fp32_bulk", {})
+        for kn, v in kern.items():
+            if kn == "copy":
                 continue
-            e = trw.get(name)
-            if not e or e.get("kernel_hash") != kernel_hash():
+            e = trw.get(kn)
+            if not e or e.get("kernel_hash") != kernel_hash(precision):
                 dram_step = None
                 break
             dram_step += e["bytes_per_launch"] * v["launches"] / K
@@ -263,8 +369,12 @@ def run_ours(args, rank, world, dev, precision=0, with_e2e=True):
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(Uh.numel() * 8), "d2h_bytes_per_step": int(Uh.numel() * 8),
                "steps": Ke, "api": "dim_step_host (pinned host state, H2D + step + D2H per step)"}
-    return dict(value=value, ms_per_step=step_us / 1e3, wl=wl, roofline=roofline, e2e=e2e, clocks=clocks,
-                launches=launches, hbm_frac=hbm_frac, hbm=hbm_obj, status_warmup=st0)
+    s.close()
+    del U, U0, flush
+    torch.cuda.empty_cache()
+    return dict(value=value, ms_per_step=step_us / 1e3, wl=wl, roofline=roofline, kernels=kern, e2e=e2e,
+                clocks=clocks, launches=launches, hbm_frac=hbm_frac, hbm=hbm_obj, status_warmup=st0, dominant=dom,
+                P=Ps)
 
 
 def run_batched(dev, world=1, steps=10, warmup=3, ninst=256):
@@ -370,8 +480,9 @@ def host_cpu():
     return {"nproc": os.cpu_count(), "model": model}
 
 
-def oracle_rate(wl, budget_s=10.0, max_steps=1000):
-    """FP64 oracle (single-threaded C) on the same workload: steps until the budget."""
+def oracle_rate(wl, budget_s=12.0, max_steps=1000):
+    """FP64 oracle (single-threaded C) on the same workload: whole steps of the
+    full grid from the initial state until the budget is spent (at least one)."""
     from oracle import oracle as O
 
     U = O.from_primitive(wl.params, wl.prim)
@@ -384,6 +495,19 @@ def oracle_rate(wl, budget_s=10.0, max_steps=1000):
             break
     el = time.perf_counter() - t0
     return wl.nx * wl.ny * n / el, n, el
+
+
+def brief(r, fp64=None):
+    """Summary object of one extra run (FP32 bulk or another workload)."""
+    out = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"], "clocks": r["clocks"],
+           "dominant_kernel": r["dominant"],
+           "kernels_us": {k: round(v["avg_us"], 1) for k, v in r["kernels"].items()},
+           "hbm": r["hbm"]}
+    if fp64 is not None:
+        out["speedup_vs_fp64"] = r["value"] / fp64["value"]
+    if r["roofline"] is not None:
+        out["roofline"] = {k: v for k, v in r["roofline"].items() if k != "kernels"}
+    return out
 
 
 def main():
@@ -399,18 +523,27 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
-    if args.only_adjoint:
-        from paper_2106_00282_gb300 import build as cuda_build
+    from paper_2106_00282_gb300 import build as cuda_build
 
+    if rank == 0:
         cuda_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    if args.only_adjoint:
         ra = run_adjoint(dev, world, args.adjoint_steps, args.adjoint_ckpt)
         if rank == 0:
             print(json.dumps({"adjoint": ra}))
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    r = run_ours(args, rank, world, dev)
+    rates = measure_rates(dev)
+    r = run_ours(args, rank, world, dev, rates=rates)
     r32 = None if args.no_fp32 else run_ours(args, rank, world, dev, precision=1, with_e2e=False)
+    imp = imp32 = None
+    if not args.no_impact and args.workload != "impact":
+        imp = run_ours(args, rank, world, dev, with_e2e=False, workload="impact", rates=rates)
+        if not args.no_fp32:
+            imp32 = run_ours(args, rank, world, dev, precision=1, with_e2e=False, workload="impact")
     rb = None if args.no_batch else run_batched(dev, world, ninst=args.batch_ninst)
     ra = None if args.no_adjoint else run_adjoint(dev, world, args.adjoint_steps, args.adjoint_ckpt)
     if rank == 0:
@@ -419,10 +552,10 @@ def main():
         if not args.no_cpu:
             from paper_2106_00282_gb300 import inputs as I
 
-            rate, nst, el = oracle_rate(I.bench_workload(args.workload))
+            rate, nst, el = oracle_rate(I.bench_workload(args.workload), budget_s=args.cpu_budget)
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{nst} oracle steps of the full {wl.nx}x{wl.ny} grid from the initial state "
-                             f"({el:.1f} s, single-threaded C, -O2 -ffp-contract=off)",
+                   "sample": f"the first {nst} oracle steps of the full {wl.nx}x{wl.ny} grid from the initial "
+                             f"state ({el:.1f} s, single-threaded C, -O2 -ffp-contract=off)",
                    "host": host_cpu()}
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -430,20 +563,24 @@ def main():
                 "config": dict(workload_desc(wl), parallelism=f"replicas{world}" if world > 1 else "single"),
                 "hbm_roofline_frac_alg": r["hbm_frac"], "hbm": r["hbm"], "roofline": r["roofline"],
                 "cpu_baseline": cpu,
-                "e2e": r["e2e"], "clocks": r["clocks"], "gpu_launches": r["launches"]}
+                "e2e": r["e2e"], "clocks": r["clocks"], "gpu_launches": r["launches"],
+                "rates": rates,
+                "cheb_P": {k: sorted({P for row in v for P in (row if isinstance(row, list) else [row])})
+                           for k, v in r["P"].items()} if r["P"] else None}
+        if r32 is not None:
+            line["fp32_bulk"] = dict(brief(r32, r), **{
+                "precision": "FP32 flux/stencil arithmetic; FP64 state accumulation, phase pressures, "
+                             "volume-fraction transport, relaxation root solves, Chebyshev parameters",
+                "accuracy": "relative L1 per conserved field vs the FP64 oracle <= 2e-5 after 100 steps "
+                            "(tests/test_gpu_fp32.py)"})
+        if imp is not None:
+            line["impact"] = dict(brief(imp), config=workload_desc(imp["wl"]))
+            if imp32 is not None:
+                line["impact"]["fp32_bulk"] = brief(imp32, imp)
         if rb is not None:
             line["batched"] = rb
         if ra is not None:
             line["adjoint"] = ra
-        if r32 is not None:
-            line["fp32_bulk"] = {
-                "value": r32["value"], "unit": UNIT, "ms_per_step": r32["ms_per_step"],
-                "speedup_vs_fp64": r32["value"] / r["value"], "clocks": r32["clocks"],
-                "kernels_us": {k: round(v["avg_us"], 1) for k, v in r32["roofline"]["kernels"].items()},
-                "precision": "FP32 flux/stencil arithmetic; FP64 state accumulation, phase pressures, "
-                             "volume-fraction transport, relaxation root solves, Chebyshev parameters",
-                "accuracy": "relative L1 per conserved field vs the FP64 oracle <= 2e-5 after 100 steps "
-                            "(tests/test_gpu_fp32.py)"}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -459,7 +596,11 @@ def main_reference(args, rank, world):
     O.build()
     wl = I.bench_workload(args.workload)
     U = O.from_primitive(wl.params, wl.prim)
-    for _ in range(max(3, args.warmup)):
+    # the plain C oracle has no warm-up effects beyond the first step's page
+    # faults: one untimed step keeps the run within a few minutes on the
+    # 2048^2 grid (seconds per step)
+    wu = 1 if wl.nx * wl.ny > 1 << 20 else max(3, args.warmup)
+    for _ in range(wu):
         U = O.step(wl.params, U, wl.dx, wl.dy, 1)[0]
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -467,12 +608,12 @@ def main_reference(args, rank, world):
     el = time.perf_counter() - t0
     value = wl.nx * wl.ny * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * el / args.steps,
+            "steps": args.steps, "warmup": wu, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_desc(wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full oracle steps of the {wl.nx}x{wl.ny} grid after "
-                                       f"{max(3, args.warmup)} warm-up steps",
+                                       f"{wu} untimed step(s)",
                              "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

@@ -232,7 +232,9 @@ int dim_wait_selftest(dim_ctx *c, double seconds);
  * parametrisation to dim_grad.  Asynchronous.  Errors: DIM_EINVAL, DIM_ECUDA. */
 int dim_from_primitive_vjp(dim_ctx *c, const double *prim, const double *Ubar, double *primbar);
 
-/* The sweep of dim_hllc_sweep without a context and without any allocation.
+/* The sweep of dim_hllc_sweep without a context and without any allocation,
+ * in the precision p->precision selects (the FP64 or the FP32-bulk sweep
+ * kernel, as dim_hllc_sweep picks them).
  * The paper has no counterpart: this entry point exists for callers that
  * cannot let a library allocate device memory -- applications whose own pool
  * allocator owns all device memory, programs with a device-memory budget fixed
@@ -244,8 +246,9 @@ int dim_from_primitive_vjp(dim_ctx *c, const double *prim, const double *Ubar, d
  * until the process exits.
  *  - p, nx, ny, dx, dy: as for dim_init (validated the same way); U: device
  *    state as everywhere (8 planes, caller-owned), updated in place; axis 0 = x,
- *    1 = y; dt > 0; relax != 0 applies the Sec. 3.3 pressure relaxation after
- *    the sweep; cuda_stream: a cudaStream_t (NULL: legacy default stream).
+ *    1 = y; dt > 0; relax != 0 applies the pressure relaxation of
+ *    dim_relax(DIM_RELAX_PRESSURE) after the sweep; cuda_stream: a
+ *    cudaStream_t (NULL: legacy default stream).
  *  - Returns DIM_ETOOLARGE if nx * ny > DIM_NOALLOC_MAX_CELLS, DIM_EINVAL for
  *    invalid arguments, DIM_ECUDA if a CUDA call fails.  Asynchronous.
  *  - The first call on a device sets that device up (looks up the array's
@@ -254,7 +257,11 @@ int dim_from_primitive_vjp(dim_ctx *c, const double *prim, const double *Ubar, d
  *  - All calls on a device share the one array, which keeps the last call's
  *    contents (the status scalars are cleared at every call): calls that
  *    overlap on the GPU (different streams, or different host threads) race and
- *    give wrong results; serialise them. */
+ *    give wrong results; serialise them.
+ *  - The sweep's status bits (NaN met, a relaxation quadratic without an
+ *    admissible root) go to status scalars inside the fixed array, which no
+ *    entry point reads: this entry point cannot report them.  A caller that
+ *    needs them uses dim_hllc_sweep and dim_status. */
 #define DIM_NOALLOC_MAX_CELLS 65536
 int dim_hllc_sweep_noalloc(const dim_params *p, int nx, int ny, double dx, double dy, double *U, int axis, double dt,
                            int relax, void *cuda_stream);

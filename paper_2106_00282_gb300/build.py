@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdim.so")
 SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulk32.cu", "dim_batch.cu",
-           "dim_adjoint.cu", "dim_grad.cu"]
+           "dim_adjoint.cu", "dim_grad.cu", "dim_probe.cu"]
 # the FP32-bulk kernels may contract multiply-adds (no bit-compatibility claim)
 FMA_SOURCES = {"dim_bulk32.cu", "dim_batch.cu"}
 HEADERS = ["dim_device.cuh", "dim_bulk32.cuh", "dim_ctx.h"]
@@ -42,7 +42,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     """Compile (if stale) and return the path of libdim.so."""
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "dim.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h) for h in ("dim.h", "dim_probe.h")]
     procs, objs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -415,13 +415,21 @@ int dim_step_host(dim_ctx *c, double *U_host, int nsteps, double *dt_last)
     const size_t n = (size_t)c->p.n, bytes = sizeof(double) * 8 * n, two = sizeof(double) * 2 * n;
     if (!c->Uh && cudaMalloc(&c->Uh, bytes) != cudaSuccess) return DIM_ECUDA;
     if (!c->side) {
-        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
-            c->side = nullptr;
+        // the two events first, the stream last: c->side is set only once all
+        // three exist, and a failure destroys whatever was created
+        cudaEvent_t em = nullptr, eo = nullptr;
+        cudaStream_t sd = nullptr;
+        if (cudaEventCreateWithFlags(&em, cudaEventDisableTiming) != cudaSuccess) em = nullptr;
+        if (em && cudaEventCreateWithFlags(&eo, cudaEventDisableTiming) != cudaSuccess) eo = nullptr;
+        if (eo && cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking) != cudaSuccess) sd = nullptr;
+        if (!sd) {
+            if (eo) cudaEventDestroy(eo);
+            if (em) cudaEventDestroy(em);
             return DIM_ECUDA;
         }
-        if (cudaEventCreateWithFlags(&c->ev_mass, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_mom, cudaEventDisableTiming) != cudaSuccess)
-            return DIM_ECUDA;
+        c->ev_mass = em;
+        c->ev_mom = eo;
+        c->side = sd;
     }
     TRY(cudaMemcpyAsync(c->Uh, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
     if (nsteps == 0) {

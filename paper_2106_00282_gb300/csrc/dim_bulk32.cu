@@ -293,13 +293,19 @@ constexpr int SY32_TN = 32, SY32_TL = 8;
 
 static int g_heat32_blocks = 0, g_visc32_blocks[2] = {0, 0};
 
-cudaError_t bulk32_setup(int nsm)
+// the FP32 sweep kernels' shared-memory limit (once per device)
+cudaError_t sweep32_setup()
 {
     cudaError_t e = cudaFuncSetAttribute(k_sweep32<0, SX32_TN, SX32_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sweep32_smem(SX32_TN, SX32_TL));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_sweep32<1, SY32_TN, SY32_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep32_smem(SY32_TN, SY32_TL));
+    return cudaFuncSetAttribute(k_sweep32<1, SY32_TN, SY32_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep32_smem(SY32_TN, SY32_TL));
+}
+
+cudaError_t bulk32_setup(int nsm)
+{
+    cudaError_t e = sweep32_setup();
     if (e != cudaSuccess) return e;
     int b = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heat32, 256, 0);

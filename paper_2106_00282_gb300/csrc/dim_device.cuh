@@ -138,25 +138,37 @@ __device__ __forceinline__ bool lt_i(double x, double y)  // x < y
 // iterations -- reciprocal r <- r + r(1 - b r), reciprocal square root
 // y <- y + y(1/2 - x y^2 / 2), each doubling the correct bits -- and one
 // final correction of the quotient q <- q + r(a - b q) (Markstein) and of the
-// root s <- s + (y/2)(x - s^2).  Within about an ulp of the IEEE results (checked
-// against them on the GPU), at a fraction of the cost of the IEEE division
-// and square-root sequences on the FP64 pipe.  The FP64 path keeps IEEE / and
-// sqrt (FAST = false below).
+// root s <- s + (y/2)(x - s^2).  Within an ulp of the IEEE results, at a
+// fraction of the cost of the IEEE division and square-root sequences on the
+// FP64 pipe.  The approximations flush subnormal operands and results to zero
+// and the corrections turn infinities into NaN, so both routines check their
+// domain on the integer pipe and hand everything outside it to the IEEE
+// operation (an out-of-line call, taken only at the edges):
+//   fast_div(a, b): b normal with a normal reciprocal (biased exponent of b in
+//     1..2044), and the quotient a normal finite number or a zero from a = +-0;
+//   fast_sqrt(x): x positive, normal and finite.
+// The FP64 path keeps IEEE / and sqrt (FAST = false below).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double fast_rcp(double b)
+static __device__ __noinline__ double ieee_div(double a, double b) { return a / b; }
+static __device__ __noinline__ double ieee_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ unsigned biased_exp(double x)  // the 11-bit exponent field, sign bit above it
+{
+    return (unsigned)__double2hiint(x) >> 20;
+}
+__device__ __forceinline__ double fast_div(double a, double b)
 {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
     double e = fma(-b, r, 1.0);
     r = fma(r, e, r);
     e = fma(-b, r, 1.0);
-    return fma(r, e, r);
-}
-__device__ __forceinline__ double fast_div(double a, double b)
-{
-    const double r = fast_rcp(b);
-    const double q = a * r;
-    return fma(r, fma(-b, q, a), q);
+    r = fma(r, e, r);
+    const double q0 = a * r;
+    const double q = fma(r, fma(-b, q0, a), q0);
+    const unsigned eb = biased_exp(b) & 0x7ffu, eq = biased_exp(q) & 0x7ffu;
+    const bool a_zero = (__double_as_longlong(a) << 1) == 0;
+    const bool ok = (eb - 1u) < 2044u && ((eq - 1u) < 2046u || a_zero);
+    return ok ? (a_zero ? q0 : q) : ieee_div(a, b);  // q0 = a r keeps the sign of a zero quotient
 }
 __device__ __forceinline__ double fast_sqrt(double x)
 {
@@ -167,7 +179,8 @@ __device__ __forceinline__ double fast_sqrt(double x)
     y = fma(y, fma(-h * y, y, 0.5), y);
     const double s = x * y;
     const double r = fma(-s, s, x);
-    return x > 0.0 ? fma(0.5 * y, r, s) : x;  // sqrt(0) = 0 (and NaN stays NaN)
+    const bool ok = (biased_exp(x) - 1u) < 2046u;  // sign bit clear, exponent 1..2046
+    return ok ? fma(0.5 * y, r, s) : ieee_sqrt(x);
 }
 template <bool FAST>
 __device__ __forceinline__ double dv(double a, double b)

@@ -20,8 +20,11 @@
 
 namespace dimk {
 cudaError_t sweep_setup();
+cudaError_t sweep32_setup();
 cudaError_t launch_sweep(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
                          int relax, int check, cudaStream_t s);
+cudaError_t launch_sweep32(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
+                           int relax, int check, cudaStream_t s);
 }  // namespace dimk
 int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, dimk::DevParams *out);
 
@@ -41,8 +44,8 @@ double *g_scratch_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per
 bool g_ready[kMaxDevices];
 
 // once per device, with that device current: the device address of the array
-// (the host-side name is only a stand-in) and the sweep kernels' shared-memory
-// attribute
+// (the host-side name is only a stand-in) and the shared-memory attribute of
+// the sweep kernels of both precisions
 int setup_current_device(double **scratch)
 {
     int dev = 0;
@@ -52,7 +55,7 @@ int setup_current_device(double **scratch)
     if (!g_ready[dev]) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return DIM_ECUDA;
-        if (dimk::sweep_setup() != cudaSuccess) return DIM_ECUDA;
+        if (dimk::sweep_setup() != cudaSuccess || dimk::sweep32_setup() != cudaSuccess) return DIM_ECUDA;
         g_scratch_ptr[dev] = (double *)ptr;
         g_ready[dev] = true;
     }
@@ -78,7 +81,11 @@ extern "C" int dim_hllc_sweep_noalloc(const dim_params *p, int nx, int ny, doubl
     dimk::Scalars *sc = (dimk::Scalars *)(scratch + 8 * kPlaneDoubles);
     // the array keeps the previous call's contents: the status scalars start at zero
     if (cudaMemsetAsync(sc, 0, sizeof(dimk::Scalars), s) != cudaSuccess) return DIM_ECUDA;
-    if (dimk::launch_sweep(dp, axis, U, Uout, dt, sc, relax, 0, s) != cudaSuccess) return DIM_ECUDA;
+    // the kernel of the parameters' precision, as dim_hllc_sweep picks it
+    const cudaError_t e = dp.precision == DIM_PRECISION_FP32_BULK
+                              ? dimk::launch_sweep32(dp, axis, U, Uout, dt, sc, relax, 0, s)
+                              : dimk::launch_sweep(dp, axis, U, Uout, dt, sc, relax, 0, s);
+    if (e != cudaSuccess) return DIM_ECUDA;
     if (cudaMemcpyAsync(U, Uout, sizeof(double) * 8 * (size_t)dp.n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return DIM_ECUDA;
     return DIM_OK;

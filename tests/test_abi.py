@@ -9,8 +9,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "dim.h")).read()
+def _declared(header="dim.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(dim_[a-z_]+)\s*\(", src)))
 
@@ -31,6 +31,14 @@ def test_header_symbols_exported(lib):
     assert sorted(_lib.SYMBOLS) == names
     for n in names:
         assert getattr(lib, n) is not None, n
+    probes = _declared("dim_probe.h")
+    assert sorted(_lib.PROBE_SYMBOLS) == probes
+    for n in probes:
+        assert getattr(lib, n) is not None, n
+
+
+def test_every_header_checked():
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["dim.h", "dim_probe.h"]
 
 
 def test_strerror(lib):
@@ -73,3 +81,7 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dim_step_sched(None, None, 1, None, 0) == _lib.DIM_EINVAL
     assert lib.dim_from_primitive_vjp(None, None, None, None) == _lib.DIM_EINVAL
     assert lib.dim_wait_selftest(None, 0.1) == _lib.DIM_EINVAL
+    ms, ops = C.c_double(), C.c_double()
+    assert lib.dim_probe_rate(9, 0, 10, None, C.byref(ms), C.byref(ops)) == _lib.DIM_EINVAL
+    assert lib.dim_probe_rate(0, 0, 0, None, C.byref(ms), C.byref(ops)) == _lib.DIM_EINVAL
+    assert lib.dim_probe_fastmath(None, None, None, None, 4, None) == _lib.DIM_EINVAL
