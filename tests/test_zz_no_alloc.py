@@ -23,7 +23,10 @@ def _rel_l1(a, b):
     return num / np.maximum(den, 1e-300)
 
 
-def test_noalloc_sweep_matches_context_sweep():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_noalloc_sweep_matches_context_sweep(precision):
+    """precision 0: the FP64 sweep; 1: the FP32-bulk sweep (the parameters pick
+    the kernel on both paths)."""
     import torch
 
     from paper_2106_00282_gb300 import _lib, build, inputs as I
@@ -33,6 +36,7 @@ def test_noalloc_sweep_matches_context_sweep():
     build.build()
     L = _lib.load()
     wl = I.impact(240, 200)  # 48,000 cells: several tiles per axis and ragged tails
+    wl.params = wl.params.replace(precision=precision)
     assert wl.nx * wl.ny <= _lib.NOALLOC_MAX_CELLS
     s = Solver(wl.params, wl.nx, wl.ny, wl.dx, wl.dy)
     U = s.from_primitive(torch.from_numpy(wl.prim).cuda())
