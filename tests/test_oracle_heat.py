@@ -126,9 +126,20 @@ def test_lim_maximum_principle(O, I, tau, P):
     assert abs(v1.sum() - v0.sum()) < 1e-10
 
 
+def _cheb_b(P, lam):
+    """Eq. LIM parameters: beta_m = cos((2m - 1) pi / (2P)) in decreasing order
+    (reading of the ordering), a_m = lam (beta_1 - beta_m)/(1 + beta_1),
+    b = (a_P, ..., a_2, a_P, ..., a_1)."""
+    beta = [math.cos((2 * m - 1) * math.pi / (2 * P)) for m in range(1, P + 1)]
+    a = [lam * (beta[0] - beta[m - 1]) / (1.0 + beta[0]) for m in range(1, P + 1)]
+    return [a[m - 1] for m in range(P, 1, -1)] + [a[m - 1] for m in range(P, 0, -1)]
+
+
 def test_lim_matches_dense_polynomial(O, I):
     """The 2P-1 sweeps equal the same recurrence carried out with the dense
-    matrix of the operator (checks the stencil, the face means and the walls)."""
+    matrix of the operator (checks the stencil, the face means and the walls):
+    Eq. LIM as printed, v <- (v^n + tau b_m v + tau A v) / (1 + tau b_m), with
+    the 1/h^2 of Eq. qk_dis per face and the parameters b_m computed here."""
     rng = np.random.default_rng(9)
     nx, ny = 6, 5
     lam = rng.uniform(0.5, 2.0, (ny, nx))
@@ -139,11 +150,12 @@ def test_lim_matches_dense_polynomial(O, I):
         tau = 0.02
         v1, Pn, lm = O.lim_solve(p, lam, V, v0, 0.1, 0.1, tau)
         A = _dense_operator(lam, V, 0.1, 0.1, bc)
-        b = O.cheb_schedule(Pn, lm)
+        b = _cheb_b(Pn, lm)
+        assert np.allclose(b, O.cheb_schedule(Pn, lm), rtol=1e-14, atol=1e-14 * lm)
         v = v0.reshape(-1).copy()
         u0 = v.copy()
         for m in range(2 * Pn - 1):
-            v = (u0 + tau * b[m] * v + tau * (A @ v)) * (1 / (1 + tau * b[m]))
+            v = (u0 + tau * b[m] * v + tau * (A @ v)) / (1 + tau * b[m])
         assert np.max(np.abs(v - v1.reshape(-1))) < 1e-12
 
 

@@ -53,6 +53,26 @@ def test_sound_speed_of_air(O, I):
         assert abs(1.0 / dt - 346.2) < 1.0
 
 
+def test_sound_speed_of_stiffened_water(O, I):
+    """A stiffened-gas phase at temperature T has p + pinf = (gamma - 1) rho Cv T
+    (Eq. eos_stiffened2), so c^2 = gamma (p + pinf)/rho = gamma (gamma - 1) Cv T,
+    whatever the pressure: water (gamma 4.4, pinf 6e8, Cv 1606) at 300 K gives
+    c = 2684.7 m/s at 1e5, 1e8 and 1e9 Pa (a dropped pinf would give 21 m/s at
+    1e5 Pa).  The air traces (alpha_2 = 1e-8) move c by < 1e-7."""
+    p = I.Params(gamma=(4.4, 1.4), pinf=(6e8, 0.0), cv=(1606.0, 714.0), cfl=1.0)
+    c_exact = math.sqrt(4.4 * 3.4 * 1606.0 * 300.0)
+    assert abs(c_exact - 2684.7) < 0.05
+    for pr_ in (1e5, 1e8, 1e9):
+        for T in (300.0, 600.0):
+            prim = np.zeros((5, 1, 2))
+            prim[0] = 1e-8
+            prim[1] = pr_
+            prim[2] = T
+            U = O.from_primitive(p, prim)
+            c = 1.0 / O.dt(p, U, 1.0, 1.0)
+            assert abs(c / (c_exact * math.sqrt(T / 300.0)) - 1.0) < 1e-6, (pr_, T, c)
+
+
 def test_primitive_roundtrip(O, I):
     """Both phases at the prescribed (p, T) after the conversion (Eqs.
     eos_stiffened, eos_stiffened2)."""
