@@ -193,7 +193,7 @@ def measure_rates(dev) -> dict:
     chains of one operation in every thread, 8 blocks of 256 threads per SM,
     CUDA events; best of three after one warm-up): FP64 FMA and FP32 FMA in
     TFLOP/s, FP64 add/multiply without contraction in TFLOP/s, IEEE FP64
-    division and square root and the FP32-bulk kernels' division in G/s."""
+    division and square root in G/s."""
     import ctypes as C
 
     import torch
@@ -204,7 +204,7 @@ def measure_rates(dev) -> dict:
     stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     kinds = {"dfma_tflops": (_lib.PROBE_DFMA, 4000, 1e12), "daddmul_tflops": (_lib.PROBE_DADDMUL, 4000, 1e12),
              "ddiv_gops": (_lib.PROBE_DDIV, 1000, 1e9), "dsqrt_gops": (_lib.PROBE_DSQRT, 1000, 1e9),
-             "ffma_tflops": (_lib.PROBE_FFMA, 100000, 1e12), "fastdiv_gops": (_lib.PROBE_FASTDIV, 1000, 1e9)}
+             "ffma_tflops": (_lib.PROBE_FFMA, 100000, 1e12)}
     out = {}
     for name, (kind, iters, scale) in kinds.items():
         best = 0.0
@@ -569,8 +569,10 @@ def main():
                            for k, v in r["P"].items()} if r["P"] else None}
         if r32 is not None:
             line["fp32_bulk"] = dict(brief(r32, r), **{
-                "precision": "FP32 flux/stencil arithmetic; FP64 state accumulation, phase pressures, "
-                             "volume-fraction transport, relaxation root solves, Chebyshev parameters",
+                "precision": "no FP64 arithmetic inside a step: float-float state (accumulation, phase "
+                             "pressures, volume fraction, cold energies, Newton-corrected relaxation roots), "
+                             "FP32 flux, relaxation and stencil arithmetic; FP64 <-> float-float conversion "
+                             "once per call",
                 "accuracy": "relative L1 per conserved field vs the FP64 oracle <= 2e-5 after 100 steps "
                             "(tests/test_gpu_fp32.py)"})
         if imp is not None:

@@ -68,9 +68,12 @@ extern "C" {
 #define DIM_P_CLAMP 2            /* P = clamp(formula, p_min, p_max) */
 
 #define DIM_PRECISION_FP64 0      /* every operation in FP64 */
-#define DIM_PRECISION_FP32_BULK 1 /* flux and stencil arithmetic in FP32; state accumulation, phase
-                                     pressures, volume-fraction transport and the relaxation root solves
-                                     in FP64 */
+#define DIM_PRECISION_FP32_BULK 1 /* no FP64 arithmetic inside a step: the state is carried as
+                                     float-float pairs (47 bits), which hold the accumulation, the phase
+                                     pressures' cancellation against the stiffened-gas cold energy, the
+                                     volume fraction and its transport, and one Newton correction of each
+                                     relaxation root; flux, relaxation and stencil arithmetic in FP32.  The
+                                     caller's state stays FP64; each call converts it once in and out */
 
 #define DIM_RELAX_PRESSURE 0    /* dim_relax: Sec. 3.3 three-step pressure relaxation */
 #define DIM_RELAX_TEMPERATURE 1 /* dim_relax: Sec. 3.4.1 temperature relaxation */
@@ -304,8 +307,9 @@ int dim_status(dim_ctx *c, unsigned *flags, int reset);
 /* Per-kernel timing with CUDA events on the context stream.  enable != 0 turns
  * it on (events around every launch), 0 off.  dim_kernel_time returns the
  * accumulated launches and milliseconds of kernel `name` ("sweep_x",
- * "sweep_y", "heat", "viscous_x", "viscous_y", "wave_max", "relax") since the
- * last reset; synchronizes. */
+ * "sweep_y", "heat", "viscous_x", "viscous_y", "wave_max", "relax", "copy",
+ * "convert": the FP64 <-> float-float state conversions of the FP32-bulk form)
+ * since the last reset; synchronizes. */
 int dim_profile(dim_ctx *c, int enable, int reset);
 int dim_kernel_time(dim_ctx *c, const char *name, int *launches, double *ms);
 

@@ -30,8 +30,8 @@ SYMBOLS = ["dim_init", "dim_destroy", "dim_from_primitive", "dim_cfl_dt", "dim_s
            "dim_batch_layout", "dim_batch_from_primitive", "dim_batch_step", "dim_batch_autotune",
            "dim_batch_status", "dim_step_sched", "dim_from_primitive_vjp", "dim_wait_selftest"]
 # measurement and self-check entry points (include/dim_probe.h)
-PROBE_SYMBOLS = ["dim_probe_rate", "dim_probe_fastmath"]
-PROBE_DFMA, PROBE_DADDMUL, PROBE_DDIV, PROBE_DSQRT, PROBE_FFMA, PROBE_FASTDIV = 0, 1, 2, 3, 4, 5
+PROBE_SYMBOLS = ["dim_probe_rate", "dim_probe_ff_roundtrip"]
+PROBE_DFMA, PROBE_DADDMUL, PROBE_DDIV, PROBE_DSQRT, PROBE_FFMA = 0, 1, 2, 3, 4
 
 
 class DimParams(C.Structure):
@@ -106,8 +106,8 @@ def load(path: str = LIB_PATH):
     L.dim_strerror.argtypes = [i]
     L.dim_probe_rate.argtypes = [i, i, i, vp, pd, pd]
     L.dim_probe_rate.restype = i
-    L.dim_probe_fastmath.argtypes = [vp, vp, vp, vp, i, vp]
-    L.dim_probe_fastmath.restype = i
+    L.dim_probe_ff_roundtrip.argtypes = [vp, vp, i, vp]
+    L.dim_probe_ff_roundtrip.restype = i
     L.dim_strerror.restype = C.c_char_p
     for name in SYMBOLS:
         if name not in ("dim_destroy", "dim_strerror") and not name.startswith("dim_batch"):

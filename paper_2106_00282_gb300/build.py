@@ -14,11 +14,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdim.so")
-SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulk32.cu", "dim_batch.cu",
+SOURCES = ["dim_api.cu", "dim_sweep.cu", "dim_parabolic.cu", "dim_noalloc.cu", "dim_bulkff.cu", "dim_batch.cu",
            "dim_adjoint.cu", "dim_grad.cu", "dim_probe.cu"]
-# the FP32-bulk kernels may contract multiply-adds (no bit-compatibility claim)
-FMA_SOURCES = {"dim_bulk32.cu", "dim_batch.cu"}
-HEADERS = ["dim_device.cuh", "dim_bulk32.cuh", "dim_ctx.h"]
+# the FP32-bulk kernels may contract multiply-adds (no bit-compatibility claim;
+# their float-float operations are explicit round-to-nearest intrinsics, which
+# are never contracted)
+FMA_SOURCES = {"dim_bulkff.cu", "dim_batch.cu"}
+HEADERS = ["dim_device.cuh", "dim_ff.cuh", "dim_ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

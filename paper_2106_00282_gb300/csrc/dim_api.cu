@@ -15,8 +15,8 @@
 
 using namespace dimctx;
 
-static const char *const kKernelNames[K_NKERNELS] = {"sweep_x", "sweep_y", "heat", "viscous_x",
-                                                     "viscous_y", "wave_max", "relax", "copy"};
+static const char *const kKernelNames[K_NKERNELS] = {"sweep_x", "sweep_y", "heat",  "viscous_x", "viscous_y",
+                                                     "wave_max", "relax",   "copy", "convert"};
 
 static bool g_setup_done[64];
 
@@ -85,26 +85,24 @@ static dimk::ViscScratch visc_scratch(dim_ctx *c)
 
 static bool fp32(const dim_ctx *c) { return c->p.precision == DIM_PRECISION_FP32_BULK; }
 
+// FP64 stage launchers
 static cudaError_t run_sweep(dim_ctx *c, int axis, const double *Uin, double *Uout, double dt, int relax, int check)
 {
-    return fp32(c) ? dimk::launch_sweep32(c->p, axis, Uin, Uout, dt, c->sc, relax, check, c->stream)
-                   : dimk::launch_sweep(c->p, axis, Uin, Uout, dt, c->sc, relax, check, c->stream);
+    return dimk::launch_sweep(c->p, axis, Uin, Uout, dt, c->sc, relax, check, c->stream);
 }
-static cudaError_t run_wave(dim_ctx *c, const double *U)
-{
-    return fp32(c) ? dimk::launch_wave_max32(c->p, U, c->sc, c->stream)
-                   : dimk::launch_wave_max(c->p, U, c->sc, c->stream);
-}
+static cudaError_t run_wave(dim_ctx *c, const double *U) { return dimk::launch_wave_max(c->p, U, c->sc, c->stream); }
 static cudaError_t run_heat(dim_ctx *c, double *U, double dt, int trelax_first, int check)
 {
-    return fp32(c) ? dimk::launch_heat32(c->p, U, c->S, c->sc, dt, trelax_first, check, c->stream)
-                   : dimk::launch_heat(c->p, U, heat_scratch(c), c->sc, dt, trelax_first, check, c->stream);
+    return dimk::launch_heat(c->p, U, heat_scratch(c), c->sc, dt, trelax_first, check, c->stream);
 }
 static cudaError_t run_visc(dim_ctx *c, int axis, double *U, double dt, int relax, int check)
 {
-    return fp32(c) ? dimk::launch_visc32(c->p, axis, U, c->S, c->sc, dt, relax, check, c->stream)
-                   : dimk::launch_visc(c->p, axis, U, visc_scratch(c), c->sc, dt, relax, check, c->stream);
+    return dimk::launch_visc(c->p, axis, U, visc_scratch(c), c->sc, dt, relax, check, c->stream);
 }
+
+// FP32 bulk: the second float-float buffer of the sweeps (the context's U2)
+static float2 *ff_other(dim_ctx *c) { return (float2 *)c->U2; }
+static size_t state_len(const dim_ctx *c) { return 8 * (size_t)c->p.n; }
 
 #define TIMED(c, kid, launch)                      \
     do {                                           \
@@ -234,7 +232,7 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
         int nsm = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             dimk::sweep_setup() != cudaSuccess || dimk::parabolic_setup(nsm) != cudaSuccess ||
-            dimk::bulk32_setup(nsm) != cudaSuccess) {
+            dimk::bulkff_setup(nsm) != cudaSuccess) {
             free(c);
             return DIM_ECUDA;
         }
@@ -243,10 +241,12 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
     size_t plane = sizeof(double) * (size_t)p.n;
     if (cudaMalloc(&c->U2, 8 * plane) != cudaSuccess || cudaMalloc(&c->S, dimk::SCRATCH_PLANES * plane) != cudaSuccess ||
         cudaMalloc(&c->sc, sizeof(Scalars)) != cudaSuccess || cudaMemset(c->sc, 0, sizeof(Scalars)) != cudaSuccess ||
-        cudaMalloc(&c->beta, sizeof(double) * dimk::PMAX * dimk::PMAX) != cudaSuccess) {
+        cudaMalloc(&c->beta, sizeof(double) * dimk::PMAX * dimk::PMAX) != cudaSuccess ||
+        (p.precision == DIM_PRECISION_FP32_BULK && cudaMalloc(&c->Uf, 8 * plane) != cudaSuccess)) {
         dim_destroy(c);
         return DIM_ECUDA;
     }
+    c->ffp = dimk::ffp_of(p);
     {
         // roots of the Chebyshev polynomials T_P, P = 1..PMAX, in decreasing order
         const double pi = 3.14159265358979323846;
@@ -269,6 +269,7 @@ void dim_destroy(dim_ctx *c)
     cudaStreamSynchronize(c->stream);
     grad_free(c);
     cudaFree(c->U2);
+    cudaFree(c->Uf);
     cudaFree(c->S);
     cudaFree(c->Uh);
     if (c->side) {
@@ -298,7 +299,12 @@ int dim_cfl_dt(dim_ctx *c, const double *U, double *dt)
 {
     if (!c || !U || !dt) return DIM_EINVAL;
     TRY(reset_accumulators(c));
-    TIMED(c, K_WAVE, run_wave(c, U));
+    if (fp32(c)) {
+        TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
+        TIMED(c, K_WAVE, dimk::launch_wave_ff(c->p, c->ffp, c->Uf, c->sc, c->stream));
+    } else {
+        TIMED(c, K_WAVE, run_wave(c, U));
+    }
     unsigned long long bits = 0;
     TRY(cudaMemcpyAsync(&bits, &c->sc->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
     TRY(cudaStreamSynchronize(c->stream));
@@ -370,6 +376,57 @@ static int step_once(dim_ctx *c, double *U, StepMarks *mk = nullptr)
     return DIM_OK;
 }
 
+// FP32 bulk: one split step on the float-float state *cur, the sweeps
+// alternating between the two FF buffers (same stages as step_once)
+static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth)
+{
+    const dim_params &h = c->hp;
+    const DevParams &p = c->p;
+    const dimk::FFP &f = c->ffp;
+    const bool vis = viscous_on(h), heat = heat_on(h), trx = h.trelax != DIM_TRELAX_OFF;
+    const bool sx = p.nx > 1, sy = p.ny > 1;
+    enum { LAST_SX, LAST_SY, LAST_VX, LAST_VY, LAST_TR, LAST_HEAT } last;
+    if (heat) last = LAST_HEAT;
+    else if (trx) last = LAST_TR;
+    else if (vis) last = sy ? LAST_VY : LAST_VX;
+    else last = sy ? LAST_SY : LAST_SX;
+
+    TRY(reset_accumulators(c));
+    TIMED(c, K_WAVE, dimk::launch_wave_ff(p, f, cur, c->sc, c->stream));
+    if (sx) {
+        TIMED(c, K_SWEEP_X, dimk::launch_sweep_ff(p, f, 0, cur, oth, 0.0, c->sc, 1, last == LAST_SX, c->stream));
+        float2 *t = cur; cur = oth; oth = t;
+    }
+    if (sy) {
+        TIMED(c, K_SWEEP_Y, dimk::launch_sweep_ff(p, f, 1, cur, oth, 0.0, c->sc, 1, last == LAST_SY, c->stream));
+        float2 *t = cur; cur = oth; oth = t;
+    }
+    if (vis) {
+        if (sx) TIMED(c, K_VISC_X, dimk::launch_visc_ff(p, f, 0, cur, c->S, c->sc, 0.0, !sy, last == LAST_VX, c->stream));
+        if (sy) TIMED(c, K_VISC_Y, dimk::launch_visc_ff(p, f, 1, cur, c->S, c->sc, 0.0, 1, last == LAST_VY, c->stream));
+    }
+    if (heat) {
+        TIMED(c, K_HEAT, dimk::launch_heat_ff(p, f, cur, c->S, c->sc, 0.0, 1, 1, c->stream));
+    } else if (trx) {
+        TIMED(c, K_RELAX, dimk::launch_relax_ff(p, f, cur, c->sc, DIM_RELAX_TEMPERATURE, 1, c->stream));
+    }
+    return DIM_OK;
+}
+
+// FP32 bulk: nsteps steps of the device state U through the FF planes (one
+// conversion in, one out)
+static int steps_ff(dim_ctx *c, double *U, int nsteps)
+{
+    float2 *cur = c->Uf, *oth = ff_other(c);
+    TIMED(c, K_CONVERT, dimk::launch_ff_in(U, cur, state_len(c), c->stream));
+    for (int s = 0; s < nsteps; s++) {
+        int r = step_once_ff(c, cur, oth);
+        if (r != DIM_OK) return r;
+    }
+    TIMED(c, K_CONVERT, dimk::launch_ff_out(cur, U, state_len(c), c->stream));
+    return DIM_OK;
+}
+
 // After a timed-out grid barrier the barrier counters may hold arrivals of
 // blocks that left: clear them so that the next cooperative launch starts
 // from a consistent barrier.
@@ -401,9 +458,16 @@ static int read_back(dim_ctx *c, double *dt_last)
 int dim_step(dim_ctx *c, double *U, int nsteps, double *dt_last)
 {
     if (!c || !U || nsteps < 0) return DIM_EINVAL;
-    for (int s = 0; s < nsteps; s++) {
-        int r = step_once(c, U);
-        if (r != DIM_OK) return r;
+    if (fp32(c)) {
+        if (nsteps > 0) {
+            int r = steps_ff(c, U, nsteps);
+            if (r != DIM_OK) return r;
+        }
+    } else {
+        for (int s = 0; s < nsteps; s++) {
+            int r = step_once(c, U);
+            if (r != DIM_OK) return r;
+        }
     }
     if (dt_last && nsteps > 0) return read_back(c, dt_last);
     return DIM_OK;
@@ -432,7 +496,11 @@ int dim_step_host(dim_ctx *c, double *U_host, int nsteps, double *dt_last)
         c->side = sd;
     }
     TRY(cudaMemcpyAsync(c->Uh, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
-    if (nsteps == 0) {
+    if (fp32(c) && nsteps > 0) {
+        int r = steps_ff(c, c->Uh, nsteps);
+        if (r != DIM_OK) return r;
+        TRY(cudaMemcpyAsync(U_host, c->Uh, bytes, cudaMemcpyDeviceToHost, c->stream));
+    } else if (nsteps == 0) {
         TRY(cudaMemcpyAsync(U_host, c->Uh, bytes, cudaMemcpyDeviceToHost, c->stream));
     } else {
         for (int s = 0; s + 1 < nsteps; s++) {
@@ -461,6 +529,13 @@ int dim_hllc_sweep(dim_ctx *c, double *U, int axis, double dt, int relax)
 {
     if (!c || !U || (axis != 0 && axis != 1) || !(dt > 0.0)) return DIM_EINVAL;
     TRY(reset_accumulators(c));
+    if (fp32(c)) {
+        TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
+        TIMED(c, axis == 0 ? K_SWEEP_X : K_SWEEP_Y,
+              dimk::launch_sweep_ff(c->p, c->ffp, axis, c->Uf, ff_other(c), dt, c->sc, relax, 0, c->stream));
+        TIMED(c, K_CONVERT, dimk::launch_ff_out(ff_other(c), U, state_len(c), c->stream));
+        return DIM_OK;
+    }
     TIMED(c, axis == 0 ? K_SWEEP_X : K_SWEEP_Y, run_sweep(c, axis, U, c->U2, dt, relax, 0));
     TIMED(c, K_COPY, cudaMemcpyAsync(U, c->U2, sizeof(double) * 8 * (size_t)c->p.n, cudaMemcpyDeviceToDevice, c->stream));
     return DIM_OK;
@@ -469,6 +544,12 @@ int dim_hllc_sweep(dim_ctx *c, double *U, int axis, double dt, int relax)
 int dim_relax(dim_ctx *c, double *U, int which)
 {
     if (!c || !U || (which != DIM_RELAX_PRESSURE && which != DIM_RELAX_TEMPERATURE)) return DIM_EINVAL;
+    if (fp32(c)) {
+        TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
+        TIMED(c, K_RELAX, dimk::launch_relax_ff(c->p, c->ffp, c->Uf, c->sc, which, 0, c->stream));
+        TIMED(c, K_CONVERT, dimk::launch_ff_out(c->Uf, U, state_len(c), c->stream));
+        return DIM_OK;
+    }
     TIMED(c, K_RELAX, dimk::launch_relax(c->p, U, c->sc, which, 0, c->stream));
     return DIM_OK;
 }
@@ -478,8 +559,15 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
     if (!c || !U || !(dt > 0.0)) return DIM_EINVAL;
     TRY(reset_accumulators(c));
     int slot = 0;
+    const bool f32 = fp32(c);
     if (kind == DIM_PARABOLIC_HEAT) {
-        TIMED(c, K_HEAT, run_heat(c, U, dt, 0, 0));
+        if (f32) {
+            TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
+            TIMED(c, K_HEAT, dimk::launch_heat_ff(c->p, c->ffp, c->Uf, c->S, c->sc, dt, 0, 0, c->stream));
+            TIMED(c, K_CONVERT, dimk::launch_ff_out(c->Uf, U, state_len(c), c->stream));
+        } else {
+            TIMED(c, K_HEAT, run_heat(c, U, dt, 0, 0));
+        }
         slot = 0;
     } else if (kind == DIM_PARABOLIC_VISCOUS_X || kind == DIM_PARABOLIC_VISCOUS_Y) {
         int axis = kind == DIM_PARABOLIC_VISCOUS_X ? 0 : 1;
@@ -487,7 +575,14 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
             if (P_used) *P_used = 0;
             return DIM_OK;
         }
-        TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y, run_visc(c, axis, U, dt, 0, 0));
+        if (f32) {
+            TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
+            TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y,
+                  dimk::launch_visc_ff(c->p, c->ffp, axis, c->Uf, c->S, c->sc, dt, 0, 0, c->stream));
+            TIMED(c, K_CONVERT, dimk::launch_ff_out(c->Uf, U, state_len(c), c->stream));
+        } else {
+            TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y, run_visc(c, axis, U, dt, 0, 0));
+        }
         slot = 1 + axis;
     } else {
         return DIM_EINVAL;

@@ -1,12 +1,14 @@
 // dim_batch.cu -- many independent grids of uneven sizes advanced together in
 // one persistent cooperative launch per split step (sm_103a, FP32 bulk).
 //
-// Every instance keeps the single-grid layout (8 FP64 planes of its own
-// nx*ny cells) at its cell offset inside one packed buffer, its own parameters
-// (grid, spacing), its own CFL time step, its own lambda_max and Chebyshev
-// parameter count.  One launch runs all stages of one step for all instances,
-// separated by bounded grid barriers:
-//   reset -> CFL maxima -> x sweep (tiles) -> y sweep (tiles)
+// Every instance keeps the single-grid layout (8 planes of its own nx*ny cells)
+// at its cell offset inside one packed buffer, its own parameters (grid,
+// spacing), its own CFL time step, its own lambda_max and Chebyshev parameter
+// count.  A call converts the packed FP64 state to float-float planes once,
+// runs its steps on them with the cell arithmetic of the single-grid FP32-bulk
+// form (dim_ff.cuh), and converts back.  One launch runs all stages of one
+// step for all instances, separated by bounded grid barriers:
+//   reset -> CFL maxima -> time steps -> x sweep (tiles) -> y sweep (tiles)
 //   -> viscous x, viscous y -> temperature relaxation + heat conduction,
 // each parabolic stage as coefficients -> lambda_max -> per-instance schedule
 // -> 2P-2 sweeps (up to the largest P of the batch, idle for instances that
@@ -19,7 +21,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "dim_bulk32.cuh"
+#include "dim_ff.cuh"
 
 namespace dimk {
 
@@ -27,13 +29,17 @@ constexpr int BCH = 2048;  // cells per chunk
 
 struct BatchDev {
     const DevParams *prm;  // [ninst]
+    const FFP *ffp;        // [ninst]
     const long long *off;  // [ninst + 1] cell offsets
     const int *tx, *ty, *ch;  // [ninst + 1] prefix sums of x tiles, y tiles, chunks
     Scalars *sc;           // [ninst]
     Scalars *g;            // grid barrier; P[slot] = largest 2P - 2 of a solve
-    double *bs;            // [3][ninst][2 PMAX] Chebyshev schedules (viscous x, viscous y, heat)
+    double *bs;            // [3][ninst][2 PMAX] Chebyshev parameters b_m (viscous x, viscous y, heat)
+    float *tbf, *rdf;      // [3][ninst][2 PMAX] tau b_m and 1 / (1 + tau b_m)
+    float *dtf;            // [ninst] time step of the step
     int *Pi;               // [3][ninst] P per instance and solve
-    double *U, *U2, *S;
+    float2 *U, *U2;        // float-float state planes (packed), sweep ping-pong
+    double *S;             // scratch: 8 planes of doubles per instance, used as FP32 planes
     int ninst;
     int viscous, heat, trelax;
 };
@@ -60,6 +66,8 @@ __device__ __forceinline__ int chunk_range(const BatchDev &d, int t, int &c0, in
     return i;
 }
 
+__device__ __forceinline__ float *scr_f(const BatchDev &d, int i) { return (float *)(d.S + 8 * d.off[i]); }
+
 // ---------------------------------------------------------------------------
 // stages
 // ---------------------------------------------------------------------------
@@ -68,62 +76,70 @@ __device__ void stage_wave(const BatchDev &d)
     const int nch = d.ch[d.ninst];
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
-        const DevParams &p = d.prm[i];
-        const PF f = pf_of(p);
-        const int n = p.n;
-        const double *U = d.U + 8 * d.off[i];
+        const int i = chunk_range(d, t, c0, c1);
+        const FFP &f = d.ffp[i];
+        const size_t n = (size_t)d.prm[i].n;
+        const float2 *U = d.U + 8 * d.off[i];
         float m = 0.f;
         unsigned st = 0;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            double q[NQ];
+            ff q[NQ];
 #pragma unroll
-            for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
-            st |= check_state(p, q);
-            double a2 = q[7], a1 = 1.0 - a2;
-            float p1 = (float)sg_p<true>(p, 0, q[4], a1), p2 = (float)sg_p<true>(p, 1, q[5], a2);
-            float rho = (float)(q[0] + q[1]);
-            float cs = sqrtf(((float)a1 * f.g[0] * (p1 + f.pinf[0]) + (float)a2 * f.g[1] * (p2 + f.pinf[1])) / rho);
-            float sx = (fabsf((float)q[2] / rho) + cs) * (float)p.idx;
-            float sy = (fabsf((float)q[3] / rho) + cs) * (float)p.idy;
+            for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * n + c);
+            st |= ff_check(f, q);
+            const ff a1 = ff_sub(ff_one(), q[7]);
+            const float p1 = ff_phase_p(f, 0, q[4], a1), p2 = ff_phase_p(f, 1, q[5], q[7]);
+            const float rho = ff_f(q[0]) + ff_f(q[1]);
+            const float cs = ff_sound(f, ff_f(a1), ff_f(q[7]), p1, p2, rho);
+            const float sx = (fabsf(__fdividef(ff_f(q[2]), rho)) + cs) * f.idx;
+            const float sy = (fabsf(__fdividef(ff_f(q[3]), rho)) + cs) * f.idy;
             m = fmaxf(m, fmaxf(sx, sy));
             if (isnan(sx) || isnan(sy)) st |= DIM_ST_NAN;
         }
-        block_max_to(&d.sc[i].smax, (double)m);
+        block_max_to_f(&d.sc[i].smax, m);
         flag(&d.sc[i], st);
     }
 }
 
+// the time step of every instance, once per step
+__device__ void stage_dt(const BatchDev &d)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ninst; i += gridDim.x * blockDim.x)
+        d.dtf[i] = (float)(d.prm[i].cfl / read_acc(&d.sc[i].smax));
+}
+
 template <int AXIS, int TN, int TL>
-__device__ void stage_sweep(const BatchDev &d, const double *Uin_all, double *Uout_all, double *smem)
+__device__ void stage_sweep(const BatchDev &d, const float2 *Uin_all, float2 *Uout_all, void *smem)
 {
     const int *pre = AXIS == 0 ? d.tx : d.ty;
     const int nt = pre[d.ninst];
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        int i = find_inst(pre, d.ninst, t);
+        const int i = find_inst(pre, d.ninst, t);
         const DevParams &p = d.prm[i];
-        int k = t - pre[i];
-        int len = AXIS == 0 ? p.nx : p.ny;
-        int nal = (len + TN - 1) / TN;  // tiles along the sweep axis
-        int kl = k / nal, ka = k - kl * nal;
-        double dt = p.cfl / read_acc(&d.sc[i].smax);
-        sweep32_tile<AXIS, TN, TL>(p, Uin_all + 8 * d.off[i], Uout_all + 8 * d.off[i], dt, &d.sc[i], 1, 0, ka * TN,
-                                   kl * TL, smem);
+        const FFP &f = d.ffp[i];
+        const int k = t - pre[i];
+        const int len = AXIS == 0 ? p.nx : p.ny;
+        const int nal = (len + TN - 1) / TN;  // tiles along the sweep axis
+        const int kl = k / nal, ka = k - kl * nal;
+        const float dtdx = d.dtf[i] * (AXIS == 0 ? f.idx : f.idy);
+        sweepff_tile<AXIS, TN, TL>(p, f, Uin_all + 8 * d.off[i], Uout_all + 8 * d.off[i], dtdx, &d.sc[i], 1, 0,
+                                   ka * TN, kl * TL, smem);
     }
 }
 
-// per-instance Chebyshev parameters of solve `slot` and the largest sweep count
+// per-instance Chebyshev parameters of solve `slot` (FP64 from the root table,
+// then tau b_m and 1/(1 + tau b_m) in FP32) and the largest sweep count
 __device__ void stage_schedule(const BatchDev &d, int slot, int lam_slot, bool viscous)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const int per = 2 * PMAX;
     for (int e = tid; e < d.ninst * per; e += nth) {
-        int i = e / per, s = e - i * per;
+        const int i = e / per, s = e - i * per;
         const DevParams &p = d.prm[i];
-        double tau = p.cfl / read_acc(&d.sc[i].smax);
-        double lam = read_acc(&d.sc[i].lam[lam_slot]);
+        const double tau = p.cfl / read_acc(&d.sc[i].smax);
+        const double lam = read_acc(&d.sc[i].lam[lam_slot]);
         unsigned capped;
-        int P = viscous ? cheb_P_visc(p, tau, lam, capped) : cheb_P(p, tau, lam, capped);
+        const int P = viscous ? cheb_P_visc(p, tau, lam, capped) : cheb_P(p, tau, lam, capped);
         if (s == 0) {
             d.Pi[slot * d.ninst + i] = P;
             atomicMax(&d.g->P[slot], 2 * P - 2);
@@ -132,66 +148,61 @@ __device__ void stage_schedule(const BatchDev &d, int slot, int lam_slot, bool v
         }
         if (s < 2 * P - 1) {
             const double *beta = p.beta + (P - 1) * PMAX;
-            int m = s < P - 1 ? P - s : 2 * P - 1 - s;
-            d.bs[((size_t)slot * d.ninst + i) * per + s] = lam * (beta[0] - beta[m - 1]) / (1.0 + beta[0]);
+            const int m = s < P - 1 ? P - s : 2 * P - 1 - s;
+            const double b = lam * (beta[0] - beta[m - 1]) / (1.0 + beta[0]);
+            const size_t o = ((size_t)slot * d.ninst + i) * per + s;
+            d.bs[o] = b;
+            d.tbf[o] = (float)(tau * b);
+            d.rdf[o] = (float)(1.0 / (1.0 + tau * b));
         }
     }
 }
 
-// viscous step along AXIS for all instances (Sec. 3.2), FP32 bulk
+// viscous step along AXIS for all instances (Sec. 3.2), FP32 bulk; scratch per
+// instance (FP32 planes): V, a1, a2, u0, w0, ua, ub, wa, wb
 template <int AXIS>
 __device__ bool stage_visc(const BatchDev &d, int relax)
 {
     constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
     constexpr int SLOT = AXIS, LAM = AXIS == 0 ? LAM_VX : LAM_VY;
     const int nch = d.ch[d.ninst];
-    // scratch per instance: plane 0 (FP64) alpha snapshot, then FP32 planes V, u0, w0, ua, ub, wa, wb
-    auto scr = [&](int i, double *&A2, float *&F) {
-        size_t n = (size_t)d.prm[i].n;
-        A2 = d.S + 8 * d.off[i];
-        F = (float *)(A2 + n);
-    };
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
-        const DevParams &p = d.prm[i];
-        int n = p.n;
-        double *U = d.U + 8 * d.off[i];
-        double *A2;
-        float *F;
-        scr(i, A2, F);
+        const int i = chunk_range(d, t, c0, c1);
+        const size_t n = (size_t)d.prm[i].n;
+        const float2 *U = d.U + 8 * d.off[i];
+        float *F = scr_f(d, i);
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            float rho = (float)(U[c] + U[n + c]);
-            F[c] = 1.f / rho;
-            A2[c] = U[7 * n + c];
-            F[n + c] = (float)U[QN * n + c] / rho;
-            F[2 * n + c] = (float)U[QT * n + c] / rho;
+            const float rho = ff_f(ld_ff(U, c)) + ff_f(ld_ff(U, n + c));
+            const ff a2 = ld_ff(U, 7 * n + c);
+            F[c] = __fdividef(1.f, rho);
+            F[n + c] = ff_f(ff_sub(ff_one(), a2));
+            F[2 * n + c] = ff_f(a2);
+            F[3 * n + c] = __fdividef(ff_f(ld_ff(U, QN * n + c)), rho);
+            F[4 * n + c] = __fdividef(ff_f(ld_ff(U, QT * n + c)), rho);
         }
     }
     if (!grid_barrier(d.g)) return false;
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
+        const int i = chunk_range(d, t, c0, c1);
         const DevParams &p = d.prm[i];
-        double *A2;
-        float *F;
-        scr(i, A2, F);
-        const float ih2 = (float)(AXIS == 0 ? p.idx2 : p.idy2);
-        const float mu0 = (float)p.mu[0], mu1 = (float)p.mu[1];
+        const FFP &f = d.ffp[i];
+        const size_t n = (size_t)p.n;
+        const float *F = scr_f(d, i);
+        const float ih2 = AXIS == 0 ? f.idx2 : f.idy2;
+        const float mu0 = f.mu[0], mu1 = f.mu[1];
+        auto mu_of = [&](int cc) { return F[n + cc] * mu0 + F[2 * n + cc] * mu1; };
         float lm = 0.f;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            Nb nb = neighbours(p, c);
-            int cm = AXIS == 0 ? nb.xm : nb.ym, cp = AXIS == 0 ? nb.xp : nb.yp;
-            auto mu_of = [&](int cc) {
-                float a = (float)A2[cc];
-                return (1.f - a) * mu0 + a * mu1;
-            };
-            float lc = 4.f / 3.f * mu_of(c);
-            float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_of(cm) + lc) : 0.f;
-            float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_of(cp)) : 0.f;
+            const Nb nb = neighbours(p, c);
+            const int cm = AXIS == 0 ? nb.xm : nb.ym, cp = AXIS == 0 ? nb.xp : nb.yp;
+            const float lc = 4.f / 3.f * mu_of(c);
+            const float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_of(cm) + lc) : 0.f;
+            const float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_of(cp)) : 0.f;
             lm = fmaxf(lm, 2.f * F[c] * ((fl + fr) * ih2));
         }
-        block_max_to(&d.sc[i].lam[LAM], (double)lm);
+        block_max_to_f(&d.sc[i].lam[LAM], lm);
     }
     if (!grid_barrier(d.g)) return false;
     stage_schedule(d, SLOT, LAM, true);
@@ -200,160 +211,149 @@ __device__ bool stage_visc(const BatchDev &d, int relax)
     for (int m = 1; m <= M; m++) {
         for (int t = blockIdx.x; t < nch; t += gridDim.x) {
             int c0, c1;
-            int i = chunk_range(d, t, c0, c1);
-            int P = d.Pi[SLOT * d.ninst + i];
+            const int i = chunk_range(d, t, c0, c1);
+            const int P = d.Pi[SLOT * d.ninst + i];
             if (m > 2 * P - 2) continue;
             const DevParams &p = d.prm[i];
-            int n = p.n;
-            double *A2;
-            float *F;
-            scr(i, A2, F);
-            float *V = F, *u0 = F + n, *w0 = F + 2 * (size_t)n;
-            const float *uin = m == 1 ? u0 : (((m - 1) & 1) ? F + 3 * (size_t)n : F + 4 * (size_t)n);
-            const float *win = m == 1 ? w0 : (((m - 1) & 1) ? F + 5 * (size_t)n : F + 6 * (size_t)n);
-            float *uo = (m & 1) ? F + 3 * (size_t)n : F + 4 * (size_t)n;
-            float *wo = (m & 1) ? F + 5 * (size_t)n : F + 6 * (size_t)n;
-            const double tau = p.cfl / read_acc(&d.sc[i].smax);
-            const double b = d.bs[((size_t)SLOT * d.ninst + i) * 2 * PMAX + (m - 1)];
-            const float tb = (float)(tau * b), rden = (float)(1.0 / (1.0 + tau * b)), tauf = (float)tau;
-            const float ih2 = (float)(AXIS == 0 ? p.idx2 : p.idy2);
-            const float mu0 = (float)p.mu[0], mu1 = (float)p.mu[1];
+            const FFP &f = d.ffp[i];
+            const size_t n = (size_t)p.n;
+            float *F = scr_f(d, i);
+            const float *V = F, *a1 = F + n, *a2 = F + 2 * n, *u0 = F + 3 * n, *w0 = F + 4 * n;
+            const float *uin = m == 1 ? u0 : (((m - 1) & 1) ? F + 5 * n : F + 6 * n);
+            const float *win = m == 1 ? w0 : (((m - 1) & 1) ? F + 7 * n : F + 8 * n);
+            float *uo = (m & 1) ? F + 5 * n : F + 6 * n;
+            float *wo = (m & 1) ? F + 7 * n : F + 8 * n;
+            const size_t o = ((size_t)SLOT * d.ninst + i) * 2 * PMAX + (m - 1);
+            const float tb = d.tbf[o], rd = d.rdf[o], tauf = d.dtf[i];
+            const float ih2 = AXIS == 0 ? f.idx2 : f.idy2;
+            const float mu0 = f.mu[0], mu1 = f.mu[1];
+            auto mu_of = [&](int cc) { return a1[cc] * mu0 + a2[cc] * mu1; };
             for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-                Nb nb = neighbours(p, c);
-                int cm = AXIS == 0 ? nb.xm : nb.ym, cp = AXIS == 0 ? nb.xp : nb.yp;
-                auto mu_of = [&](int cc) {
-                    float a = (float)A2[cc];
-                    return (1.f - a) * mu0 + a * mu1;
-                };
-                float mc = mu_of(c);
-                float mm = cm >= 0 ? 0.5f * (mu_of(cm) + mc) : 0.f;
-                float mp = cp >= 0 ? 0.5f * (mc + mu_of(cp)) : 0.f;
-                float uc = uin[c], wc = win[c];
-                float Lu = (cp >= 0 ? 4.f / 3.f * mp * (uin[cp] - uc) * ih2 : 0.f) -
-                           (cm >= 0 ? 4.f / 3.f * mm * (uc - uin[cm]) * ih2 : 0.f);
-                float Lw = (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.f) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.f);
-                uo[c] = (u0[c] + tb * uc + tauf * V[c] * Lu) * rden;
-                wo[c] = (w0[c] + tb * wc + tauf * V[c] * Lw) * rden;
+                const Nb nb = neighbours(p, c);
+                const int cm = AXIS == 0 ? nb.xm : nb.ym, cp = AXIS == 0 ? nb.xp : nb.yp;
+                const float mc = mu_of(c);
+                const float mm = cm >= 0 ? 0.5f * (mu_of(cm) + mc) : 0.f;
+                const float mp = cp >= 0 ? 0.5f * (mc + mu_of(cp)) : 0.f;
+                const float uc = uin[c], wc = win[c];
+                const float Lu = (cp >= 0 ? 4.f / 3.f * mp * (uin[cp] - uc) * ih2 : 0.f) -
+                                 (cm >= 0 ? 4.f / 3.f * mm * (uc - uin[cm]) * ih2 : 0.f);
+                const float Lw =
+                    (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.f) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.f);
+                uo[c] = (u0[c] + tb * uc + tauf * V[c] * Lu) * rd;
+                wo[c] = (w0[c] + tb * wc + tauf * V[c] * Lw) * rd;
             }
         }
         if (!grid_barrier(d.g)) return false;
     }
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
+        const int i = chunk_range(d, t, c0, c1);
         const DevParams &p = d.prm[i];
-        int n = p.n;
-        int P = d.Pi[SLOT * d.ninst + i];
-        double *U = d.U + 8 * d.off[i];
-        double *A2;
-        float *F;
-        scr(i, A2, F);
-        int last = 2 * P - 2;
-        const float *uin = last == 0 ? F + n : ((last & 1) ? F + 3 * (size_t)n : F + 4 * (size_t)n);
-        const float *win = last == 0 ? F + 2 * (size_t)n : ((last & 1) ? F + 5 * (size_t)n : F + 6 * (size_t)n);
-        const double tau = p.cfl / read_acc(&d.sc[i].smax);
-        const double ih = AXIS == 0 ? p.idx : p.idy;
-        const float ihf = (float)ih;
-        const float mu0 = (float)p.mu[0], mu1 = (float)p.mu[1];
+        const FFP &f = d.ffp[i];
+        const size_t n = (size_t)p.n;
+        const int P = d.Pi[SLOT * d.ninst + i];
+        float2 *U = d.U + 8 * d.off[i];
+        const float *F = scr_f(d, i);
+        const float *a1 = F + n, *a2 = F + 2 * n;
+        const int last = 2 * P - 2;
+        const float *uin = last == 0 ? F + 3 * n : ((last & 1) ? F + 5 * n : F + 6 * n);
+        const float *win = last == 0 ? F + 4 * n : ((last & 1) ? F + 7 * n : F + 8 * n);
+        const float ih = AXIS == 0 ? f.idx : f.idy;
+        const float ti = d.dtf[i] * ih;
+        const float mu0 = f.mu[0], mu1 = f.mu[1];
+        auto mu_of = [&](int cc) { return a1[cc] * mu0 + a2[cc] * mu1; };
         unsigned st = 0;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            Nb nb = neighbours(p, c);
-            int cm = AXIS == 0 ? nb.xm : nb.ym, cp = AXIS == 0 ? nb.xp : nb.yp;
-            auto mu_of = [&](int cc) {
-                float a = (float)A2[cc];
-                return (1.f - a) * mu0 + a * mu1;
-            };
-            float mc = mu_of(c);
-            float Fn[2], Ft[2], W[2];
-            double aF1[2], aF2[2];
+            const Nb nb = neighbours(p, c);
+            const int cm = AXIS == 0 ? nb.xm : nb.ym, cp = AXIS == 0 ? nb.xp : nb.yp;
+            const float mc = mu_of(c);
+            float Fn[2], Ft[2], W[2], aF1[2], aF2[2];
+#pragma unroll
             for (int sd = 0; sd < 2; sd++) {
-                int cl = sd == 0 ? cm : c, cr = sd == 0 ? c : cp;
+                const int cl = sd == 0 ? cm : c, cr = sd == 0 ? c : cp;
                 if ((sd == 0 ? cm : cp) < 0) {
-                    Fn[sd] = Ft[sd] = W[sd] = 0.f;
-                    aF1[sd] = aF2[sd] = 0.0;
+                    Fn[sd] = Ft[sd] = W[sd] = aF1[sd] = aF2[sd] = 0.f;
                     continue;
                 }
-                float ml = sd == 0 ? mu_of(cm) : mc, mr = sd == 0 ? mc : mu_of(cp);
-                float lmf = 0.5f * (ml + mr);
-                Fn[sd] = 4.f / 3.f * lmf * (uin[cr] - uin[cl]) * ihf;
-                Ft[sd] = lmf * (win[cr] - win[cl]) * ihf;
+                const float lmf = 0.5f * ((sd == 0 ? mu_of(cm) : mc) + (sd == 0 ? mc : mu_of(cp)));
+                Fn[sd] = 4.f / 3.f * lmf * (uin[cr] - uin[cl]) * ih;
+                Ft[sd] = lmf * (win[cr] - win[cl]) * ih;
                 W[sd] = 0.5f * (uin[cl] + uin[cr]) * Fn[sd] + 0.5f * (win[cl] + win[cr]) * Ft[sd];
-                double a2l = A2[cl], a2r = A2[cr];
-                aF2[sd] = 0.5 * (a2l + a2r);
-                aF1[sd] = 0.5 * ((1.0 - a2l) + (1.0 - a2r));
+                aF1[sd] = 0.5f * (a1[cl] + a1[cr]);
+                aF2[sd] = 0.5f * (a2[cl] + a2[cr]);
             }
-            double uh = uin[c], wh = win[c];
-            double q[NQ];
+            const float uh = uin[c], wh = win[c];
+            ff q[NQ];
 #pragma unroll
-            for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
-            q[QN] += tau * (double)(Fn[1] - Fn[0]) * ih;
-            q[QT] += tau * (double)(Ft[1] - Ft[0]) * ih;
-            q[6] += tau * (double)(W[1] - W[0]) * ih;
-            q[4] += tau * (aF1[1] * W[1] - aF1[0] * W[0]) * ih -
-                    tau * (uh * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + wh * (aF1[1] * Ft[1] - aF1[0] * Ft[0])) * ih;
-            q[5] += tau * (aF2[1] * W[1] - aF2[0] * W[0]) * ih -
-                    tau * (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0])) * ih;
+            for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * n + c);
+            q[QN] = ff_add_f(q[QN], ti * (Fn[1] - Fn[0]));
+            q[QT] = ff_add_f(q[QT], ti * (Ft[1] - Ft[0]));
+            q[6] = ff_add_f(q[6], ti * (W[1] - W[0]));
+            q[4] = ff_add_f(q[4], ti * ((aF1[1] * W[1] - aF1[0] * W[0]) - (uh * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) +
+                                                                        wh * (aF1[1] * Ft[1] - aF1[0] * Ft[0]))));
+            q[5] = ff_add_f(q[5], ti * ((aF2[1] * W[1] - aF2[0] * W[0]) - (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) +
+                                                                        wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0]))));
             if (relax) {
-                unsigned r = prelax<true>(p, q);
+                const unsigned r = ff_prelax(f, q);
                 if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
                 st |= r & DIM_ST_NAN;
             }
-            U[QN * n + c] = q[QN];
-            U[QT * n + c] = q[QT];
-            U[4 * n + c] = q[4];
-            U[5 * n + c] = q[5];
-            U[6 * n + c] = q[6];
-            U[7 * n + c] = q[7];
+#pragma unroll
+            for (int k = 2; k < NQ; k++) st_ff(U, k * n + c, q[k]);
         }
         flag(&d.sc[i], st);
     }
     return grid_barrier(d.g);
 }
 
-// temperature relaxation + heat conduction for all instances (Sec. 3.4), FP32 bulk
+// temperature relaxation + heat conduction for all instances (Sec. 3.4), FP32
+// bulk, one Algorithm-1 iteration; scratch per instance (FP32 planes): T0, V,
+// L, va, vb, Ia
 __device__ bool stage_heat(const BatchDev &d)
 {
     constexpr int SLOT = 2;
     const int nch = d.ch[d.ninst];
-    // scratch per instance: plane 0 (FP64, unused here), FP32 planes T0, V, L, va, vb, Ia
-    auto scr = [&](int i) { return (float *)(d.S + 8 * d.off[i] + d.prm[i].n); };
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
-        const DevParams &p = d.prm[i];
-        int n = p.n;
-        double *U = d.U + 8 * d.off[i];
-        float *F = scr(i);
+        const int i = chunk_range(d, t, c0, c1);
+        const FFP &f = d.ffp[i];
+        const size_t n = (size_t)d.prm[i].n;
+        float2 *U = d.U + 8 * d.off[i];
+        float *F = scr_f(d, i);
         unsigned st = 0;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            double m1 = U[c], m2 = U[n + c], T, a2;
-            unsigned r = equilibrium<true>(p, m1, m2, U[4 * n + c] + U[5 * n + c], T, a2);
+            const ff M1 = ld_ff(U, c), M2 = ld_ff(U, n + c);
+            const float m1 = ff_f(M1), m2 = ff_f(M2);
+            ff E1 = ld_ff(U, 4 * n + c), E2 = ld_ff(U, 5 * n + c);
+            float T;
+            ff a2;
+            const unsigned r = ff_equilibrium(f, M1, M2, ff_add(E1, E2), T, a2, E1, E2);
             if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
             st |= r & DIM_ST_NAN;
-            U[4 * n + c] = m1 * p.cv[0] * T + (1.0 - a2) * p.pinf[0];
-            U[5 * n + c] = m2 * p.cv[1] * T + a2 * p.pinf[1];
-            U[7 * n + c] = a2;
-            F[c] = (float)T;
+            st_ff(U, 4 * n + c, E1);
+            st_ff(U, 5 * n + c, E2);
+            st_ff(U, 7 * n + c, a2);
+            F[c] = T;
             float V, L;
-            heat_coeffs_f(p, m1, m2, T, a2, V, L);
+            ff_heat_coeffs(f, m1, m2, T, a2, V, L);
             F[n + c] = V;
             F[2 * n + c] = L;
-            F[5 * (size_t)n + c] = (float)((1.0 - a2) * p.src[0] + a2 * p.src[1]);
+            F[5 * n + c] = ff_f(ff_sub(ff_one(), a2)) * f.src[0] + ff_f(a2) * f.src[1];
         }
         flag(&d.sc[i], st);
     }
     if (!grid_barrier(d.g)) return false;
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
+        const int i = chunk_range(d, t, c0, c1);
         const DevParams &p = d.prm[i];
-        int n = p.n;
-        float *F = scr(i);
-        const float idx2 = (float)p.idx2, idy2 = (float)p.idy2;
+        const FFP &f = d.ffp[i];
+        const size_t n = (size_t)p.n;
+        const float *F = scr_f(d, i);
         float lm = 0.f;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x)
-            lm = fmaxf(lm, gershf(p, neighbours(p, c), c, F + n, F + 2 * (size_t)n, idx2, idy2));
-        block_max_to(&d.sc[i].lam[0], (double)lm);
+            lm = fmaxf(lm, gershf(p, neighbours(p, c), c, F + n, F + 2 * n, f.idx2, f.idy2));
+        block_max_to_f(&d.sc[i].lam[0], lm);
     }
     if (!grid_barrier(d.g)) return false;
     stage_schedule(d, SLOT, 0, false);
@@ -362,60 +362,54 @@ __device__ bool stage_heat(const BatchDev &d)
     for (int m = 1; m <= M; m++) {
         for (int t = blockIdx.x; t < nch; t += gridDim.x) {
             int c0, c1;
-            int i = chunk_range(d, t, c0, c1);
-            int P = d.Pi[SLOT * d.ninst + i];
+            const int i = chunk_range(d, t, c0, c1);
+            const int P = d.Pi[SLOT * d.ninst + i];
             if (m > 2 * P - 2) continue;
             const DevParams &p = d.prm[i];
-            int n = p.n;
-            float *F = scr(i);
-            const float *T0 = F, *V = F + n, *L = F + 2 * (size_t)n;
-            const float *vin = m == 1 ? T0 : (((m - 1) & 1) ? F + 3 * (size_t)n : F + 4 * (size_t)n);
-            float *vout = (m & 1) ? F + 3 * (size_t)n : F + 4 * (size_t)n;
-            const double tau = p.cfl / read_acc(&d.sc[i].smax);
-            const double b = d.bs[((size_t)SLOT * d.ninst + i) * 2 * PMAX + (m - 1)];
-            const float tb = (float)(tau * b), rden = (float)(1.0 / (1.0 + tau * b)), tauf = (float)tau;
-            const float idx2 = (float)p.idx2, idy2 = (float)p.idy2;
-            const float *Ia = F + 5 * (size_t)n;
+            const FFP &f = d.ffp[i];
+            const size_t n = (size_t)p.n;
+            float *F = scr_f(d, i);
+            const float *T0 = F, *V = F + n, *L = F + 2 * n, *Ia = F + 5 * n;
+            const float *vin = m == 1 ? T0 : (((m - 1) & 1) ? F + 3 * n : F + 4 * n);
+            float *vout = (m & 1) ? F + 3 * n : F + 4 * n;
+            const size_t o = ((size_t)SLOT * d.ninst + i) * 2 * PMAX + (m - 1);
+            const float tb = d.tbf[o], rd = d.rdf[o], tauf = d.dtf[i];
             for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-                float Lv = lapf(p, neighbours(p, c), c, vin, L, idx2, idy2);
-                vout[c] = (T0[c] + tb * vin[c] + tauf * V[c] * (Lv + Ia[c])) * rden;
+                const float Lv = lapf(p, neighbours(p, c), c, vin, L, f.idx2, f.idy2);
+                vout[c] = (T0[c] + tb * vin[c] + tauf * V[c] * (Lv + Ia[c])) * rd;
             }
         }
         if (!grid_barrier(d.g)) return false;
     }
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
+        const int i = chunk_range(d, t, c0, c1);
         const DevParams &p = d.prm[i];
-        int n = p.n;
-        int P = d.Pi[SLOT * d.ninst + i];
-        double *U = d.U + 8 * d.off[i];
-        float *F = scr(i);
-        int last = 2 * P - 2;
-        const float *vin = last == 0 ? F : ((last & 1) ? F + 3 * (size_t)n : F + 4 * (size_t)n);
-        const float *L = F + 2 * (size_t)n;
-        const double tau = p.cfl / read_acc(&d.sc[i].smax);
-        const float idx2 = (float)p.idx2, idy2 = (float)p.idy2;
+        const FFP &f = d.ffp[i];
+        const size_t n = (size_t)p.n;
+        const int P = d.Pi[SLOT * d.ninst + i];
+        float2 *U = d.U + 8 * d.off[i];
+        const float *F = scr_f(d, i);
+        const int last = 2 * P - 2;
+        const float *vin = last == 0 ? F : ((last & 1) ? F + 3 * n : F + 4 * n);
+        const float *L = F + 2 * n;
+        const float tauf = d.dtf[i];
         unsigned st = 0;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            double q = (double)lapf(p, neighbours(p, c), c, vin, L, idx2, idy2) + (double)F[5 * (size_t)n + c];
-            double m1 = U[c], m2 = U[n + c];
-            double T, a2;
-            unsigned r = equilibrium<true>(p, m1, m2, U[4 * n + c] + U[5 * n + c] + tau * q, T, a2);
-            double Q[NQ];
-            Q[0] = m1;
-            Q[1] = m2;
-            Q[2] = U[2 * n + c];
-            Q[3] = U[3 * n + c];
-            Q[4] = m1 * p.cv[0] * T + (1.0 - a2) * p.pinf[0];
-            Q[5] = m2 * p.cv[1] * T + a2 * p.pinf[1];
-            Q[6] = U[6 * n + c] + tau * q;
-            Q[7] = a2;
-            U[4 * n + c] = Q[4];
-            U[5 * n + c] = Q[5];
-            U[6 * n + c] = Q[6];
-            U[7 * n + c] = Q[7];
-            st |= check_state(p, Q) | (r & DIM_ST_NAN);
+            const float dq = tauf * (lapf(p, neighbours(p, c), c, vin, L, f.idx2, f.idy2) + F[5 * n + c]);
+            ff q[NQ];
+            q[0] = ld_ff(U, c);
+            q[1] = ld_ff(U, n + c);
+            q[2] = q[3] = ff_of(0.f);
+            float T;
+            const unsigned r = ff_equilibrium(f, q[0], q[1], ff_add_f(ff_add(ld_ff(U, 4 * n + c), ld_ff(U, 5 * n + c)), dq),
+                                              T, q[7], q[4], q[5]);
+            q[6] = ff_add_f(ld_ff(U, 6 * n + c), dq);
+            st_ff(U, 4 * n + c, q[4]);
+            st_ff(U, 5 * n + c, q[5]);
+            st_ff(U, 6 * n + c, q[6]);
+            st_ff(U, 7 * n + c, q[7]);
+            st |= ff_check(f, q) | (r & DIM_ST_NAN);
         }
         flag(&d.sc[i], st);
     }
@@ -428,24 +422,21 @@ __device__ void stage_trelax(const BatchDev &d)
     const int nch = d.ch[d.ninst];
     for (int t = blockIdx.x; t < nch; t += gridDim.x) {
         int c0, c1;
-        int i = chunk_range(d, t, c0, c1);
-        const DevParams &p = d.prm[i];
-        int n = p.n;
-        double *U = d.U + 8 * d.off[i];
+        const int i = chunk_range(d, t, c0, c1);
+        const FFP &f = d.ffp[i];
+        const size_t n = (size_t)d.prm[i].n;
+        float2 *U = d.U + 8 * d.off[i];
         unsigned st = 0;
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            double q[NQ];
+            ff q[NQ];
 #pragma unroll
-            for (int k = 0; k < NQ; k++) q[k] = U[k * n + c];
-            double T, a;
-            unsigned r = equilibrium<true>(p, q[0], q[1], q[4] + q[5], T, a);
-            q[4] = q[0] * p.cv[0] * T + (1.0 - a) * p.pinf[0];
-            q[5] = q[1] * p.cv[1] * T + a * p.pinf[1];
-            q[7] = a;
-            U[4 * n + c] = q[4];
-            U[5 * n + c] = q[5];
-            U[7 * n + c] = q[7];
-            st |= check_state(p, q) | (r & DIM_ST_NAN);
+            for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * n + c);
+            float T;
+            const unsigned r = ff_equilibrium(f, q[0], q[1], ff_add(q[4], q[5]), T, q[7], q[4], q[5]);
+            st_ff(U, 4 * n + c, q[4]);
+            st_ff(U, 5 * n + c, q[5]);
+            st_ff(U, 7 * n + c, q[7]);
+            st |= ff_check(f, q) | (r & DIM_ST_NAN);
         }
         flag(&d.sc[i], st);
     }
@@ -454,7 +445,7 @@ __device__ void stage_trelax(const BatchDev &d)
 template <int TNX, int TLX, int TNY, int TLY>
 __global__ void __launch_bounds__(256) k_batch_step(BatchDev d)
 {
-    extern __shared__ double smem[];
+    extern __shared__ float4 smem_b[];
     // per-instance accumulators of this step
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ninst; i += gridDim.x * blockDim.x) {
         d.sc[i].smax = 0ull;
@@ -466,9 +457,11 @@ __global__ void __launch_bounds__(256) k_batch_step(BatchDev d)
     if (!grid_barrier(d.g)) return;
     stage_wave(d);
     if (!grid_barrier(d.g)) return;
-    stage_sweep<0, TNX, TLX>(d, d.U, d.U2, smem);
+    stage_dt(d);
     if (!grid_barrier(d.g)) return;
-    stage_sweep<1, TNY, TLY>(d, d.U2, d.U, smem);
+    stage_sweep<0, TNX, TLX>(d, d.U, d.U2, smem_b);
+    if (!grid_barrier(d.g)) return;
+    stage_sweep<1, TNY, TLY>(d, d.U2, d.U, smem_b);
     if (!grid_barrier(d.g)) return;
     if (d.viscous) {
         if (!stage_visc<0>(d, 0)) return;
@@ -492,7 +485,7 @@ struct Variant {
 
 #define DIM_BATCH_VARIANT(a, b, c, e)                                                          \
     Variant{(const void *)k_batch_step<a, b, c, e>, a, b, c, e,                                \
-            sweep32_smem(a, b) > sweep32_smem(c, e) ? sweep32_smem(a, b) : sweep32_smem(c, e)}
+            sweepff_smem(a, b) > sweepff_smem(c, e) ? sweepff_smem(a, b) : sweepff_smem(c, e)}
 
 static const Variant kVariants[] = {
     DIM_BATCH_VARIANT(256, 1, 32, 8),
@@ -555,6 +548,9 @@ void batch_tiles(int v, int nx, int ny, int *tiles_x, int *tiles_y)
 int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, dimk::DevParams *out);
 namespace dimk {
 cudaError_t launch_from_primitive(const DevParams &p, const double *prim, double *U, Scalars *sc, cudaStream_t s);
+FFP ffp_of(const DevParams &p);
+cudaError_t launch_ff_in(const double *U, float2 *F, size_t m, cudaStream_t s);
+cudaError_t launch_ff_out(const float2 *F, double *U, size_t m, cudaStream_t s);
 }
 
 using dimk::DevParams;
@@ -571,17 +567,19 @@ struct dim_batch {
     long long *off_h;
     // device tables
     DevParams *prm;
+    dimk::FFP *ffp;
     long long *off;
     int *ch;
     int *tx[dimk::kNumVariants], *ty[dimk::kNumVariants];
     Scalars *sc, *g;
-    double *bs, *U2, *S, *beta;
+    double *bs, *S, *beta;
+    float *tbf, *rdf, *dtf;
+    float2 *Uf, *Uf2;  // float-float state planes (packed) while steps run
     int *Pi;
     int viscous, heat, trelax;
     int nsm, maxb[dimk::kNumVariants];
     int variant, blocks;
     cudaGraphExec_t gexec;
-    double *gU;
     int gvariant, gblocks;
 };
 
@@ -590,6 +588,7 @@ static void batch_free(dim_batch *b)
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     cudaFree(b->prm);
+    cudaFree(b->ffp);
     cudaFree(b->off);
     cudaFree(b->ch);
     for (int v = 0; v < dimk::kNumVariants; v++) {
@@ -599,7 +598,11 @@ static void batch_free(dim_batch *b)
     cudaFree(b->sc);
     cudaFree(b->g);
     cudaFree(b->bs);
-    cudaFree(b->U2);
+    cudaFree(b->tbf);
+    cudaFree(b->rdf);
+    cudaFree(b->dtf);
+    cudaFree(b->Uf);
+    cudaFree(b->Uf2);
     cudaFree(b->S);
     cudaFree(b->beta);
     cudaFree(b->Pi);
@@ -611,10 +614,11 @@ static void batch_free(dim_batch *b)
     free(b);
 }
 
-static dimk::BatchDev batch_dev(const dim_batch *b, double *U)
+static dimk::BatchDev batch_dev(const dim_batch *b)
 {
     dimk::BatchDev d;
     d.prm = b->prm;
+    d.ffp = b->ffp;
     d.off = b->off;
     d.tx = b->tx[b->variant];
     d.ty = b->ty[b->variant];
@@ -622,9 +626,12 @@ static dimk::BatchDev batch_dev(const dim_batch *b, double *U)
     d.sc = b->sc;
     d.g = b->g;
     d.bs = b->bs;
+    d.tbf = b->tbf;
+    d.rdf = b->rdf;
+    d.dtf = b->dtf;
     d.Pi = b->Pi;
-    d.U = U;
-    d.U2 = b->U2;
+    d.U = b->Uf;
+    d.U2 = b->Uf2;
     d.S = b->S;
     d.ninst = b->ninst;
     d.viscous = b->viscous;
@@ -633,12 +640,12 @@ static dimk::BatchDev batch_dev(const dim_batch *b, double *U)
     return d;
 }
 
-// one step on the internal stream (no graph)
-static cudaError_t batch_step_direct(dim_batch *b, double *U, cudaStream_t s)
+// one step of the FF state on the internal stream (no graph)
+static cudaError_t batch_step_direct(dim_batch *b, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(b->g, 0, offsetof(Scalars, status), s);
     if (e != cudaSuccess) return e;
-    return dimk::batch_launch(b->variant, b->blocks, batch_dev(b, U), s);
+    return dimk::batch_launch(b->variant, b->blocks, batch_dev(b), s);
 }
 
 extern "C" {
@@ -676,6 +683,7 @@ int dim_batch_init(dim_batch **out, const dim_params *hp, int ninst, const int *
     ch_h[ninst] = (int)chunks;
     b->ncell = off;
     if (r == DIM_OK && (off > (1LL << 31) / 8 || chunks > (1LL << 30))) r = DIM_EINVAL;
+    if (r == DIM_OK && hp->n_outer != 1) r = DIM_EINVAL;  // batches run one Algorithm-1 iteration
     if (r != DIM_OK) {
         free(ch_h); free(t_h); batch_free(b);
         return r;
@@ -699,6 +707,12 @@ int dim_batch_init(dim_batch **out, const dim_params *hp, int ninst, const int *
          cudaMemcpy(b->beta, tab, sizeof(double) * dimk::PMAX * dimk::PMAX, cudaMemcpyHostToDevice) == cudaSuccess;
     free(tab);
     for (int i = 0; ok && i < ninst; i++) b->prm_h[i].beta = b->beta;
+    dimk::FFP *ffp_h = (dimk::FFP *)calloc(ninst, sizeof(dimk::FFP));
+    ok = ok && ffp_h;
+    for (int i = 0; ok && i < ninst; i++) ffp_h[i] = dimk::ffp_of(b->prm_h[i]);
+    ok = ok && cudaMalloc(&b->ffp, sizeof(dimk::FFP) * ninst) == cudaSuccess &&
+         cudaMemcpy(b->ffp, ffp_h, sizeof(dimk::FFP) * ninst, cudaMemcpyHostToDevice) == cudaSuccess;
+    free(ffp_h);
     ok = ok && cudaMalloc(&b->prm, sizeof(DevParams) * ninst) == cudaSuccess &&
          cudaMemcpy(b->prm, b->prm_h, sizeof(DevParams) * ninst, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMalloc(&b->off, sizeof(long long) * (ninst + 1)) == cudaSuccess &&
@@ -730,8 +744,12 @@ int dim_batch_init(dim_batch **out, const dim_params *hp, int ninst, const int *
          cudaMemset(b->sc, 0, sizeof(Scalars) * ninst) == cudaSuccess &&
          cudaMalloc(&b->g, sizeof(Scalars)) == cudaSuccess && cudaMemset(b->g, 0, sizeof(Scalars)) == cudaSuccess &&
          cudaMalloc(&b->bs, sizeof(double) * 3 * ninst * 2 * dimk::PMAX) == cudaSuccess &&
+         cudaMalloc(&b->tbf, sizeof(float) * 3 * ninst * 2 * dimk::PMAX) == cudaSuccess &&
+         cudaMalloc(&b->rdf, sizeof(float) * 3 * ninst * 2 * dimk::PMAX) == cudaSuccess &&
+         cudaMalloc(&b->dtf, sizeof(float) * ninst) == cudaSuccess &&
          cudaMalloc(&b->Pi, sizeof(int) * 3 * ninst) == cudaSuccess &&
-         cudaMalloc(&b->U2, sizeof(double) * 8 * N) == cudaSuccess &&
+         cudaMalloc(&b->Uf, sizeof(float2) * 8 * N) == cudaSuccess &&
+         cudaMalloc(&b->Uf2, sizeof(float2) * 8 * N) == cudaSuccess &&
          cudaMalloc(&b->S, sizeof(double) * 8 * N) == cudaSuccess &&
          cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
@@ -771,20 +789,23 @@ int dim_batch_from_primitive(dim_batch *b, const double *prim, double *U)
     return DIM_OK;
 }
 
-// the caller's stream -> internal stream -> the caller's stream
+// the caller's stream -> internal stream (state to FF planes, steps, back) ->
+// the caller's stream
 static int batch_run(dim_batch *b, double *U, int nsteps, bool use_graph)
 {
+    const size_t m = 8 * (size_t)b->ncell;
     if (cudaEventRecord(b->ev_in, b->user) != cudaSuccess || cudaStreamWaitEvent(b->own, b->ev_in, 0) != cudaSuccess)
         return DIM_ECUDA;
-    if (use_graph) {
-        if (!b->gexec || b->gU != U || b->gvariant != b->variant || b->gblocks != b->blocks) {
+    if (nsteps > 0 && dimk::launch_ff_in(U, b->Uf, m, b->own) != cudaSuccess) return DIM_ECUDA;
+    if (use_graph && nsteps > 0) {
+        if (!b->gexec || b->gvariant != b->variant || b->gblocks != b->blocks) {
             if (b->gexec) {
                 cudaGraphExecDestroy(b->gexec);
                 b->gexec = nullptr;
             }
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DIM_ECUDA;
-            cudaError_t e = batch_step_direct(b, U, b->own);
+            cudaError_t e = batch_step_direct(b, b->own);
             cudaError_t e2 = cudaStreamEndCapture(b->own, &graph);
             if (e != cudaSuccess || e2 != cudaSuccess || !graph) {
                 if (graph) cudaGraphDestroy(graph);
@@ -796,7 +817,6 @@ static int batch_run(dim_batch *b, double *U, int nsteps, bool use_graph)
                 b->gexec = nullptr;
                 return DIM_ECUDA;
             }
-            b->gU = U;
             b->gvariant = b->variant;
             b->gblocks = b->blocks;
         }
@@ -804,8 +824,9 @@ static int batch_run(dim_batch *b, double *U, int nsteps, bool use_graph)
             if (cudaGraphLaunch(b->gexec, b->own) != cudaSuccess) return DIM_ECUDA;
     } else {
         for (int s = 0; s < nsteps; s++)
-            if (batch_step_direct(b, U, b->own) != cudaSuccess) return DIM_ECUDA;
+            if (batch_step_direct(b, b->own) != cudaSuccess) return DIM_ECUDA;
     }
+    if (nsteps > 0 && dimk::launch_ff_out(b->Uf, U, m, b->own) != cudaSuccess) return DIM_ECUDA;
     if (cudaEventRecord(b->ev_out, b->own) != cudaSuccess || cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess)
         return DIM_ECUDA;
     return DIM_OK;
@@ -820,25 +841,28 @@ int dim_batch_step(dim_batch *b, double *U, int nsteps)
 int dim_batch_autotune(dim_batch *b, const double *U, int *config)
 {
     if (!b || !U) return DIM_EINVAL;
-    size_t bytes = sizeof(double) * 8 * (size_t)b->ncell;
-    double *Ut = nullptr;
-    if (cudaMalloc(&Ut, bytes) != cudaSuccess) return DIM_ECUDA;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    if (cudaStreamSynchronize(b->user) != cudaSuccess) { cudaFree(Ut); return DIM_ECUDA; }
+    const size_t m = 8 * (size_t)b->ncell;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaStreamSynchronize(b->user) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return DIM_ECUDA;
+    }
     float best = 1e30f;
     int bv = 0, bb = b->maxb[0] * b->nsm;
     int rc = DIM_OK;
+    // every trial starts from the caller's state converted into the FF planes
+    // (the caller's U is only read)
     for (int v = 0; v < dimk::kNumVariants && rc == DIM_OK; v++) {
         for (int per = 1; per <= b->maxb[v] && rc == DIM_OK; per++) {
             if (per != 1 && per != b->maxb[v]) continue;
             b->variant = v;
             b->blocks = per * b->nsm;
-            if (cudaMemcpyAsync(Ut, U, bytes, cudaMemcpyDeviceToDevice, b->own) != cudaSuccess ||
-                batch_step_direct(b, Ut, b->own) != cudaSuccess || cudaEventRecord(e0, b->own) != cudaSuccess ||
-                batch_step_direct(b, Ut, b->own) != cudaSuccess || batch_step_direct(b, Ut, b->own) != cudaSuccess ||
-                cudaEventRecord(e1, b->own) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            if (dimk::launch_ff_in(U, b->Uf, m, b->own) != cudaSuccess || batch_step_direct(b, b->own) != cudaSuccess ||
+                cudaEventRecord(e0, b->own) != cudaSuccess || batch_step_direct(b, b->own) != cudaSuccess ||
+                batch_step_direct(b, b->own) != cudaSuccess || cudaEventRecord(e1, b->own) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess) {
                 rc = DIM_ECUDA;
                 break;
             }
@@ -853,7 +877,6 @@ int dim_batch_autotune(dim_batch *b, const double *U, int *config)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(Ut);
     b->variant = bv;
     b->blocks = bb;
     // the trial steps ran on a copy; their status bits are not the caller's

@@ -1,0 +1,539 @@
+// dim_bulkff.cu -- the FP32-bulk form of the split step (sm_103a): the same
+// stages and launch structure as the FP64 kernels (dim_sweep.cu,
+// dim_parabolic.cu) on a float-float copy of the state (dim_ff.cuh), with no
+// FP64 instruction inside a step:
+//   FF:   the conserved state and its accumulation; the phase pressures' E_k /
+//         a_k - cold_k; the volume fraction, its reconstruction and flux, and
+//         the cold energies it carries; the kinetic energy in the relaxations;
+//   FP32: MUSCL reconstruction of m_k, u_n, u_t, p_k; face states, sound
+//         speeds, HLLC; the relaxation roots (in the phase-pressure form of
+//         dim_ff.cuh); viscous and heat coefficients; every Chebyshev sweep.
+// The Chebyshev parameters b_m come from the FP64 root table once per block.
+#include "dim_ff.cuh"
+
+namespace dimk {
+
+// ---------------------------------------------------------------------------
+// FP64 <-> FF planes
+// ---------------------------------------------------------------------------
+__global__ void k_ff_in(const double *__restrict__ U, float2 *__restrict__ F, size_t m)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        const ff a = ff_from_d(U[i]);
+        F[i] = make_float2(a.h, a.l);
+    }
+}
+
+// may run in place (F and U the same memory): each element is read before it is written
+__global__ void k_ff_out(const float2 *F, double *U, size_t m)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = F[i];
+        U[i] = ff_to_d(ff{v.x, v.y});
+    }
+}
+
+// per-block time step: dt_host if positive, else cfl / S of the step's CFL reduction
+__device__ __forceinline__ float block_dt(const DevParams &p, const Scalars *sc, double dt_host)
+{
+    __shared__ float s_dt;
+    if (threadIdx.x == 0) s_dt = (float)(dt_host > 0.0 ? dt_host : p.cfl / read_acc(&sc->smax));
+    __syncthreads();
+    return s_dt;
+}
+
+// CFL bound (Sec. 3.1) and input check
+__global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f, const float2 *__restrict__ U,
+                                                 Scalars *sc)
+{
+    const int n = p.n;
+    float m = 0.f;
+    unsigned st = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        ff q[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
+        st |= ff_check(f, q);
+        const ff a1 = ff_sub(ff_one(), q[7]);
+        const float p1 = ff_phase_p(f, 0, q[4], a1), p2 = ff_phase_p(f, 1, q[5], q[7]);
+        const float rho = ff_f(q[0]) + ff_f(q[1]);
+        const float cs = ff_sound(f, ff_f(a1), ff_f(q[7]), p1, p2, rho);
+        if (p.nx > 1) {
+            const float s = (fabsf(__fdividef(ff_f(q[2]), rho)) + cs) * f.idx;
+            m = fmaxf(m, s);
+            if (isnan(s)) st |= DIM_ST_NAN;
+        }
+        if (p.ny > 1) {
+            const float s = (fabsf(__fdividef(ff_f(q[3]), rho)) + cs) * f.idy;
+            m = fmaxf(m, s);
+            if (isnan(s)) st |= DIM_ST_NAN;
+        }
+    }
+    block_max_to_f(&sc->smax, m);
+    flag(sc, st);
+}
+
+template <int AXIS, int TN, int TL>
+__global__ void __launch_bounds__(TN *TL) k_sweepff(const DevParams p, const FFP f, const float2 *__restrict__ Uin,
+                                                    float2 *__restrict__ Uout, double dt_host, Scalars *sc,
+                                                    int relax, int check)
+{
+    extern __shared__ float4 smem_ff[];
+    const float dtdx = block_dt(p, sc, dt_host) * (AXIS == 0 ? f.idx : f.idy);
+    sweepff_tile<AXIS, TN, TL>(p, f, Uin, Uout, dtdx, sc, relax, check, blockIdx.x * TN, blockIdx.y * TL, smem_ff);
+}
+
+// pointwise relaxation in place: DIM_RELAX_PRESSURE (Sec. 3.3) or
+// DIM_RELAX_TEMPERATURE (Sec. 3.4.1 equilibrium), optionally with the
+// end-of-step check
+__global__ void __launch_bounds__(256) k_relaxff(const DevParams p, const FFP f, float2 *U, Scalars *sc, int which,
+                                                 int check)
+{
+    const int n = p.n;
+    unsigned st = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        ff q[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
+        unsigned r;
+        if (which == DIM_RELAX_PRESSURE) {
+            r = ff_prelax(f, q);
+        } else {
+            float T;
+            r = ff_equilibrium(f, q[0], q[1], ff_add(q[4], q[5]), T, q[7], q[4], q[5]);
+        }
+        if (check) st |= ff_check(f, q) | (r & DIM_ST_NAN);
+        else st |= r & (DIM_ST_NAN | DIM_ST_NONPHYS | DIM_ST_NOROOT);
+        st_ff(U, 4 * (size_t)n + c, q[4]);
+        st_ff(U, 5 * (size_t)n + c, q[5]);
+        st_ff(U, 7 * (size_t)n + c, q[7]);
+    }
+    flag(sc, st);
+}
+
+// Chebyshev parameters of one solve for the whole block: P (thread 0), then
+// b_m, tau b_m and 1/(1 + tau b_m) per position (Sec. 3.2, Eq. LIM)
+__device__ __forceinline__ int block_schedule(const DevParams &p, double tau, double lam, bool viscous, float *s_tb,
+                                              float *s_rd, unsigned &capped)
+{
+    __shared__ int s_P;
+    __shared__ unsigned s_cap;
+    __shared__ double s_b[2 * PMAX];
+    if (threadIdx.x == 0) {
+        unsigned cp;
+        s_P = viscous ? cheb_P_visc(p, tau, lam, cp) : cheb_P(p, tau, lam, cp);
+        s_cap = cp;
+    }
+    __syncthreads();
+    const int P = s_P;
+    cheb_schedule_block(p, P, lam, s_b);
+    __syncthreads();
+    for (int s = threadIdx.x; s < 2 * P - 1; s += blockDim.x) {
+        s_tb[s] = (float)(tau * s_b[s]);
+        s_rd[s] = (float)(1.0 / (1.0 + tau * s_b[s]));
+    }
+    __syncthreads();
+    capped = s_cap;
+    return P;
+}
+
+// FP32 scratch of the heat stage (planes of n floats) and the FF volume
+// fraction of an outer iteration
+struct HeatFF {
+    float *T0, *V, *L, *va, *vb, *Ti, *Ia;
+    float2 *Ai;
+};
+
+// temperature relaxation + heat conduction by the local-iteration method
+// (Sec. 3.4, Algorithm 1), cooperative: coefficients -> lambda_max -> P, b_m
+// -> 2P - 2 predictor sweeps -> conservative last sweep + projection
+__global__ void __launch_bounds__(256) k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s, Scalars *sc,
+                                                double dt_host, int trelax_first, int check)
+{
+    __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
+    const int n = p.n;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    __shared__ double s_tau;
+    if (threadIdx.x == 0) s_tau = dt_host > 0.0 ? dt_host : p.cfl / read_acc(&sc->smax);
+    __syncthreads();
+    const double tau = s_tau;
+    const float tauf = (float)tau;
+    const int nout = p.n_outer < 1 ? 1 : (p.n_outer > 8 ? 8 : p.n_outer);
+    unsigned st = 0;
+
+    for (int c = t0; c < n; c += nt) {
+        const ff M1 = ld_ff(U, c), M2 = ld_ff(U, n + (size_t)c);
+        const float m1 = ff_f(M1), m2 = ff_f(M2);
+        ff E1 = ld_ff(U, 4 * (size_t)n + c), E2 = ld_ff(U, 5 * (size_t)n + c), a2 = ld_ff(U, 7 * (size_t)n + c);
+        float T;
+        if (trelax_first) {
+            const unsigned r = ff_equilibrium(f, M1, M2, ff_add(E1, E2), T, a2, E1, E2);
+            if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+            st |= r & DIM_ST_NAN;
+            st_ff(U, 4 * (size_t)n + c, E1);
+            st_ff(U, 5 * (size_t)n + c, E2);
+            st_ff(U, 7 * (size_t)n + c, a2);
+        } else {
+            T = ff_mixture_T(f, m1, m2, E1, E2, a2);
+        }
+        s.T0[c] = T;
+        float V, L;
+        ff_heat_coeffs(f, m1, m2, T, a2, V, L);
+        s.V[c] = V;
+        s.L[c] = L;
+        const float a2f = ff_f(a2);
+        s.Ia[c] = ff_f(ff_sub(ff_one(), a2)) * f.src[0] + a2f * f.src[1];
+    }
+    for (int it = 0; it < nout; it++) {
+        if (!grid_barrier(sc)) return;
+        float lm = 0.f;
+        for (int c = t0; c < n; c += nt) lm = fmaxf(lm, gershf(p, neighbours(p, c), c, s.V, s.L, f.idx2, f.idy2));
+        block_max_to_f(&sc->lam[it], lm);
+        if (!grid_barrier(sc)) return;
+        unsigned capped;
+        const int P = block_schedule(p, tau, read_acc(&sc->lam[it]), false, s_tb, s_rd, capped);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicMax(&sc->P[0], P);
+            if (capped) st |= capped;
+        }
+        const float *vin = s.T0;
+        for (int m = 1; m <= 2 * P - 2; m++) {
+            float *vout = (m & 1) ? s.va : s.vb;
+            const float tb = s_tb[m - 1], rd = s_rd[m - 1];
+            for (int c = t0; c < n; c += nt) {
+                const float Lv = lapf(p, neighbours(p, c), c, vin, s.L, f.idx2, f.idy2);
+                vout[c] = (s.T0[c] + tb * vin[c] + tauf * s.V[c] * (Lv + s.Ia[c])) * rd;
+            }
+            if (!grid_barrier(sc)) return;
+            vin = vout;
+        }
+        const bool last = it == nout - 1;
+        for (int c = t0; c < n; c += nt) {
+            const float dq = tauf * (lapf(p, neighbours(p, c), c, vin, s.L, f.idx2, f.idy2) + s.Ia[c]);
+            const ff M1 = ld_ff(U, c), M2 = ld_ff(U, n + (size_t)c);
+            const ff E1 = ld_ff(U, 4 * (size_t)n + c), E2 = ld_ff(U, 5 * (size_t)n + c);
+            float T;
+            ff a2, E1n, E2n;
+            const unsigned r = ff_equilibrium(f, M1, M2, ff_add_f(ff_add(E1, E2), dq), T, a2, E1n, E2n);
+            if (last) {
+                ff q[NQ];
+                q[0] = M1;
+                q[1] = M2;
+                q[2] = q[3] = ff_of(0.f);
+                q[4] = E1n;
+                q[5] = E2n;
+                q[6] = ff_add_f(ld_ff(U, 6 * (size_t)n + c), dq);
+                q[7] = a2;
+                st_ff(U, 4 * (size_t)n + c, q[4]);
+                st_ff(U, 5 * (size_t)n + c, q[5]);
+                st_ff(U, 6 * (size_t)n + c, q[6]);
+                st_ff(U, 7 * (size_t)n + c, q[7]);
+                if (check) st |= ff_check(f, q) | (r & DIM_ST_NAN);
+                else if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+            } else {
+                if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+                s.Ti[c] = T;
+                st_ff(s.Ai, c, a2);
+            }
+        }
+        if (!last) {
+            if (!grid_barrier(sc)) return;
+            for (int c = t0; c < n; c += nt) {
+                const float m1 = ff_f(ld_ff(U, c)), m2 = ff_f(ld_ff(U, n + (size_t)c));
+                const ff a2 = ld_ff(s.Ai, c);
+                float V, L;
+                ff_heat_coeffs(f, m1, m2, s.Ti[c], a2, V, L);
+                s.V[c] = V;
+                s.L[c] = L;
+                s.Ia[c] = ff_f(ff_sub(ff_one(), a2)) * f.src[0] + ff_f(a2) * f.src[1];
+            }
+        }
+    }
+    flag(sc, st);
+}
+
+// FP32 scratch of the viscous stage (planes of n floats)
+struct ViscFF {
+    float *V, *a1, *a2, *u0, *w0, *ua, *ub, *wa, *wb;
+};
+
+// viscous step along AXIS (Sec. 3.2), cooperative: velocities, 1/rho and the
+// volume fractions -> lambda_max -> P, b_m -> 2P - 2 predictor sweeps on
+// (u_n with 4/3 mu, u_t with mu) -> conservative last sweep with the energy
+// updates (+ pressure relaxation)
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, float2 *U, ViscFF s, Scalars *sc,
+                                                double dt_host, int relax, int check)
+{
+    __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
+    constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
+    constexpr int SLOT = AXIS == 0 ? LAM_VX : LAM_VY;
+    const int n = p.n;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    __shared__ double s_tau;
+    if (threadIdx.x == 0) s_tau = dt_host > 0.0 ? dt_host : p.cfl / read_acc(&sc->smax);
+    __syncthreads();
+    const double tau = s_tau;
+    const float tauf = (float)tau;
+    const float ih2 = AXIS == 0 ? f.idx2 : f.idy2;
+    const float ih = AXIS == 0 ? f.idx : f.idy;
+    const float mu0 = f.mu[0], mu1 = f.mu[1];
+    unsigned st = 0;
+
+    for (int c = t0; c < n; c += nt) {
+        const float rho = ff_f(ld_ff(U, c)) + ff_f(ld_ff(U, n + (size_t)c));
+        const ff a2 = ld_ff(U, 7 * (size_t)n + c);
+        s.V[c] = __fdividef(1.f, rho);
+        s.a2[c] = ff_f(a2);
+        s.a1[c] = ff_f(ff_sub(ff_one(), a2));
+        s.u0[c] = __fdividef(ff_f(ld_ff(U, QN * (size_t)n + c)), rho);
+        s.w0[c] = __fdividef(ff_f(ld_ff(U, QT * (size_t)n + c)), rho);
+    }
+    if (!grid_barrier(sc)) return;
+    auto mu_of = [&](int c) { return s.a1[c] * mu0 + s.a2[c] * mu1; };
+    auto nbs = [&](int c, int &cm, int &cp) {
+        const Nb nb = neighbours(p, c);
+        cm = AXIS == 0 ? nb.xm : nb.ym;
+        cp = AXIS == 0 ? nb.xp : nb.yp;
+    };
+    float lm = 0.f;
+    for (int c = t0; c < n; c += nt) {
+        int cm, cp;
+        nbs(c, cm, cp);
+        const float lc = 4.f / 3.f * mu_of(c);
+        const float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_of(cm) + lc) : 0.f;
+        const float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_of(cp)) : 0.f;
+        lm = fmaxf(lm, 2.f * s.V[c] * ((fl + fr) * ih2));
+    }
+    block_max_to_f(&sc->lam[SLOT], lm);
+    if (!grid_barrier(sc)) return;
+    unsigned capped;
+    const int P = block_schedule(p, tau, read_acc(&sc->lam[SLOT]), true, s_tb, s_rd, capped);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicMax(&sc->P[1 + AXIS], P);
+        if (capped) st |= capped;
+    }
+    const float *uin = s.u0, *win = s.w0;
+    for (int m = 1; m <= 2 * P - 2; m++) {
+        float *uo = (m & 1) ? s.ua : s.ub;
+        float *wo = (m & 1) ? s.wa : s.wb;
+        const float tb = s_tb[m - 1], rd = s_rd[m - 1];
+        for (int c = t0; c < n; c += nt) {
+            int cm, cp;
+            nbs(c, cm, cp);
+            const float mc = mu_of(c);
+            const float mm = cm >= 0 ? 0.5f * (mu_of(cm) + mc) : 0.f;
+            const float mp = cp >= 0 ? 0.5f * (mc + mu_of(cp)) : 0.f;
+            const float uc = uin[c], wc = win[c];
+            const float Lu = (cp >= 0 ? 4.f / 3.f * mp * (uin[cp] - uc) * ih2 : 0.f) -
+                             (cm >= 0 ? 4.f / 3.f * mm * (uc - uin[cm]) * ih2 : 0.f);
+            const float Lw =
+                (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.f) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.f);
+            uo[c] = (s.u0[c] + tb * uc + tauf * s.V[c] * Lu) * rd;
+            wo[c] = (s.w0[c] + tb * wc + tauf * s.V[c] * Lw) * rd;
+        }
+        if (!grid_barrier(sc)) return;
+        uin = uo;
+        win = wo;
+    }
+    for (int c = t0; c < n; c += nt) {
+        int cm, cp;
+        nbs(c, cm, cp);
+        const float mc = mu_of(c);
+        float Fn[2], Ft[2], W[2], aF1[2], aF2[2];
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            const int cl = sd == 0 ? cm : c, cr = sd == 0 ? c : cp;
+            if ((sd == 0 ? cm : cp) < 0) {
+                Fn[sd] = Ft[sd] = W[sd] = aF1[sd] = aF2[sd] = 0.f;
+                continue;
+            }
+            const float lmf = 0.5f * ((sd == 0 ? mu_of(cm) : mc) + (sd == 0 ? mc : mu_of(cp)));
+            Fn[sd] = 4.f / 3.f * lmf * (uin[cr] - uin[cl]) * ih;
+            Ft[sd] = lmf * (win[cr] - win[cl]) * ih;
+            W[sd] = 0.5f * (uin[cl] + uin[cr]) * Fn[sd] + 0.5f * (win[cl] + win[cr]) * Ft[sd];
+            aF1[sd] = 0.5f * (s.a1[cl] + s.a1[cr]);
+            aF2[sd] = 0.5f * (s.a2[cl] + s.a2[cr]);
+        }
+        const float uh = uin[c], wh = win[c];
+        const float ti = tauf * ih;
+        ff q[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
+        q[QN] = ff_add_f(q[QN], ti * (Fn[1] - Fn[0]));
+        q[QT] = ff_add_f(q[QT], ti * (Ft[1] - Ft[0]));
+        q[6] = ff_add_f(q[6], ti * (W[1] - W[0]));
+        q[4] = ff_add_f(q[4], ti * ((aF1[1] * W[1] - aF1[0] * W[0]) -
+                                    (uh * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + wh * (aF1[1] * Ft[1] - aF1[0] * Ft[0]))));
+        q[5] = ff_add_f(q[5], ti * ((aF2[1] * W[1] - aF2[0] * W[0]) -
+                                    (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0]))));
+        if (relax) {
+            const unsigned r = ff_prelax(f, q);
+            if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
+            st |= r & DIM_ST_NAN;
+        }
+        if (check) st |= ff_check(f, q);
+#pragma unroll
+        for (int k = 2; k < NQ; k++) st_ff(U, k * (size_t)n + c, q[k]);
+    }
+    flag(sc, st);
+}
+
+// ---------------------------------------------------------------------------
+// host side: constants, set-up, launchers
+// ---------------------------------------------------------------------------
+constexpr int SXF_TN = 128, SXF_TL = 1;
+constexpr int SYF_TN = 32, SYF_TL = 8;
+
+static int g_heatff_blocks = 0, g_viscff_blocks[2] = {0, 0};
+
+static ff host_split(double x)
+{
+    const float h = (float)x;
+    return ff{h, (float)(x - (double)h)};
+}
+
+FFP ffp_of(const DevParams &p)
+{
+    FFP f;
+    memset(&f, 0, sizeof(f));
+    for (int k = 0; k < 2; k++) {
+        f.g[k] = (float)p.g[k];
+        f.gm1[k] = (float)p.gm1[k];
+        f.igm1[k] = (float)p.inv_gm1[k];
+        f.pinf[k] = (float)p.pinf[k];
+        f.gpinf[k] = (float)p.gpinf[k];
+        f.cv[k] = (float)p.cv[k];
+        f.mu[k] = (float)p.mu[k];
+        f.k0[k] = (float)p.k0[k];
+        f.src[k] = (float)p.src[k];
+        f.cold[k] = host_split(p.gpinf[k] * p.inv_gm1[k]);
+        f.pinf_ff[k] = host_split(p.pinf[k]);
+        f.g_ff[k] = host_split(p.g[k]);
+        f.gm1_ff[k] = host_split(p.gm1[k]);
+        f.cv_ff[k] = host_split(p.cv[k]);
+        f.gcv_ff[k] = host_split(p.gm1[k] * p.cv[k]);
+    }
+    f.B1_ff = host_split(p.pinf[0] - p.pinf[1]);
+    f.dcold = host_split(p.gpinf[0] * p.inv_gm1[0] - p.gpinf[1] * p.inv_gm1[1]);
+    f.B1 = (float)(p.pinf[0] - p.pinf[1]);
+    f.cfl = (float)p.cfl;
+    f.idx = (float)p.idx;
+    f.idy = (float)p.idy;
+    f.idx2 = (float)p.idx2;
+    f.idy2 = (float)p.idy2;
+    f.inv_Tref = (float)p.inv_Tref;
+    f.k_exp = (float)p.k_exp;
+    f.k_pow = p.k_pow;
+    return f;
+}
+
+// the sweep kernels' shared-memory limit (once per device)
+cudaError_t sweepff_setup()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sweepff<0, SXF_TN, SXF_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sweepff_smem(SXF_TN, SXF_TL));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweepff<1, SYF_TN, SYF_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweepff_smem(SYF_TN, SYF_TL));
+}
+
+cudaError_t bulkff_setup(int nsm)
+{
+    cudaError_t e = sweepff_setup();
+    if (e != cudaSuccess) return e;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff, 256, 0);
+    if (e != cudaSuccess) return e;
+    g_heatff_blocks = b * nsm;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<0>, 256, 0);
+    if (e != cudaSuccess) return e;
+    g_viscff_blocks[0] = b * nsm;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<1>, 256, 0);
+    if (e != cudaSuccess) return e;
+    g_viscff_blocks[1] = b * nsm;
+    return cudaSuccess;
+}
+
+static int elementwise_grid(size_t m)
+{
+    size_t g = (m + 255) / 256;
+    return g < 152 * 16 ? (int)g : 152 * 16;
+}
+
+cudaError_t launch_ff_in(const double *U, float2 *F, size_t m, cudaStream_t s)
+{
+    k_ff_in<<<elementwise_grid(m), 256, 0, s>>>(U, F, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ff_out(const float2 *F, double *U, size_t m, cudaStream_t s)
+{
+    k_ff_out<<<elementwise_grid(m), 256, 0, s>>>(F, U, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave_ff(const DevParams &p, const FFP &f, const float2 *U, Scalars *sc, cudaStream_t s)
+{
+    k_wave_ff<<<elementwise_grid((size_t)p.n), 256, 0, s>>>(p, f, U, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_ff(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
+                            double dt_host, Scalars *sc, int relax, int check, cudaStream_t s)
+{
+    if (axis == 0) {
+        dim3 grid((p.nx + SXF_TN - 1) / SXF_TN, (p.ny + SXF_TL - 1) / SXF_TL);
+        k_sweepff<0, SXF_TN, SXF_TL><<<grid, SXF_TN * SXF_TL, sweepff_smem(SXF_TN, SXF_TL), s>>>(
+            p, f, Uin, Uout, dt_host, sc, relax, check);
+    } else {
+        dim3 grid((p.ny + SYF_TN - 1) / SYF_TN, (p.nx + SYF_TL - 1) / SYF_TL);
+        k_sweepff<1, SYF_TN, SYF_TL><<<grid, SYF_TN * SYF_TL, sweepff_smem(SYF_TN, SYF_TL), s>>>(
+            p, f, Uin, Uout, dt_host, sc, relax, check);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars *sc, int which, int check,
+                            cudaStream_t s)
+{
+    k_relaxff<<<elementwise_grid((size_t)p.n), 256, 0, s>>>(p, f, U, sc, which, check);
+    return cudaGetLastError();
+}
+
+static int coop_grid(int maxb, int n)
+{
+    const int need = (n + 255) / 256;
+    return need < maxb ? need : maxb;
+}
+
+// the FP32 planes alias the context's FP64 scratch planes S (two floats per double)
+cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
+                           int trelax_first, int check, cudaStream_t st)
+{
+    const size_t n = (size_t)p.n;
+    float *F = (float *)S;
+    HeatFF hs{F, F + n, F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n, F + 6 * n, (float2 *)(F + 8 * n)};
+    DevParams pp = p;
+    FFP ff_ = f;
+    void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&hs, (void *)&sc, (void *)&dt_host,
+                    (void *)&trelax_first, (void *)&check};
+    return cudaLaunchCooperativeKernel((const void *)k_heatff, dim3(coop_grid(g_heatff_blocks, p.n)), dim3(256), args,
+                                       0, st);
+}
+
+cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, float2 *U, double *S, Scalars *sc,
+                           double dt_host, int relax, int check, cudaStream_t st)
+{
+    const size_t n = (size_t)p.n;
+    float *F = (float *)S;
+    ViscFF vs{F, F + n, F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n, F + 6 * n, F + 7 * n, F + 8 * n};
+    DevParams pp = p;
+    FFP ff_ = f;
+    void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&vs, (void *)&sc, (void *)&dt_host,
+                    (void *)&relax, (void *)&check};
+    const void *fn = axis == 0 ? (const void *)k_viscff<0> : (const void *)k_viscff<1>;
+    return cudaLaunchCooperativeKernel(fn, dim3(coop_grid(g_viscff_blocks[axis], p.n)), dim3(256), args, 0, st);
+}
+
+}  // namespace dimk

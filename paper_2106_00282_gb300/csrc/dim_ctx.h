@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dim.h"
-#include "dim_device.cuh"
+#include "dim_ff.cuh"
 
 namespace dimk {
 cudaError_t sweep_setup();
@@ -19,14 +19,20 @@ cudaError_t launch_heat(const DevParams &p, double *U, const HeatScratch &s, Sca
                         int trelax_first, int check, cudaStream_t st);
 cudaError_t launch_visc(const DevParams &p, int axis, double *U, const ViscScratch &s, Scalars *sc, double dt_host,
                         int relax, int check, cudaStream_t st);
-cudaError_t bulk32_setup(int nsm);
-cudaError_t launch_sweep32(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
-                           int relax, int check, cudaStream_t s);
-cudaError_t launch_wave_max32(const DevParams &p, const double *U, Scalars *sc, cudaStream_t s);
-cudaError_t launch_heat32(const DevParams &p, double *U, double *S, Scalars *sc, double dt_host, int trelax_first,
-                          int check, cudaStream_t st);
-cudaError_t launch_visc32(const DevParams &p, int axis, double *U, double *S, Scalars *sc, double dt_host, int relax,
-                          int check, cudaStream_t st);
+// FP32-bulk form on float-float state planes (dim_bulkff.cu)
+cudaError_t bulkff_setup(int nsm);
+FFP ffp_of(const DevParams &p);
+cudaError_t launch_ff_in(const double *U, float2 *F, size_t m, cudaStream_t s);
+cudaError_t launch_ff_out(const float2 *F, double *U, size_t m, cudaStream_t s);
+cudaError_t launch_wave_ff(const DevParams &p, const FFP &f, const float2 *U, Scalars *sc, cudaStream_t s);
+cudaError_t launch_sweep_ff(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
+                            double dt_host, Scalars *sc, int relax, int check, cudaStream_t s);
+cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars *sc, int which, int check,
+                            cudaStream_t s);
+cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
+                           int trelax_first, int check, cudaStream_t st);
+cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, float2 *U, double *S, Scalars *sc,
+                           double dt_host, int relax, int check, cudaStream_t st);
 }  // namespace dimk
 
 using dimk::DevParams;
@@ -34,7 +40,7 @@ using dimk::Scalars;
 
 namespace dimctx {
 
-enum KernelId { K_SWEEP_X, K_SWEEP_Y, K_HEAT, K_VISC_X, K_VISC_Y, K_WAVE, K_RELAX, K_COPY, K_NKERNELS };
+enum KernelId { K_SWEEP_X, K_SWEEP_Y, K_HEAT, K_VISC_X, K_VISC_Y, K_WAVE, K_RELAX, K_COPY, K_CONVERT, K_NKERNELS };
 
 struct ProfRec {
     int kid;
@@ -59,6 +65,10 @@ struct dim_ctx {
     cudaStream_t side;
     cudaEvent_t ev_mass, ev_mom;
     double *beta; // Chebyshev roots table (PMAX x PMAX)
+    // FP32 bulk: the state as float-float planes (8 planes of n float2) while
+    // steps run; U2 holds the other buffer of the sweeps' ping-pong
+    float2 *Uf;
+    dimk::FFP ffp;
     Scalars *sc;
     int device;
     // profiling

@@ -132,77 +132,12 @@ __device__ __forceinline__ bool lt_i(double x, double y)  // x < y
 }
 
 // ---------------------------------------------------------------------------
-// FP64 division and square root for the FP32-bulk kernels, which carry no
-// bit-identity requirement: the hardware approximations (PTX
-// rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64) refined by Newton-Raphson
-// iterations -- reciprocal r <- r + r(1 - b r), reciprocal square root
-// y <- y + y(1/2 - x y^2 / 2), each doubling the correct bits -- and one
-// final correction of the quotient q <- q + r(a - b q) (Markstein) and of the
-// root s <- s + (y/2)(x - s^2).  Within an ulp of the IEEE results, at a
-// fraction of the cost of the IEEE division and square-root sequences on the
-// FP64 pipe.  The approximations flush subnormal operands and results to zero
-// and the corrections turn infinities into NaN, so both routines check their
-// domain on the integer pipe and hand everything outside it to the IEEE
-// operation (an out-of-line call, taken only at the edges):
-//   fast_div(a, b): b normal with a normal reciprocal (biased exponent of b in
-//     1..2044), and the quotient a normal finite number or a zero from a = +-0;
-//   fast_sqrt(x): x positive, normal and finite.
-// The FP64 path keeps IEEE / and sqrt (FAST = false below).
-// ---------------------------------------------------------------------------
-static __device__ __noinline__ double ieee_div(double a, double b) { return a / b; }
-static __device__ __noinline__ double ieee_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ unsigned biased_exp(double x)  // the 11-bit exponent field, sign bit above it
-{
-    return (unsigned)__double2hiint(x) >> 20;
-}
-__device__ __forceinline__ double fast_div(double a, double b)
-{
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
-    double e = fma(-b, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-b, r, 1.0);
-    r = fma(r, e, r);
-    const double q0 = a * r;
-    const double q = fma(r, fma(-b, q0, a), q0);
-    const unsigned eb = biased_exp(b) & 0x7ffu, eq = biased_exp(q) & 0x7ffu;
-    const bool a_zero = (__double_as_longlong(a) << 1) == 0;
-    const bool ok = (eb - 1u) < 2044u && ((eq - 1u) < 2046u || a_zero);
-    return ok ? (a_zero ? q0 : q) : ieee_div(a, b);  // q0 = a r keeps the sign of a zero quotient
-}
-__device__ __forceinline__ double fast_sqrt(double x)
-{
-    double y;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double h = 0.5 * x;
-    y = fma(y, fma(-h * y, y, 0.5), y);
-    y = fma(y, fma(-h * y, y, 0.5), y);
-    const double s = x * y;
-    const double r = fma(-s, s, x);
-    const bool ok = (biased_exp(x) - 1u) < 2046u;  // sign bit clear, exponent 1..2046
-    return ok ? fma(0.5 * y, r, s) : ieee_sqrt(x);
-}
-template <bool FAST>
-__device__ __forceinline__ double dv(double a, double b)
-{
-    if constexpr (FAST) return fast_div(a, b);
-    else return a / b;
-}
-template <bool FAST>
-__device__ __forceinline__ double dsq(double x)
-{
-    if constexpr (FAST) return fast_sqrt(x);
-    else return sqrt(x);
-}
-
-// ---------------------------------------------------------------------------
 // Stiffened gas (Eqs. eos_stiffened, eos_stiffened2 with q_k = 0)
 // ---------------------------------------------------------------------------
 // p_k = (gamma_k - 1) E_k / alpha_k - gamma_k pinf_k, E_k = alpha_k rho_k e_k
-template <bool FAST = false>
 __device__ __forceinline__ double sg_p(const DevParams &p, int k, double Ek, double ak)
 {
-    return dv<FAST>(p.gm1[k] * Ek, ak) - p.gpinf[k];
+    return p.gm1[k] * Ek / ak - p.gpinf[k];
 }
 // E_k = alpha_k (p + gamma_k pinf_k) / (gamma_k - 1)
 __device__ __forceinline__ double sg_E(const DevParams &p, int k, double pr, double ak)
@@ -274,7 +209,6 @@ __device__ __forceinline__ unsigned check_state(const DevParams &p, const double
 // B_k = (g_k-1) a_k^0; a_1(p) + a_2(p) = 1 is a quadratic whose larger root is
 // the unique one with p + pinf_k > 0.  Step (2): p from the mixture energy.
 // Step (3): E_k = E_k(p, a_k).
-template <bool FAST = false>
 __device__ __forceinline__ unsigned prelax(const DevParams &p, double *q)
 {
     const double g1 = p.g[0], g2 = p.g[1];
@@ -287,14 +221,14 @@ __device__ __forceinline__ unsigned prelax(const DevParams &p, double *q)
     double disc = B * B - 4.0 * A * C;
     unsigned st = 0;
     if (lt0_i(disc)) { st |= DIM_ST_NOROOT; disc = 0.0; }
-    double sq = dsq<FAST>(disc);
-    double pr = le0_i(B) ? dv<FAST>(sq - B, 2.0 * A) : dv<FAST>(2.0 * C, -B - sq);
-    double a2n = dv<FAST>(ak2 + bk2 * pr, g2 * pr + ek2);
+    double sq = sqrt(disc);
+    double pr = le0_i(B) ? (sq - B) / (2.0 * A) : (2.0 * C) / (-B - sq);
+    double a2n = (ak2 + bk2 * pr) / (g2 * pr + ek2);
     double a1n = 1.0 - a2n;
     double rho = q[0] + q[1];
-    double rhoe = q[6] - dv<FAST>(0.5 * (q[2] * q[2] + q[3] * q[3]), rho);
-    double p2 = dv<FAST>(rhoe - (a1n * p.g[0] * p.pinf[0] * p.inv_gm1[0] + a2n * p.g[1] * p.pinf[1] * p.inv_gm1[1]),
-                         a1n * p.inv_gm1[0] + a2n * p.inv_gm1[1]);
+    double rhoe = q[6] - 0.5 * (q[2] * q[2] + q[3] * q[3]) / rho;
+    double p2 = (rhoe - (a1n * p.g[0] * p.pinf[0] * p.inv_gm1[0] + a2n * p.g[1] * p.pinf[1] * p.inv_gm1[1])) /
+                (a1n * p.inv_gm1[0] + a2n * p.inv_gm1[1]);
     q[4] = sg_E(p, 0, p2, a1n);
     q[5] = sg_E(p, 1, p2, a2n);
     q[7] = a2n;
@@ -312,7 +246,6 @@ __device__ __forceinline__ unsigned prelax(const DevParams &p, double *q)
 //   qa a^2 + qb a + qc = 0, qa = B1 (G + C), qb = E G - B1 G2C2 - C B1,
 //   qc = -E G2C2, E = rho e - pinf_1;  admissible root (sqrt(d) - qb)/(2 qa).
 // ---------------------------------------------------------------------------
-template <bool FAST = false>
 __device__ __forceinline__ unsigned equilibrium(const DevParams &p, double m1, double m2, double rhoe, double &T,
                                                 double &a)
 {
@@ -326,9 +259,9 @@ __device__ __forceinline__ unsigned equilibrium(const DevParams &p, double m1, d
     double disc = qb * qb - 4.0 * qa * qc;
     unsigned st = 0;
     if (lt0_i(disc)) { st |= DIM_ST_NOROOT; disc = 0.0; }
-    double sq = dsq<FAST>(disc);
-    a = gt0_i(qb) ? dv<FAST>(-2.0 * qc, qb + sq) : dv<FAST>(sq - qb, 2.0 * qa);
-    T = dv<FAST>(E + B1 * a, C);
+    double sq = sqrt(disc);
+    a = gt0_i(qb) ? (-2.0 * qc) / (qb + sq) : (sq - qb) / (2.0 * qa);
+    T = (E + B1 * a) / C;
     if (!(gt0_i(a) && lt_i(a, 1.0) && gt0_i(T))) st |= DIM_ST_NONPHYS;
     if (nan_i(a) || nan_i(T)) st |= DIM_ST_NAN;
     return st;
@@ -380,11 +313,10 @@ __device__ __forceinline__ unsigned trelax_cell(const DevParams &p, double m1, d
 }
 
 // mixture temperature of a cell in thermal equilibrium (energy form of Eq. Taverage)
-template <bool FAST = false>
 __device__ __forceinline__ double mixture_T(const DevParams &p, double m1, double m2, double E1, double E2, double a2)
 {
     double C = m1 * p.cv[0] + m2 * p.cv[1];
-    return dv<FAST>(E1 + E2 - (1.0 - a2) * p.pinf[0] - a2 * p.pinf[1], C);
+    return (E1 + E2 - (1.0 - a2) * p.pinf[0] - a2 * p.pinf[1]) / C;
 }
 
 // conduction coefficients at (T, a): V = dT/d(rho e) = 1/(C + B1^2/K),

@@ -16,15 +16,18 @@
 #include <mutex>
 
 #include "../../include/dim.h"
-#include "dim_device.cuh"
+#include "dim_ff.cuh"
 
 namespace dimk {
 cudaError_t sweep_setup();
-cudaError_t sweep32_setup();
+cudaError_t sweepff_setup();
 cudaError_t launch_sweep(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
                          int relax, int check, cudaStream_t s);
-cudaError_t launch_sweep32(const DevParams &p, int axis, const double *Uin, double *Uout, double dt_host, Scalars *sc,
-                           int relax, int check, cudaStream_t s);
+FFP ffp_of(const DevParams &p);
+cudaError_t launch_ff_in(const double *U, float2 *F, size_t m, cudaStream_t s);
+cudaError_t launch_ff_out(const float2 *F, double *U, size_t m, cudaStream_t s);
+cudaError_t launch_sweep_ff(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
+                            double dt_host, Scalars *sc, int relax, int check, cudaStream_t s);
 }  // namespace dimk
 int dim_host_params(const dim_params *hp, int nx, int ny, double dx, double dy, dimk::DevParams *out);
 
@@ -55,7 +58,7 @@ int setup_current_device(double **scratch)
     if (!g_ready[dev]) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return DIM_ECUDA;
-        if (dimk::sweep_setup() != cudaSuccess || dimk::sweep32_setup() != cudaSuccess) return DIM_ECUDA;
+        if (dimk::sweep_setup() != cudaSuccess || dimk::sweepff_setup() != cudaSuccess) return DIM_ECUDA;
         g_scratch_ptr[dev] = (double *)ptr;
         g_ready[dev] = true;
     }
@@ -81,12 +84,21 @@ extern "C" int dim_hllc_sweep_noalloc(const dim_params *p, int nx, int ny, doubl
     dimk::Scalars *sc = (dimk::Scalars *)(scratch + 8 * kPlaneDoubles);
     // the array keeps the previous call's contents: the status scalars start at zero
     if (cudaMemsetAsync(sc, 0, sizeof(dimk::Scalars), s) != cudaSuccess) return DIM_ECUDA;
-    // the kernel of the parameters' precision, as dim_hllc_sweep picks it
-    const cudaError_t e = dp.precision == DIM_PRECISION_FP32_BULK
-                              ? dimk::launch_sweep32(dp, axis, U, Uout, dt, sc, relax, 0, s)
-                              : dimk::launch_sweep(dp, axis, U, Uout, dt, sc, relax, 0, s);
-    if (e != cudaSuccess) return DIM_ECUDA;
-    if (cudaMemcpyAsync(U, Uout, sizeof(double) * 8 * (size_t)dp.n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return DIM_ECUDA;
+    const size_t m = 8 * (size_t)dp.n;
+    if (dp.precision == DIM_PRECISION_FP32_BULK) {
+        // the FP32-bulk sweep of dim_hllc_sweep: the state converted to
+        // float-float planes in the array, swept into U's own memory (8 planes
+        // of float pairs take the bytes of 8 planes of doubles), converted back
+        // in place
+        float2 *F = (float2 *)scratch;
+        const dimk::FFP f = dimk::ffp_of(dp);
+        if (dimk::launch_ff_in(U, F, m, s) != cudaSuccess ||
+            dimk::launch_sweep_ff(dp, f, axis, F, (float2 *)U, dt, sc, relax, 0, s) != cudaSuccess ||
+            dimk::launch_ff_out((const float2 *)U, U, m, s) != cudaSuccess)
+            return DIM_ECUDA;
+        return DIM_OK;
+    }
+    if (dimk::launch_sweep(dp, axis, U, Uout, dt, sc, relax, 0, s) != cudaSuccess) return DIM_ECUDA;
+    if (cudaMemcpyAsync(U, Uout, sizeof(double) * m, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return DIM_ECUDA;
     return DIM_OK;
 }

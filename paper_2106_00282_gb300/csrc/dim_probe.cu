@@ -1,5 +1,5 @@
 // dim_probe.cu -- arithmetic-rate probes and the elementwise check of the
-// FP32-bulk kernels' FP64 division and square root (include/dim_probe.h).
+// FP32-bulk form's FP64 <-> float-float state conversion (include/dim_probe.h).
 //
 // A probe kernel runs, in every thread, NCH independent dependency chains of
 // one operation (enough independent work per warp to cover the pipeline
@@ -10,7 +10,7 @@
 
 #include "../../include/dim.h"
 #include "../../include/dim_probe.h"
-#include "dim_device.cuh"
+#include "dim_ff.cuh"
 
 namespace {
 
@@ -44,8 +44,7 @@ __global__ void __launch_bounds__(TPB) k_probe(int iters, double a, double b, do
                 if constexpr (KIND == DIM_PROBE_DFMA) x[k] = fma(x[k], a, b);
                 else if constexpr (KIND == DIM_PROBE_DADDMUL) x[k] = __dadd_rn(__dmul_rn(x[k], a), b);
                 else if constexpr (KIND == DIM_PROBE_DDIV) x[k] = a / x[k];  // alternates between x0 and a/x0
-                else if constexpr (KIND == DIM_PROBE_DSQRT) x[k] = sqrt(x[k]) * a;  // converges to a^2
-                else x[k] = dimk::fast_div(a, x[k]);
+                else x[k] = sqrt(x[k]) * a;  // DIM_PROBE_DSQRT: converges to a^2
             }
         }
         double s = 0.0;
@@ -55,19 +54,17 @@ __global__ void __launch_bounds__(TPB) k_probe(int iters, double a, double b, do
     }
 }
 
-__global__ void k_fastmath(const double *__restrict__ a, const double *__restrict__ b, double *q, double *r, int n)
+__global__ void k_ff_roundtrip(const double *__restrict__ x, double *__restrict__ y, int n)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (q) q[i] = dimk::fast_div(a[i], b[i]);
-        if (r) r[i] = dimk::fast_sqrt(a[i]);
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = dimk::ff_to_d(dimk::ff_from_d(x[i]));
 }
 
 }  // namespace
 
 extern "C" int dim_probe_rate(int kind, int blocks, int iters, void *cuda_stream, double *ms, double *ops)
 {
-    if (kind < DIM_PROBE_DFMA || kind > DIM_PROBE_FASTDIV || iters < 1 || !ms || !ops) return DIM_EINVAL;
+    if (kind < DIM_PROBE_DFMA || kind > DIM_PROBE_FFMA || iters < 1 || !ms || !ops) return DIM_EINVAL;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
@@ -80,7 +77,7 @@ extern "C" int dim_probe_rate(int kind, int blocks, int iters, void *cuda_stream
     // operands: a contraction for the FMA chains (fixed point 1), a value for
     // the division and square-root chains that keeps them in the normal range
     double a = 0.999999, b = 1e-6;
-    if (kind == DIM_PROBE_DDIV || kind == DIM_PROBE_FASTDIV) a = 1.7;
+    if (kind == DIM_PROBE_DDIV) a = 1.7;
     if (kind == DIM_PROBE_DSQRT) a = 1.3;
     if (cudaMalloc(&out, sizeof(double) * (size_t)blocks * TPB) == cudaSuccess &&
         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
@@ -91,8 +88,7 @@ extern "C" int dim_probe_rate(int kind, int blocks, int iters, void *cuda_stream
             case DIM_PROBE_DADDMUL: k_probe<DIM_PROBE_DADDMUL><<<blocks, TPB, 0, s>>>(iters, a, b, out); break;
             case DIM_PROBE_DDIV: k_probe<DIM_PROBE_DDIV><<<blocks, TPB, 0, s>>>(iters, a, b, out); break;
             case DIM_PROBE_DSQRT: k_probe<DIM_PROBE_DSQRT><<<blocks, TPB, 0, s>>>(iters, a, b, out); break;
-            case DIM_PROBE_FFMA: k_probe<DIM_PROBE_FFMA><<<blocks, TPB, 0, s>>>(iters, a, b, out); break;
-            default: k_probe<DIM_PROBE_FASTDIV><<<blocks, TPB, 0, s>>>(iters, a, b, out); break;
+            default: k_probe<DIM_PROBE_FFMA><<<blocks, TPB, 0, s>>>(iters, a, b, out); break;
             }
             e = cudaGetLastError();
         }
@@ -114,12 +110,12 @@ extern "C" int dim_probe_rate(int kind, int blocks, int iters, void *cuda_stream
     return rc;
 }
 
-extern "C" int dim_probe_fastmath(const double *a, const double *b, double *q, double *r, int n, void *cuda_stream)
+extern "C" int dim_probe_ff_roundtrip(const double *x, double *y, int n, void *cuda_stream)
 {
-    if (n < 0 || !a || !b) return DIM_EINVAL;
+    if (n < 0 || !x || !y) return DIM_EINVAL;
     if (n == 0) return DIM_OK;
     int g = (n + 255) / 256;
     if (g > 4096) g = 4096;
-    k_fastmath<<<g, 256, 0, (cudaStream_t)cuda_stream>>>(a, b, q, r, n);
+    k_ff_roundtrip<<<g, 256, 0, (cudaStream_t)cuda_stream>>>(x, y, n);
     return cudaGetLastError() == cudaSuccess ? DIM_OK : DIM_ECUDA;
 }

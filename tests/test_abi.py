@@ -82,6 +82,6 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dim_from_primitive_vjp(None, None, None, None) == _lib.DIM_EINVAL
     assert lib.dim_wait_selftest(None, 0.1) == _lib.DIM_EINVAL
     ms, ops = C.c_double(), C.c_double()
-    assert lib.dim_probe_rate(9, 0, 10, None, C.byref(ms), C.byref(ops)) == _lib.DIM_EINVAL
+    assert lib.dim_probe_rate(5, 0, 10, None, C.byref(ms), C.byref(ops)) == _lib.DIM_EINVAL
     assert lib.dim_probe_rate(0, 0, 0, None, C.byref(ms), C.byref(ops)) == _lib.DIM_EINVAL
-    assert lib.dim_probe_fastmath(None, None, None, None, 4, None) == _lib.DIM_EINVAL
+    assert lib.dim_probe_ff_roundtrip(None, None, 4, None) == _lib.DIM_EINVAL

@@ -1,6 +1,8 @@
-"""FP32-bulk form of the CUDA path (flux and stencil arithmetic in FP32; state
-accumulation, phase pressures, volume-fraction transport, relaxation root
-solves and Chebyshev parameters in FP64) against the FP64 oracle.
+"""FP32-bulk form of the CUDA path (no FP64 arithmetic inside a step: the state
+as float-float pairs holding the accumulation, the phase pressures' cancellation
+against the cold energy, the volume fraction and a Newton correction of each
+relaxation root; flux, relaxation and stencil arithmetic in FP32) against the
+FP64 oracle.
 
 Tolerance: relative L1 per conserved field <= 2e-5 after 100 steps.  The
 momentum of a flow at rest up to thermal expansion (the conduction disc) is
