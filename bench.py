@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk variant")
+    ap.add_argument("--only-fp32", action="store_true",
+                    help="run only the FP32-bulk form of the workload and print its JSON object (profiling)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched configuration")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (dim_grad) measurement")
     ap.add_argument("--only-adjoint", action="store_true",
@@ -533,6 +535,13 @@ def main():
         ra = run_adjoint(dev, world, args.adjoint_steps, args.adjoint_ckpt)
         if rank == 0:
             print(json.dumps({"adjoint": ra}))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    if args.only_fp32:
+        r32 = run_ours(args, rank, world, dev, precision=1, with_e2e=False)
+        if rank == 0:
+            print(json.dumps({"fp32_bulk": brief(r32), "config": workload_desc(r32["wl"], "fp32-bulk")}))
         if world > 1:
             torch.distributed.destroy_process_group()
         return

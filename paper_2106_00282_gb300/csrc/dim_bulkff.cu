@@ -33,11 +33,12 @@ __global__ void k_ff_out(const float2 *F, double *U, size_t m)
     }
 }
 
-// per-block time step: dt_host if positive, else cfl / S of the step's CFL reduction
-__device__ __forceinline__ float block_dt(const DevParams &p, const Scalars *sc, double dt_host)
+// per-block time step: dt_host if positive, else the step's cfl / S published
+// by the CFL kernel
+__device__ __forceinline__ float block_dt(const Scalars *sc, double dt_host)
 {
     __shared__ float s_dt;
-    if (threadIdx.x == 0) s_dt = (float)(dt_host > 0.0 ? dt_host : p.cfl / read_acc(&sc->smax));
+    if (threadIdx.x == 0) s_dt = dt_host > 0.0 ? (float)dt_host : *(volatile const float *)&sc->dt32;
     __syncthreads();
     return s_dt;
 }
@@ -71,6 +72,18 @@ __global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f,
     }
     block_max_to_f(&sc->smax, m);
     flag(sc, st);
+    // the last block to finish publishes dt = cfl / S as a float, once per step
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&sc->wave_blocks, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        sc->dt32 = (float)(p.cfl / read_acc(&sc->smax));
+        sc->wave_blocks = 0;
+    }
 }
 
 template <int AXIS, int TN, int TL>
@@ -79,7 +92,7 @@ __global__ void __launch_bounds__(TN *TL) k_sweepff(const DevParams p, const FFP
                                                     int relax, int check)
 {
     extern __shared__ float4 smem_ff[];
-    const float dtdx = block_dt(p, sc, dt_host) * (AXIS == 0 ? f.idx : f.idy);
+    const float dtdx = block_dt(sc, dt_host) * (AXIS == 0 ? f.idx : f.idy);
     sweepff_tile<AXIS, TN, TL>(p, f, Uin, Uout, dtdx, sc, relax, check, blockIdx.x * TN, blockIdx.y * TL, smem_ff);
 }
 
@@ -144,12 +157,126 @@ struct HeatFF {
     float2 *Ai;
 };
 
+// Temporally blocked predictor sweeps of Eq. (LIM) for the heat stage.  The
+// grid is cut into tiles of TBX x TBY cells (one line of up to RB - 2 HB cells
+// on a 1D grid).  A round of up to HB sweeps loads each tile with a halo of HB
+// cells -- the starting iterate, T0, tau V, tau V Ia and the face
+// coefficients Lam_f / h^2 (zero at transmissive walls) -- into shared memory,
+// sweeps there (sweep j updates the cells at least j cells inside the loaded
+// region, whose inputs the previous sweep left valid), and writes the tile's
+// cells of the last iterate back.  One grid barrier per round instead of one
+// per sweep; the halo cells are swept redundantly (15 % more stencil work with
+// 4 sweeps per round).  Rounds alternate between the two iterate planes, so no
+// block overwrites a plane another block may still read in the same round.
+constexpr int TBX = 64, TBY = 32, HB = 4;
+constexpr int RB = (TBX + 2 * HB) * (TBY + 2 * HB);
+constexpr size_t LIM_SMEM = 7 * sizeof(float) * RB;
+constexpr int HEAT_THREADS = 512;
+
+__device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Scalars *sc, int M, float tauf,
+                           const float *s_tb, const float *s_rd, float *sm, const float *&vlast)
+{
+    float *sv0 = sm, *sv1 = sm + RB, *sT = sm + 2 * RB, *stV = sm + 3 * RB, *stI = sm + 4 * RB;
+    float *sLx = sm + 5 * RB, *sLy = sm + 6 * RB;
+    const bool ax = p.nx > 1, ay = p.ny > 1;
+    const int tx = ax && ay ? TBX : (ax ? RB - 2 * HB : 1);
+    const int ty = ax && ay ? TBY : (ay ? RB - 2 * HB : 1);
+    const int hx = ax ? HB : 0, hy = ay ? HB : 0;
+    const int wx = tx + 2 * hx, wy = ty + 2 * hy;  // loaded region, at most RB cells
+    const int ntx = (p.nx + tx - 1) / tx, nty = (p.ny + ty - 1) / ty, ntiles = ntx * nty;
+    const float *vin = s.T0;
+    int m0 = 0, r = 0;
+    while (m0 < M) {
+        const int kk = min(HB, M - m0);
+        float *vout = (r & 1) ? s.vb : s.va;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int tj = t / ntx, ti = t - tj * ntx;
+            const int gx0 = ti * tx - hx, gy0 = tj * ty - hy;
+            for (int e = threadIdx.x; e < wx * wy; e += blockDim.x) {
+                const int sy = e / wx, sx = e - sy * wx;
+                int gx = gx0 + sx, gy = gy0 + sy;
+                bool in = true;
+                if (gx < 0 || gx >= p.nx) {
+                    if (p.bc[0] == DIM_BC_PERIODIC) gx = (gx % p.nx + p.nx) % p.nx;
+                    else in = false;
+                }
+                if (gy < 0 || gy >= p.ny) {
+                    if (p.bc[1] == DIM_BC_PERIODIC) gy = (gy % p.ny + p.ny) % p.ny;
+                    else in = false;
+                }
+                if (in) {
+                    const int c = gy * p.nx + gx;
+                    const float tv = tauf * s.V[c];
+                    sv0[e] = vin[c];
+                    sT[e] = s.T0[c];
+                    stV[e] = tv;
+                    stI[e] = tv * s.Ia[c];
+                    sv1[e] = s.L[c];
+                } else {  // outside a transmissive wall: no cell, no face (marked by Lam < 0)
+                    sv0[e] = sT[e] = stV[e] = stI[e] = 0.f;
+                    sv1[e] = -1.f;
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < wx * wy; e += blockDim.x) {
+                const int sy = e / wx, sx = e - sy * wx;
+                const float Lc = sv1[e];
+                float fx = 0.f, fy = 0.f;
+                if (ax && sx + 1 < wx) {
+                    const float Ln = sv1[e + 1];
+                    if (Lc >= 0.f && Ln >= 0.f) fx = 0.5f * (Lc + Ln) * f.idx2;
+                }
+                if (ay && sy + 1 < wy) {
+                    const float Ln = sv1[e + wx];
+                    if (Lc >= 0.f && Ln >= 0.f) fy = 0.5f * (Lc + Ln) * f.idy2;
+                }
+                sLx[e] = fx;
+                sLy[e] = fy;
+            }
+            __syncthreads();
+            float *a = sv0, *b = sv1;
+            for (int j = 1; j <= kk; j++) {
+                const float tb = s_tb[m0 + j - 1], rd = s_rd[m0 + j - 1];
+                const int jx = ax ? j : 0, jy = ay ? j : 0;
+                const int ux = wx - 2 * jx, uy = wy - 2 * jy;
+                for (int e = threadIdx.x; e < ux * uy; e += blockDim.x) {
+                    const int yy = e / ux;
+                    const int q = (jy + yy) * wx + jx + (e - yy * ux);
+                    const float vc = a[q];
+                    float lap = 0.f;
+                    if (ax) lap += sLx[q] * (a[q + 1] - vc) - sLx[q - 1] * (vc - a[q - 1]);
+                    if (ay) lap += sLy[q] * (a[q + wx] - vc) - sLy[q - wx] * (vc - a[q - wx]);
+                    b[q] = (sT[q] + tb * vc + stV[q] * lap + stI[q]) * rd;
+                }
+                __syncthreads();
+                float *tmp = a;
+                a = b;
+                b = tmp;
+            }
+            for (int e = threadIdx.x; e < tx * ty; e += blockDim.x) {
+                const int yy = e / tx, xx = e - yy * tx;
+                const int gx = ti * tx + xx, gy = tj * ty + yy;
+                if (gx < p.nx && gy < p.ny) vout[gy * p.nx + gx] = a[(yy + hy) * wx + xx + hx];
+            }
+            __syncthreads();  // the region is reloaded by the block's next tile
+        }
+        if (!grid_barrier(sc)) return false;
+        vin = vout;
+        m0 += kk;
+        r++;
+    }
+    vlast = vin;
+    return true;
+}
+
 // temperature relaxation + heat conduction by the local-iteration method
 // (Sec. 3.4, Algorithm 1), cooperative: coefficients -> lambda_max -> P, b_m
-// -> 2P - 2 predictor sweeps -> conservative last sweep + projection
-__global__ void __launch_bounds__(256) k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s, Scalars *sc,
-                                                double dt_host, int trelax_first, int check)
+// -> 2P - 2 predictor sweeps (temporally blocked) -> conservative last sweep
+// + projection
+__global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s,
+                                                         Scalars *sc, double dt_host, int trelax_first, int check)
 {
+    extern __shared__ float smem_lim[];
     __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
     const int n = p.n;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
@@ -197,16 +324,7 @@ __global__ void __launch_bounds__(256) k_heatff(const DevParams p, const FFP f, 
             if (capped) st |= capped;
         }
         const float *vin = s.T0;
-        for (int m = 1; m <= 2 * P - 2; m++) {
-            float *vout = (m & 1) ? s.va : s.vb;
-            const float tb = s_tb[m - 1], rd = s_rd[m - 1];
-            for (int c = t0; c < n; c += nt) {
-                const float Lv = lapf(p, neighbours(p, c), c, vin, s.L, f.idx2, f.idy2);
-                vout[c] = (s.T0[c] + tb * vin[c] + tauf * s.V[c] * (Lv + s.Ia[c])) * rd;
-            }
-            if (!grid_barrier(sc)) return;
-            vin = vout;
-        }
+        if (!lim_rounds(p, f, s, sc, 2 * P - 2, tauf, s_tb, s_rd, smem_lim, vin)) return;
         const bool last = it == nout - 1;
         for (int c = t0; c < n; c += nt) {
             const float dq = tauf * (lapf(p, neighbours(p, c), c, vin, s.L, f.idx2, f.idy2) + s.Ia[c]);
@@ -443,7 +561,9 @@ cudaError_t bulkff_setup(int nsm)
     cudaError_t e = sweepff_setup();
     if (e != cudaSuccess) return e;
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff, 256, 0);
+    e = cudaFuncSetAttribute(k_heatff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIM_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff, HEAT_THREADS, LIM_SMEM);
     if (e != cudaSuccess) return e;
     g_heatff_blocks = b * nsm;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<0>, 256, 0);
@@ -518,8 +638,9 @@ cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *
     FFP ff_ = f;
     void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&hs, (void *)&sc, (void *)&dt_host,
                     (void *)&trelax_first, (void *)&check};
-    return cudaLaunchCooperativeKernel((const void *)k_heatff, dim3(coop_grid(g_heatff_blocks, p.n)), dim3(256), args,
-                                       0, st);
+    const int need = (p.n + HEAT_THREADS - 1) / HEAT_THREADS;
+    return cudaLaunchCooperativeKernel((const void *)k_heatff, dim3(need < g_heatff_blocks ? need : g_heatff_blocks),
+                                       dim3(HEAT_THREADS), args, LIM_SMEM, st);
 }
 
 cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, float2 *U, double *S, Scalars *sc,
