@@ -377,8 +377,11 @@ static int step_once(dim_ctx *c, double *U, StepMarks *mk = nullptr)
 }
 
 // FP32 bulk: one split step on the float-float state *cur, the sweeps
-// alternating between the two FF buffers (same stages as step_once)
-static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth)
+// alternating between the two FF buffers (same stages as step_once).  Ud_in
+// (may be null): the CFL kernel converts this FP64 state into *cur first.
+// Ud_out (may be null): the heat kernel, if the step ends with it, writes the
+// end state there in FP64; *out_done tells whether it did.
+static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud_in, double *Ud_out, bool *out_done)
 {
     const dim_params &h = c->hp;
     const DevParams &p = c->p;
@@ -392,7 +395,9 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth)
     else last = sy ? LAST_SY : LAST_SX;
 
     TRY(reset_accumulators(c));
-    TIMED(c, K_WAVE, dimk::launch_wave_ff(p, f, cur, c->sc, c->stream));
+    if (Ud_in) TIMED(c, K_WAVE, dimk::launch_wave_ff_in(p, f, Ud_in, cur, c->sc, c->stream));
+    else TIMED(c, K_WAVE, dimk::launch_wave_ff(p, f, cur, c->sc, c->stream));
+    *out_done = false;
     if (sx) {
         TIMED(c, K_SWEEP_X, dimk::launch_sweep_ff(p, f, 0, cur, oth, 0.0, c->sc, 1, last == LAST_SX, c->stream));
         float2 *t = cur; cur = oth; oth = t;
@@ -406,24 +411,27 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth)
         if (sy) TIMED(c, K_VISC_Y, dimk::launch_visc_ff(p, f, 1, cur, c->S, c->sc, 0.0, 1, last == LAST_VY, c->stream));
     }
     if (heat) {
-        TIMED(c, K_HEAT, dimk::launch_heat_ff(p, f, cur, c->S, c->sc, 0.0, 1, 1, c->stream));
+        TIMED(c, K_HEAT, dimk::launch_heat_ff(p, f, cur, c->S, c->sc, 0.0, 1, 1, c->stream, Ud_out));
+        *out_done = Ud_out != nullptr;
     } else if (trx) {
         TIMED(c, K_RELAX, dimk::launch_relax_ff(p, f, cur, c->sc, DIM_RELAX_TEMPERATURE, 1, c->stream));
     }
     return DIM_OK;
 }
 
-// FP32 bulk: nsteps steps of the device state U through the FF planes (one
-// conversion in, one out)
+// FP32 bulk: nsteps (>= 1) steps of the device state U through the FF planes:
+// the first step's CFL kernel converts U in, the last step's heat kernel (or a
+// conversion pass, when the step does not end with the heat stage) writes it
+// back
 static int steps_ff(dim_ctx *c, double *U, int nsteps)
 {
     float2 *cur = c->Uf, *oth = ff_other(c);
-    TIMED(c, K_CONVERT, dimk::launch_ff_in(U, cur, state_len(c), c->stream));
+    bool out_done = false;
     for (int s = 0; s < nsteps; s++) {
-        int r = step_once_ff(c, cur, oth);
+        int r = step_once_ff(c, cur, oth, s == 0 ? U : nullptr, s == nsteps - 1 ? U : nullptr, &out_done);
         if (r != DIM_OK) return r;
     }
-    TIMED(c, K_CONVERT, dimk::launch_ff_out(cur, U, state_len(c), c->stream));
+    if (!out_done) TIMED(c, K_CONVERT, dimk::launch_ff_out(cur, U, state_len(c), c->stream));
     return DIM_OK;
 }
 

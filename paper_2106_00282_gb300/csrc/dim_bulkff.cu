@@ -43,8 +43,11 @@ __device__ __forceinline__ float block_dt(const Scalars *sc, double dt_host)
     return s_dt;
 }
 
-// CFL bound (Sec. 3.1) and input check
-__global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f, const float2 *__restrict__ U,
+// CFL bound (Sec. 3.1) and input check.  FROM_D: the state is read from the
+// caller's FP64 planes Ud and written to the FF planes U on the way (the first
+// step of a call), instead of a separate conversion pass.
+template <bool FROM_D>
+__global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f, float2 *U, const double *Ud,
                                                  Scalars *sc)
 {
     const int n = p.n;
@@ -53,7 +56,14 @@ __global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f,
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         ff q[NQ];
 #pragma unroll
-        for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
+        for (int k = 0; k < NQ; k++) {
+            if constexpr (FROM_D) {
+                q[k] = ff_from_d(Ud[k * (size_t)n + c]);
+                st_ff(U, k * (size_t)n + c, q[k]);
+            } else {
+                q[k] = ld_ff(U, k * (size_t)n + c);
+            }
+        }
         st |= ff_check(f, q);
         const ff a1 = ff_sub(ff_one(), q[7]);
         const float p1 = ff_phase_p(f, 0, q[4], a1), p2 = ff_phase_p(f, 1, q[5], q[7]);
@@ -157,33 +167,77 @@ struct HeatFF {
     float2 *Ai;
 };
 
-// Temporally blocked predictor sweeps of Eq. (LIM) for the heat stage.  The
-// grid is cut into tiles of TBX x TBY cells (one line of up to RB - 2 HB cells
-// on a 1D grid).  A round of up to HB sweeps loads each tile with a halo of HB
+// The cells of the grid as (i, j, c), without an integer division per cell:
+// row chunks of blockDim.x cells, one chunk per block iteration (grids at
+// least one block wide), else a grid-stride loop.
+template <class F>
+__device__ __forceinline__ void for_cells(const DevParams &p, F &&fn)
+{
+    if (p.nx >= (int)blockDim.x) {
+        const int nch = (p.nx + blockDim.x - 1) / blockDim.x;
+        const int nw = p.ny * nch;
+        for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+            const int j = w / nch, i = (w - j * nch) * blockDim.x + threadIdx.x;
+            if (i < p.nx) fn(i, j, j * p.nx + i);
+        }
+    } else {
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < p.n; c += gridDim.x * blockDim.x) {
+            const int j = c / p.nx;
+            fn(c - j * p.nx, j, c);
+        }
+    }
+}
+
+// neighbours of cell c = (i, j) (-1: no neighbour across a transmissive wall)
+__device__ __forceinline__ Nb nb_of(const DevParams &p, int i, int j, int c)
+{
+    Nb r;
+    r.xm = r.xp = r.ym = r.yp = -1;
+    if (p.nx > 1) {
+        if (i > 0) r.xm = c - 1;
+        else if (p.bc[0] == DIM_BC_PERIODIC) r.xm = c + p.nx - 1;
+        if (i < p.nx - 1) r.xp = c + 1;
+        else if (p.bc[0] == DIM_BC_PERIODIC) r.xp = c - (p.nx - 1);
+    }
+    if (p.ny > 1) {
+        if (j > 0) r.ym = c - p.nx;
+        else if (p.bc[1] == DIM_BC_PERIODIC) r.ym = c + (p.ny - 1) * p.nx;
+        if (j < p.ny - 1) r.yp = c + p.nx;
+        else if (p.bc[1] == DIM_BC_PERIODIC) r.yp = c - (p.ny - 1) * p.nx;
+    }
+    return r;
+}
+
+// Temporally blocked predictor sweeps of Eq. (LIM) for the heat stage.  A
+// round of up to HB sweeps loads each tile of the grid with a halo of HB
 // cells -- the starting iterate, T0, tau V, tau V Ia and the face
 // coefficients Lam_f / h^2 (zero at transmissive walls) -- into shared memory,
-// sweeps there (sweep j updates the cells at least j cells inside the loaded
-// region, whose inputs the previous sweep left valid), and writes the tile's
-// cells of the last iterate back.  One grid barrier per round instead of one
-// per sweep; the halo cells are swept redundantly (15 % more stencil work with
-// 4 sweeps per round).  Rounds alternate between the two iterate planes, so no
-// block overwrites a plane another block may still read in the same round.
-constexpr int TBX = 64, TBY = 32, HB = 4;
-constexpr int RB = (TBX + 2 * HB) * (TBY + 2 * HB);
+// sweeps there, and writes the tile's cells of the last iterate back.  Each
+// sweep updates the whole region but its outermost ring; after j sweeps the
+// cells at least j cells inside the region are exact (their inputs were), so
+// the tile's cells (HB inside) are exact after HB sweeps.  One grid barrier per
+// round instead of one per sweep; the halo is swept redundantly.  Rounds
+// alternate between the two iterate planes, so no block overwrites a plane
+// another block may still read in the same round.  2D grids: regions of
+// RX x RY cells (tiles of RX - 2 HB by RY - 2 HB) swept by the block's 512
+// threads as 64 x 8; 1D grids: a line of RB cells.
+constexpr int HB = 4, RX = 64, RY = 40, RB = RX * RY;
 constexpr size_t LIM_SMEM = 7 * sizeof(float) * RB;
 constexpr int HEAT_THREADS = 512;
+static_assert(HEAT_THREADS == RX * 8, "the 2D sweep maps the block as 64 x 8 threads");
 
 __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Scalars *sc, int M, float tauf,
                            const float *s_tb, const float *s_rd, float *sm, const float *&vlast)
 {
     float *sv0 = sm, *sv1 = sm + RB, *sT = sm + 2 * RB, *stV = sm + 3 * RB, *stI = sm + 4 * RB;
     float *sLx = sm + 5 * RB, *sLy = sm + 6 * RB;
-    const bool ax = p.nx > 1, ay = p.ny > 1;
-    const int tx = ax && ay ? TBX : (ax ? RB - 2 * HB : 1);
-    const int ty = ax && ay ? TBY : (ay ? RB - 2 * HB : 1);
+    const bool ax = p.nx > 1, ay = p.ny > 1, two = ax && ay;
+    const int wx = two ? RX : (ax ? RB : 1), wy = two ? RY : (ay ? RB : 1);  // region
     const int hx = ax ? HB : 0, hy = ay ? HB : 0;
-    const int wx = tx + 2 * hx, wy = ty + 2 * hy;  // loaded region, at most RB cells
+    const int tx = wx - 2 * hx, ty = wy - 2 * hy;  // tile
     const int ntx = (p.nx + tx - 1) / tx, nty = (p.ny + ty - 1) / ty, ntiles = ntx * nty;
+    // this thread's cells of a region: (sx0 + k * dx_, sy0 + k * dy_)
+    const int lx = threadIdx.x & (RX - 1), ly = threadIdx.x >> 6;
     const float *vin = s.T0;
     int m0 = 0, r = 0;
     while (m0 < M) {
@@ -192,8 +246,8 @@ __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Sc
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const int tj = t / ntx, ti = t - tj * ntx;
             const int gx0 = ti * tx - hx, gy0 = tj * ty - hy;
-            for (int e = threadIdx.x; e < wx * wy; e += blockDim.x) {
-                const int sy = e / wx, sx = e - sy * wx;
+            auto load = [&](int sx, int sy) {
+                const int e = sy * wx + sx;
                 int gx = gx0 + sx, gy = gy0 + sy;
                 bool in = true;
                 if (gx < 0 || gx >= p.nx) {
@@ -216,10 +270,9 @@ __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Sc
                     sv0[e] = sT[e] = stV[e] = stI[e] = 0.f;
                     sv1[e] = -1.f;
                 }
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < wx * wy; e += blockDim.x) {
-                const int sy = e / wx, sx = e - sy * wx;
+            };
+            auto faces = [&](int sx, int sy) {
+                const int e = sy * wx + sx;
                 const float Lc = sv1[e];
                 float fx = 0.f, fy = 0.f;
                 if (ax && sx + 1 < wx) {
@@ -232,31 +285,50 @@ __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Sc
                 }
                 sLx[e] = fx;
                 sLy[e] = fy;
+            };
+            if (two) {
+                for (int sy = ly; sy < RY; sy += 8) load(lx, sy);
+                __syncthreads();
+                for (int sy = ly; sy < RY; sy += 8) faces(lx, sy);
+            } else {
+                for (int e = threadIdx.x; e < RB; e += blockDim.x) load(ax ? e : 0, ax ? 0 : e);
+                __syncthreads();
+                for (int e = threadIdx.x; e < RB; e += blockDim.x) faces(ax ? e : 0, ax ? 0 : e);
             }
             __syncthreads();
             float *a = sv0, *b = sv1;
             for (int j = 1; j <= kk; j++) {
                 const float tb = s_tb[m0 + j - 1], rd = s_rd[m0 + j - 1];
-                const int jx = ax ? j : 0, jy = ay ? j : 0;
-                const int ux = wx - 2 * jx, uy = wy - 2 * jy;
-                for (int e = threadIdx.x; e < ux * uy; e += blockDim.x) {
-                    const int yy = e / ux;
-                    const int q = (jy + yy) * wx + jx + (e - yy * ux);
+                auto cell = [&](int q) {
                     const float vc = a[q];
                     float lap = 0.f;
                     if (ax) lap += sLx[q] * (a[q + 1] - vc) - sLx[q - 1] * (vc - a[q - 1]);
                     if (ay) lap += sLy[q] * (a[q + wx] - vc) - sLy[q - wx] * (vc - a[q - wx]);
                     b[q] = (sT[q] + tb * vc + stV[q] * lap + stI[q]) * rd;
+                };
+                if (two) {
+                    if (lx >= 1 && lx < RX - 1)
+                        for (int sy = 1 + ly; sy < RY - 1; sy += 8) cell(sy * RX + lx);
+                } else {
+                    for (int e = 1 + threadIdx.x; e < RB - 1; e += blockDim.x) cell(e);
                 }
                 __syncthreads();
                 float *tmp = a;
                 a = b;
                 b = tmp;
             }
-            for (int e = threadIdx.x; e < tx * ty; e += blockDim.x) {
-                const int yy = e / tx, xx = e - yy * tx;
-                const int gx = ti * tx + xx, gy = tj * ty + yy;
-                if (gx < p.nx && gy < p.ny) vout[gy * p.nx + gx] = a[(yy + hy) * wx + xx + hx];
+            if (two) {
+                const int gx = ti * tx + lx - HB;
+                if (lx >= HB && lx < RX - HB && gx < p.nx)
+                    for (int sy = HB + ly; sy < RY - HB; sy += 8) {
+                        const int gy = tj * ty + sy - HB;
+                        if (gy < p.ny) vout[gy * p.nx + gx] = a[sy * RX + lx];
+                    }
+            } else {
+                for (int e = threadIdx.x; e < (ax ? tx : ty); e += blockDim.x) {
+                    const int g = (ax ? ti * tx : tj * ty) + e;
+                    if (g < (ax ? p.nx : p.ny)) vout[g] = a[e + HB];
+                }
             }
             __syncthreads();  // the region is reloaded by the block's next tile
         }
@@ -273,8 +345,12 @@ __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Sc
 // (Sec. 3.4, Algorithm 1), cooperative: coefficients -> lambda_max -> P, b_m
 // -> 2P - 2 predictor sweeps (temporally blocked) -> conservative last sweep
 // + projection
+// Ud (may be null): the end state is written there as FP64 planes (all 8)
+// instead of to the FF planes -- the last step of a call, which then needs no
+// separate conversion pass
 __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s,
-                                                         Scalars *sc, double dt_host, int trelax_first, int check)
+                                                         Scalars *sc, double dt_host, int trelax_first, int check,
+                                                         double *Ud)
 {
     extern __shared__ float smem_lim[];
     __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
@@ -314,7 +390,7 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
     for (int it = 0; it < nout; it++) {
         if (!grid_barrier(sc)) return;
         float lm = 0.f;
-        for (int c = t0; c < n; c += nt) lm = fmaxf(lm, gershf(p, neighbours(p, c), c, s.V, s.L, f.idx2, f.idy2));
+        for_cells(p, [&](int i, int j, int c) { lm = fmaxf(lm, gershf(p, nb_of(p, i, j, c), c, s.V, s.L, f.idx2, f.idy2)); });
         block_max_to_f(&sc->lam[it], lm);
         if (!grid_barrier(sc)) return;
         unsigned capped;
@@ -326,8 +402,8 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
         const float *vin = s.T0;
         if (!lim_rounds(p, f, s, sc, 2 * P - 2, tauf, s_tb, s_rd, smem_lim, vin)) return;
         const bool last = it == nout - 1;
-        for (int c = t0; c < n; c += nt) {
-            const float dq = tauf * (lapf(p, neighbours(p, c), c, vin, s.L, f.idx2, f.idy2) + s.Ia[c]);
+        for_cells(p, [&](int i, int j, int c) {
+            const float dq = tauf * (lapf(p, nb_of(p, i, j, c), c, vin, s.L, f.idx2, f.idy2) + s.Ia[c]);
             const ff M1 = ld_ff(U, c), M2 = ld_ff(U, n + (size_t)c);
             const ff E1 = ld_ff(U, 4 * (size_t)n + c), E2 = ld_ff(U, 5 * (size_t)n + c);
             float T;
@@ -342,10 +418,17 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
                 q[5] = E2n;
                 q[6] = ff_add_f(ld_ff(U, 6 * (size_t)n + c), dq);
                 q[7] = a2;
-                st_ff(U, 4 * (size_t)n + c, q[4]);
-                st_ff(U, 5 * (size_t)n + c, q[5]);
-                st_ff(U, 6 * (size_t)n + c, q[6]);
-                st_ff(U, 7 * (size_t)n + c, q[7]);
+                if (Ud) {
+                    q[2] = ld_ff(U, 2 * (size_t)n + c);
+                    q[3] = ld_ff(U, 3 * (size_t)n + c);
+#pragma unroll
+                    for (int k = 0; k < NQ; k++) Ud[k * (size_t)n + c] = ff_to_d(q[k]);
+                } else {
+                    st_ff(U, 4 * (size_t)n + c, q[4]);
+                    st_ff(U, 5 * (size_t)n + c, q[5]);
+                    st_ff(U, 6 * (size_t)n + c, q[6]);
+                    st_ff(U, 7 * (size_t)n + c, q[7]);
+                }
                 if (check) st |= ff_check(f, q) | (r & DIM_ST_NAN);
                 else if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
             } else {
@@ -353,7 +436,7 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
                 s.Ti[c] = T;
                 st_ff(s.Ai, c, a2);
             }
-        }
+        });
         if (!last) {
             if (!grid_barrier(sc)) return;
             for (int c = t0; c < n; c += nt) {
@@ -595,7 +678,15 @@ cudaError_t launch_ff_out(const float2 *F, double *U, size_t m, cudaStream_t s)
 
 cudaError_t launch_wave_ff(const DevParams &p, const FFP &f, const float2 *U, Scalars *sc, cudaStream_t s)
 {
-    k_wave_ff<<<elementwise_grid((size_t)p.n), 256, 0, s>>>(p, f, U, sc);
+    k_wave_ff<false><<<elementwise_grid((size_t)p.n), 256, 0, s>>>(p, f, (float2 *)U, nullptr, sc);
+    return cudaGetLastError();
+}
+
+// the CFL kernel that also converts the caller's FP64 state Ud into the FF planes U
+cudaError_t launch_wave_ff_in(const DevParams &p, const FFP &f, const double *Ud, float2 *U, Scalars *sc,
+                              cudaStream_t s)
+{
+    k_wave_ff<true><<<elementwise_grid((size_t)p.n), 256, 0, s>>>(p, f, U, Ud, sc);
     return cudaGetLastError();
 }
 
@@ -629,7 +720,7 @@ static int coop_grid(int maxb, int n)
 
 // the FP32 planes alias the context's FP64 scratch planes S (two floats per double)
 cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
-                           int trelax_first, int check, cudaStream_t st)
+                           int trelax_first, int check, cudaStream_t st, double *Ud)
 {
     const size_t n = (size_t)p.n;
     float *F = (float *)S;
@@ -637,7 +728,7 @@ cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *
     DevParams pp = p;
     FFP ff_ = f;
     void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&hs, (void *)&sc, (void *)&dt_host,
-                    (void *)&trelax_first, (void *)&check};
+                    (void *)&trelax_first, (void *)&check, (void *)&Ud};
     const int need = (p.n + HEAT_THREADS - 1) / HEAT_THREADS;
     return cudaLaunchCooperativeKernel((const void *)k_heatff, dim3(need < g_heatff_blocks ? need : g_heatff_blocks),
                                        dim3(HEAT_THREADS), args, LIM_SMEM, st);

@@ -25,12 +25,14 @@ FFP ffp_of(const DevParams &p);
 cudaError_t launch_ff_in(const double *U, float2 *F, size_t m, cudaStream_t s);
 cudaError_t launch_ff_out(const float2 *F, double *U, size_t m, cudaStream_t s);
 cudaError_t launch_wave_ff(const DevParams &p, const FFP &f, const float2 *U, Scalars *sc, cudaStream_t s);
+cudaError_t launch_wave_ff_in(const DevParams &p, const FFP &f, const double *Ud, float2 *U, Scalars *sc,
+                              cudaStream_t s);
 cudaError_t launch_sweep_ff(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
                             double dt_host, Scalars *sc, int relax, int check, cudaStream_t s);
 cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars *sc, int which, int check,
                             cudaStream_t s);
 cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
-                           int trelax_first, int check, cudaStream_t st);
+                           int trelax_first, int check, cudaStream_t st, double *Ud = nullptr);
 cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, float2 *U, double *S, Scalars *sc,
                            double dt_host, int relax, int check, cudaStream_t st);
 }  // namespace dimk

@@ -131,3 +131,81 @@ def test_fp32_bulk_full_size(torch_cuda, O, I, oracle_full_size, which):
     e = rel_l1_32(G, Uo, O, wl, wl.params)
     print(f"[fp32] full {which}, {FULL_SIZE_STEPS[which]} steps: rel L1 per field {np.array2string(e, precision=2)}")
     assert np.all(e <= TOL32), e
+
+
+def test_fp32_bulk_stage_calls(torch_cuda, O, I):
+    """The per-stage entry points in FP32-bulk precision (each converts the FP64
+    state to float-float planes, runs the stage, converts back) against the
+    FP64 oracle's stages on the same input: the hyperbolic sweep along x and y
+    with and without the pressure relaxation, both relaxations on states out of
+    equilibrium, the heat-conduction solve and the viscous solves along x and
+    y.  One stage in FP32 bulk stays within 2e-6 relative L1 per field."""
+    from test_oracle_relax import _nonequilibrium_state
+
+    from paper_2106_00282_gb300 import _lib
+    from paper_2106_00282_gb300.api import Solver
+
+    tol = 2e-6
+
+    def solver(wl):
+        p32 = wl.params.replace(precision=1)
+        return Solver(p32, wl.nx, wl.ny, wl.dx, wl.dy)
+
+    def dev(a):
+        return torch_cuda.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    # sweeps on a developed impact flow
+    wl = I.impact(203, 77)
+    Uo = O.step(wl.params, O.from_primitive(wl.params, wl.prim), wl.dx, wl.dy, 3)[0]
+    s = solver(wl)
+    dt = O.dt(wl.params, Uo, wl.dx, wl.dy)
+    for axis in (0, 1):
+        for relax in (False, True):
+            U = dev(Uo)
+            s.hllc_sweep(U, axis, dt, relax)
+            ref, st = O.sweep(wl.params, Uo, wl.dx, wl.dy, axis, dt)
+            if relax:
+                ref, st = O.prelax(wl.params, ref)
+            e = rel_l1_32(U.cpu().numpy(), ref, O, wl, wl.params)
+            print(f"[fp32] sweep axis {axis} relax {relax}: {e.max():.2e}")
+            assert np.all(e <= tol), (axis, relax, e)
+    s.close()
+    # relaxations
+    for params in (I.impact(8, 8).params, I.shock_tube().params):
+        U0 = _nonequilibrium_state(I, params, 5000, 21, dT=0.3, dp=0.3, dE=1e-3)
+        wl = I.Workload("r", 5000, 1, 1.0, 1.0, params, None)
+        s = solver(wl)
+        for which, fn in ((_lib.RELAX_PRESSURE, O.prelax), (_lib.RELAX_TEMPERATURE, O.trelax)):
+            U = dev(U0)
+            s.relax(U, which)
+            ref, st = fn(params, U0)
+            G = U.cpu().numpy()
+            e = np.abs(G - ref).reshape(8, -1).sum(1) / np.maximum(np.abs(ref).reshape(8, -1).sum(1), 1e-300)
+            print(f"[fp32] relax {which}: {e.max():.2e}")
+            assert np.all(e <= tol), (which, e)
+        s.close()
+    # heat conduction and viscous solves
+    wl = I.conduction_disc(n=131, p_min=4, p_max=12)
+    U0 = O.from_primitive(wl.params, wl.prim)
+    s = solver(wl)
+    U = dev(U0)
+    P = s.cheb_parabolic(U, _lib.PARABOLIC_HEAT, 2e-5)
+    ref, st, Po = O.heat(wl.params, U0, wl.dx, wl.dy, 2e-5)
+    assert P == Po
+    e = rel_l1_32(U.cpu().numpy(), ref, O, wl, wl.params)
+    print(f"[fp32] heat P={P}: {e.max():.2e}")
+    assert np.all(e <= tol), e
+    s.close()
+    wl = I.impact(150, 70)
+    wl.params = wl.params.replace(mu=(50.0, 2.0))
+    U0 = O.step(wl.params, O.from_primitive(wl.params, wl.prim), wl.dx, wl.dy, 4)[0]
+    s = solver(wl)
+    for axis in (0, 1):
+        U = dev(U0)
+        P = s.cheb_parabolic(U, _lib.PARABOLIC_VISCOUS_X if axis == 0 else _lib.PARABOLIC_VISCOUS_Y, 2e-7)
+        ref, st, Po = O.viscous(wl.params, U0, wl.dx, wl.dy, axis, 2e-7)
+        assert P == Po
+        e = rel_l1_32(U.cpu().numpy(), ref, O, wl, wl.params)
+        print(f"[fp32] viscous axis {axis} P={P}: {e.max():.2e}")
+        assert np.all(e <= tol), (axis, e)
+    s.close()
