@@ -216,6 +216,12 @@ __device__ __forceinline__ unsigned ff_check(const FFP &f, const ff *q)
     return st;
 }
 
+// Below this minor-phase fraction an FP32 relaxation root is accurate enough:
+// the relaxed pressure moves by ~3e9 Pa per unit error of the fraction, and
+// the FP32 root's error is ~1e-7 of the minor fraction (< 3e-3 Pa here), so
+// the float-float Newton correction runs only in mixed cells.
+constexpr float kNewtonFraction = 1e-5f;
+
 // Pressure relaxation (Sec. 3.3, three steps) of one cell in place.
 // Step (1): with dE_k = -p_I da_k and p_I the relaxed pressure x, the EOS gives
 // a_k(x) - a_k^0 = d_k(x) = a_k^0 (p_k^0 - x) / (g_k (x + pinf_k)); the volume
@@ -252,23 +258,29 @@ __device__ __forceinline__ unsigned ff_prelax(const FFP &f, ff *q)
     }
     const float sq = sqrtf(disc);
     const float x = qb >= 0.f ? __fdividef(qb + sq, 2.f * qa) : __fdividef(2.f * qc, sq - qb);
-    // d_k(x) in FF, their x-derivatives in FP32, one Newton step
-    const ff y1 = ff_add_f(f.pinf_ff[0], x), y2 = ff_add_f(f.pinf_ff[1], x);
-    const ff d1 = ff_div(ff_mul(a1, ff_add_f(P1, -x)), ff_mul(y1, f.g_ff[0]));
-    const ff d2 = ff_div(ff_mul(a2, ff_add_f(P2, -x)), ff_mul(y2, f.g_ff[1]));
-    const float e1 = ff_f(y1), e2 = ff_f(y2);
-    const float dd1 = -__fdividef(A1 * (p1 + f.pinf[0]), f.g[0] * e1 * e1);
-    const float dd2 = -__fdividef(A2 * (p2 + f.pinf[1]), f.g[1] * e2 * e2);
-    const float dx = -__fdividef(ff_f(ff_add(d1, d2)), dd1 + dd2);
     ff a2n, da2;
-    if (A2 <= 0.5f) {
-        da2 = ff_add_f(d2, dd2 * dx);
-        a2n = ff_add(a2, da2);
+    const bool minor2 = A2 <= 0.5f;
+    if (fminf(A1, A2) >= kNewtonFraction) {
+        // d_k(x) in FF, their x-derivatives in FP32, one Newton step
+        const ff y1 = ff_add_f(f.pinf_ff[0], x), y2 = ff_add_f(f.pinf_ff[1], x);
+        const ff d1 = ff_div(ff_mul(a1, ff_add_f(P1, -x)), ff_mul(y1, f.g_ff[0]));
+        const ff d2 = ff_div(ff_mul(a2, ff_add_f(P2, -x)), ff_mul(y2, f.g_ff[1]));
+        const float e1 = ff_f(y1), e2 = ff_f(y2);
+        const float dd1 = -__fdividef(A1 * (p1 + f.pinf[0]), f.g[0] * e1 * e1);
+        const float dd2 = -__fdividef(A2 * (p2 + f.pinf[1]), f.g[1] * e2 * e2);
+        const float dx = -__fdividef(ff_f(ff_add(d1, d2)), dd1 + dd2);
+        if (minor2) {
+            da2 = ff_add_f(d2, dd2 * dx);
+        } else {
+            da2 = ff_neg(ff_add_f(d1, dd1 * dx));
+        }
+    } else if (minor2) {  // a nearly pure cell: the FP32 root and change suffice
+        da2 = ff_of(A2 * __fdividef(p2 - x, f.g[1] * (x + f.pinf[1])));
     } else {
-        const ff da1 = ff_add_f(d1, dd1 * dx);
-        a2n = ff_sub(ff_one(), ff_add(a1, da1));
-        da2 = ff_neg(da1);
+        da2 = ff_of(-A1 * __fdividef(p1 - x, f.g[0] * (x + f.pinf[0])));
     }
+    if (minor2) a2n = ff_add(a2, da2);
+    else a2n = ff_sub(ff_one(), ff_sub(a1, da2));
     const ff a1n = ff_sub(ff_one(), a2n);
     // rho e - E_1 - E_2 with the kinetic energy (rho u)^2 / (2 rho) in FF
     const ff rho = ff_add(q[0], q[1]);
@@ -322,13 +334,18 @@ __device__ __forceinline__ unsigned ff_equilibrium(const FFP &f, ff m1, ff m2, f
     const float sq = sqrtf(disc);
     float y = qb <= 0.f ? __fdividef(sq - qb, 2.f * Cf) : __fdividef(-2.f * qc, qb + sq);
     if (B1 == 0.f) y = __fdividef(ff_f(ff_add(GW1, GW2)), Cf);  // linear: C y = sum G_k C_k W_k
-    // Newton step on F in FF
     const ff Y2 = ff_of(y), Y1 = ff_add_f(f.B1_ff, y);
-    const ff t1 = ff_div(GW1, Y1), t2 = ff_div(GW2, Y2);
-    const float y1f = ff_f(Y1);
-    const float dF = -__fdividef(ff_f(t1), y1f) - __fdividef(ff_f(t2), y);
-    const float dy = -__fdividef(ff_f(ff_sub(ff_add(t1, t2), C)), dF);
-    const ff Yb = ff_add_f(Y2, dy), Ya = ff_add_f(Y1, dy);
+    ff Yb = Y2, Ya = Y1;
+    // Newton step on F in FF, in mixed cells (the minor fraction g_m / (g_1 + g_2)
+    // estimated in FP32 from the root)
+    const float g1e = __fdividef(ff_f(GC1), ff_f(Y1)), g2e = __fdividef(ff_f(GC2), y);
+    if (fminf(g1e, g2e) >= kNewtonFraction * (g1e + g2e)) {
+        const ff t1 = ff_div(GW1, Y1), t2 = ff_div(GW2, Y2);
+        const float dF = -__fdividef(ff_f(t1), ff_f(Y1)) - __fdividef(ff_f(t2), y);
+        const float dy = -__fdividef(ff_f(ff_sub(ff_add(t1, t2), C)), dF);
+        Yb = ff_add_f(Y2, dy);
+        Ya = ff_add_f(Y1, dy);
+    }
     const ff g1 = ff_div(GC1, Ya), g2 = ff_div(GC2, Yb);
     const ff gs = ff_add(g1, g2);
     T = __fdividef(1.f, ff_f(gs));
