@@ -1,4 +1,5 @@
-"""Algorithmic FP64 operations per cell for each kernel of the step.
+"""Algorithmic work per cell for each kernel of the step: FP64 operations
+(FLOP) and state bytes (BYTES).
 
 The algorithmic work of a stage is what the plain FP64 statement of the method
 performs: the oracle run once on an operation-counting scalar type, counting
@@ -20,6 +21,17 @@ per cell                                   1D      2D
 The kernels fuse stages: a sweep kernel applies the pressure relaxation to
 its output, the heat kernel starts with the temperature relaxation, the
 viscous kernel of the last axis ends with the pressure relaxation.
+
+Algorithmic state bytes of one launch, per cell: the conserved planes the
+stage reads once and the planes it changes written once, 8 bytes per value
+(a double, or the pair of floats of the FP32-bulk form); scratch planes and
+re-reads are not algorithmic.  The whole step reads and writes the 8-plane
+state once: 128 B.
+  CFL maximum      reads m1, m2, rho u, rho v, E1, E2, alpha_2      56
+  sweep            reads 8 planes, writes 8                         128
+  viscous, x       reads 8, writes rho u, rho v, E1, E2, rho E      104
+  viscous, y       as x, and alpha_2 (pressure relaxation)          112
+  heat             reads 8, writes E1, E2, rho E, alpha_2            96
 """
 from __future__ import annotations
 
@@ -52,3 +64,12 @@ def per_cell(kernel: str, params, P: int = 1, ndim: int = 2) -> float:
     if kernel == "relax":
         return float(PRELAX)
     raise ValueError(kernel)
+
+
+BYTES = {"wave_max": 56, "sweep_x": 128, "sweep_y": 128, "viscous_x": 104, "viscous_y": 112, "heat": 96,
+         "relax": 96}
+
+
+def bytes_per_cell(kernel: str) -> float:
+    """Algorithmic state bytes per cell of one launch of `kernel`."""
+    return float(BYTES[kernel])
