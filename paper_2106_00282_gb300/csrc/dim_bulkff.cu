@@ -458,13 +458,17 @@ struct ViscFF {
     float *V, *a1, *a2, *u0, *w0, *ua, *ub, *wa, *wb;
 };
 
-// viscous step along AXIS (Sec. 3.2), cooperative: velocities, 1/rho and the
-// volume fractions -> lambda_max -> P, b_m -> 2P - 2 predictor sweeps on
-// (u_n with 4/3 mu, u_t with mu) -> conservative last sweep with the energy
-// updates (+ pressure relaxation)
+// viscous step along AXIS (Sec. 3.2), cooperative: lambda_max from the state
+// -> P, b_m -> (P > 1: velocities, 1/rho and the volume fractions in scratch
+// planes -> 2P - 2 predictor sweeps on u_n with 4/3 mu and u_t with mu) ->
+// conservative last sweep with the energy updates (+ pressure relaxation).
+// With P = 1 (no predictor sweep, u_hat = u^n) the last sweep reads the state
+// directly and no scratch plane is written.  Out of place: the stage reads U
+// and writes all 8 planes of Uo (the last sweep reads neighbours' momenta).
 template <int AXIS>
-__global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, float2 *U, ViscFF s, Scalars *sc,
-                                                double dt_host, int relax, int check)
+__global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, const float2 *__restrict__ U,
+                                                float2 *__restrict__ Uo, ViscFF s, Scalars *sc, double dt_host,
+                                                int relax, int check)
 {
     __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
     constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
@@ -481,17 +485,18 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
     const float mu0 = f.mu[0], mu1 = f.mu[1];
     unsigned st = 0;
 
-    for (int c = t0; c < n; c += nt) {
-        const float rho = ff_f(ld_ff(U, c)) + ff_f(ld_ff(U, n + (size_t)c));
-        const ff a2 = ld_ff(U, 7 * (size_t)n + c);
-        s.V[c] = __fdividef(1.f, rho);
-        s.a2[c] = ff_f(a2);
-        s.a1[c] = ff_f(ff_sub(ff_one(), a2));
-        s.u0[c] = __fdividef(ff_f(ld_ff(U, QN * (size_t)n + c)), rho);
-        s.w0[c] = __fdividef(ff_f(ld_ff(U, QT * (size_t)n + c)), rho);
-    }
-    if (!grid_barrier(sc)) return;
-    auto mu_of = [&](int c) { return s.a1[c] * mu0 + s.a2[c] * mu1; };
+    // cell quantities from the float-float state
+    auto rho_at = [&](int c) { return ff_f(ld_ff(U, c)) + ff_f(ld_ff(U, n + (size_t)c)); };
+    auto alpha_at = [&](int c, float &a1, float &a2) {
+        const ff a = ld_ff(U, 7 * (size_t)n + c);
+        a2 = ff_f(a);
+        a1 = ff_f(ff_sub(ff_one(), a));
+    };
+    auto mu_at = [&](int c) {
+        float a1, a2;
+        alpha_at(c, a1, a2);
+        return a1 * mu0 + a2 * mu1;
+    };
     auto nbs = [&](int c, int &cm, int &cp) {
         const Nb nb = neighbours(p, c);
         cm = AXIS == 0 ? nb.xm : nb.ym;
@@ -501,10 +506,10 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
     for (int c = t0; c < n; c += nt) {
         int cm, cp;
         nbs(c, cm, cp);
-        const float lc = 4.f / 3.f * mu_of(c);
-        const float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_of(cm) + lc) : 0.f;
-        const float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_of(cp)) : 0.f;
-        lm = fmaxf(lm, 2.f * s.V[c] * ((fl + fr) * ih2));
+        const float lc = 4.f / 3.f * mu_at(c);
+        const float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_at(cm) + lc) : 0.f;
+        const float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_at(cp)) : 0.f;
+        lm = fmaxf(lm, 2.f * __fdividef(1.f, rho_at(c)) * ((fl + fr) * ih2));
     }
     block_max_to_f(&sc->lam[SLOT], lm);
     if (!grid_barrier(sc)) return;
@@ -515,48 +520,79 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
         if (capped) st |= capped;
     }
     const float *uin = s.u0, *win = s.w0;
-    for (int m = 1; m <= 2 * P - 2; m++) {
-        float *uo = (m & 1) ? s.ua : s.ub;
-        float *wo = (m & 1) ? s.wa : s.wb;
-        const float tb = s_tb[m - 1], rd = s_rd[m - 1];
+    if (P > 1) {
         for (int c = t0; c < n; c += nt) {
-            int cm, cp;
-            nbs(c, cm, cp);
-            const float mc = mu_of(c);
-            const float mm = cm >= 0 ? 0.5f * (mu_of(cm) + mc) : 0.f;
-            const float mp = cp >= 0 ? 0.5f * (mc + mu_of(cp)) : 0.f;
-            const float uc = uin[c], wc = win[c];
-            const float Lu = (cp >= 0 ? 4.f / 3.f * mp * (uin[cp] - uc) * ih2 : 0.f) -
-                             (cm >= 0 ? 4.f / 3.f * mm * (uc - uin[cm]) * ih2 : 0.f);
-            const float Lw =
-                (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.f) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.f);
-            uo[c] = (s.u0[c] + tb * uc + tauf * s.V[c] * Lu) * rd;
-            wo[c] = (s.w0[c] + tb * wc + tauf * s.V[c] * Lw) * rd;
+            const float rho = rho_at(c);
+            s.V[c] = __fdividef(1.f, rho);
+            alpha_at(c, s.a1[c], s.a2[c]);
+            s.u0[c] = __fdividef(ff_f(ld_ff(U, QN * (size_t)n + c)), rho);
+            s.w0[c] = __fdividef(ff_f(ld_ff(U, QT * (size_t)n + c)), rho);
         }
         if (!grid_barrier(sc)) return;
-        uin = uo;
-        win = wo;
+        auto mu_of = [&](int c) { return s.a1[c] * mu0 + s.a2[c] * mu1; };
+        for (int m = 1; m <= 2 * P - 2; m++) {
+            float *uo = (m & 1) ? s.ua : s.ub;
+            float *wo = (m & 1) ? s.wa : s.wb;
+            const float tb = s_tb[m - 1], rd = s_rd[m - 1];
+            for (int c = t0; c < n; c += nt) {
+                int cm, cp;
+                nbs(c, cm, cp);
+                const float mc = mu_of(c);
+                const float mm = cm >= 0 ? 0.5f * (mu_of(cm) + mc) : 0.f;
+                const float mp = cp >= 0 ? 0.5f * (mc + mu_of(cp)) : 0.f;
+                const float uc = uin[c], wc = win[c];
+                const float Lu = (cp >= 0 ? 4.f / 3.f * mp * (uin[cp] - uc) * ih2 : 0.f) -
+                                 (cm >= 0 ? 4.f / 3.f * mm * (uc - uin[cm]) * ih2 : 0.f);
+                const float Lw =
+                    (cp >= 0 ? mp * (win[cp] - wc) * ih2 : 0.f) - (cm >= 0 ? mm * (wc - win[cm]) * ih2 : 0.f);
+                uo[c] = (s.u0[c] + tb * uc + tauf * s.V[c] * Lu) * rd;
+                wo[c] = (s.w0[c] + tb * wc + tauf * s.V[c] * Lw) * rd;
+            }
+            if (!grid_barrier(sc)) return;
+            uin = uo;
+            win = wo;
+        }
     }
+    // the predicted velocities and volume fractions of a cell: from the planes
+    // (P > 1) or the state (P = 1)
+    auto cell = [&](int c, float &u, float &w, float &a1, float &a2) {
+        if (P > 1) {
+            u = uin[c];
+            w = win[c];
+            a1 = s.a1[c];
+            a2 = s.a2[c];
+        } else {
+            const float rho = rho_at(c);
+            u = __fdividef(ff_f(ld_ff(U, QN * (size_t)n + c)), rho);
+            w = __fdividef(ff_f(ld_ff(U, QT * (size_t)n + c)), rho);
+            alpha_at(c, a1, a2);
+        }
+    };
     for (int c = t0; c < n; c += nt) {
         int cm, cp;
         nbs(c, cm, cp);
-        const float mc = mu_of(c);
+        float uc, wc, a1c, a2c;
+        cell(c, uc, wc, a1c, a2c);
+        const float mc = a1c * mu0 + a2c * mu1;
         float Fn[2], Ft[2], W[2], aF1[2], aF2[2];
 #pragma unroll
         for (int sd = 0; sd < 2; sd++) {
-            const int cl = sd == 0 ? cm : c, cr = sd == 0 ? c : cp;
-            if ((sd == 0 ? cm : cp) < 0) {
+            const int cn = sd == 0 ? cm : cp;
+            if (cn < 0) {
                 Fn[sd] = Ft[sd] = W[sd] = aF1[sd] = aF2[sd] = 0.f;
                 continue;
             }
-            const float lmf = 0.5f * ((sd == 0 ? mu_of(cm) : mc) + (sd == 0 ? mc : mu_of(cp)));
-            Fn[sd] = 4.f / 3.f * lmf * (uin[cr] - uin[cl]) * ih;
-            Ft[sd] = lmf * (win[cr] - win[cl]) * ih;
-            W[sd] = 0.5f * (uin[cl] + uin[cr]) * Fn[sd] + 0.5f * (win[cl] + win[cr]) * Ft[sd];
-            aF1[sd] = 0.5f * (s.a1[cl] + s.a1[cr]);
-            aF2[sd] = 0.5f * (s.a2[cl] + s.a2[cr]);
+            float un, wn, a1n, a2n;
+            cell(cn, un, wn, a1n, a2n);
+            const float lmf = 0.5f * (mc + (a1n * mu0 + a2n * mu1));
+            // face between cl and cr: cl = cn, cr = c on the minus side
+            const float du = sd == 0 ? uc - un : un - uc, dw = sd == 0 ? wc - wn : wn - wc;
+            Fn[sd] = 4.f / 3.f * lmf * du * ih;
+            Ft[sd] = lmf * dw * ih;
+            W[sd] = 0.5f * (un + uc) * Fn[sd] + 0.5f * (wn + wc) * Ft[sd];
+            aF1[sd] = 0.5f * (a1n + a1c);
+            aF2[sd] = 0.5f * (a2n + a2c);
         }
-        const float uh = uin[c], wh = win[c];
         const float ti = tauf * ih;
         ff q[NQ];
 #pragma unroll
@@ -565,9 +601,9 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
         q[QT] = ff_add_f(q[QT], ti * (Ft[1] - Ft[0]));
         q[6] = ff_add_f(q[6], ti * (W[1] - W[0]));
         q[4] = ff_add_f(q[4], ti * ((aF1[1] * W[1] - aF1[0] * W[0]) -
-                                    (uh * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + wh * (aF1[1] * Ft[1] - aF1[0] * Ft[0]))));
+                                    (uc * (aF1[1] * Fn[1] - aF1[0] * Fn[0]) + wc * (aF1[1] * Ft[1] - aF1[0] * Ft[0]))));
         q[5] = ff_add_f(q[5], ti * ((aF2[1] * W[1] - aF2[0] * W[0]) -
-                                    (uh * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wh * (aF2[1] * Ft[1] - aF2[0] * Ft[0]))));
+                                    (uc * (aF2[1] * Fn[1] - aF2[0] * Fn[0]) + wc * (aF2[1] * Ft[1] - aF2[0] * Ft[0]))));
         if (relax) {
             const unsigned r = ff_prelax(f, q);
             if (r & (DIM_ST_NONPHYS | DIM_ST_NOROOT)) st |= DIM_ST_TRANSIENT;
@@ -575,7 +611,7 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
         }
         if (check) st |= ff_check(f, q);
 #pragma unroll
-        for (int k = 2; k < NQ; k++) st_ff(U, k * (size_t)n + c, q[k]);
+        for (int k = 0; k < NQ; k++) st_ff(Uo, k * (size_t)n + c, q[k]);
     }
     flag(sc, st);
 }
@@ -734,15 +770,15 @@ cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *
                                        dim3(HEAT_THREADS), args, LIM_SMEM, st);
 }
 
-cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, float2 *U, double *S, Scalars *sc,
-                           double dt_host, int relax, int check, cudaStream_t st)
+cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, const float2 *U, float2 *Uo, double *S,
+                           Scalars *sc, double dt_host, int relax, int check, cudaStream_t st)
 {
     const size_t n = (size_t)p.n;
     float *F = (float *)S;
     ViscFF vs{F, F + n, F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n, F + 6 * n, F + 7 * n, F + 8 * n};
     DevParams pp = p;
     FFP ff_ = f;
-    void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&vs, (void *)&sc, (void *)&dt_host,
+    void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&Uo, (void *)&vs, (void *)&sc, (void *)&dt_host,
                     (void *)&relax, (void *)&check};
     const void *fn = axis == 0 ? (const void *)k_viscff<0> : (const void *)k_viscff<1>;
     return cudaLaunchCooperativeKernel(fn, dim3(coop_grid(g_viscff_blocks[axis], p.n)), dim3(256), args, 0, st);

@@ -33,8 +33,8 @@ cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars
                             cudaStream_t s);
 cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
                            int trelax_first, int check, cudaStream_t st, double *Ud = nullptr);
-cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, float2 *U, double *S, Scalars *sc,
-                           double dt_host, int relax, int check, cudaStream_t st);
+cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, const float2 *U, float2 *Uo, double *S,
+                           Scalars *sc, double dt_host, int relax, int check, cudaStream_t st);
 }  // namespace dimk
 
 using dimk::DevParams;
