@@ -247,6 +247,7 @@ int dim_init(dim_ctx **out, const dim_params *hp, int nx, int ny, double dx, dou
         return DIM_ECUDA;
     }
     c->ffp = dimk::ffp_of(p);
+    c->lim_tma = p.precision == DIM_PRECISION_FP32_BULK ? dimk::heat_tma_setup(p, c->S, &c->lim) : 0;
     {
         // roots of the Chebyshev polynomials T_P, P = 1..PMAX, in decreasing order
         const double pi = 3.14159265358979323846;
@@ -418,7 +419,8 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud
         }
     }
     if (heat) {
-        TIMED(c, K_HEAT, dimk::launch_heat_ff(p, f, cur, c->S, c->sc, 0.0, 1, 1, c->stream, Ud_out));
+        TIMED(c, K_HEAT,
+              dimk::launch_heat_ff(p, f, cur, c->S, c->sc, 0.0, 1, 1, c->stream, Ud_out, &c->lim, c->lim_tma));
         *out_done = Ud_out != nullptr;
     } else if (trx) {
         TIMED(c, K_RELAX, dimk::launch_relax_ff(p, f, cur, c->sc, DIM_RELAX_TEMPERATURE, 1, c->stream));
@@ -578,7 +580,8 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
     if (kind == DIM_PARABOLIC_HEAT) {
         if (f32) {
             TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
-            TIMED(c, K_HEAT, dimk::launch_heat_ff(c->p, c->ffp, c->Uf, c->S, c->sc, dt, 0, 0, c->stream));
+            TIMED(c, K_HEAT, dimk::launch_heat_ff(c->p, c->ffp, c->Uf, c->S, c->sc, dt, 0, 0, c->stream, nullptr,
+                                                  &c->lim, c->lim_tma));
             TIMED(c, K_CONVERT, dimk::launch_ff_out(c->Uf, U, state_len(c), c->stream));
         } else {
             TIMED(c, K_HEAT, run_heat(c, U, dt, 0, 0));

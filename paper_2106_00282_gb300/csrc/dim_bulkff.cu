@@ -9,6 +9,8 @@
 //         speeds, HLLC; the relaxation roots (in the phase-pressure form of
 //         dim_ff.cuh); viscous and heat coefficients; every Chebyshev sweep.
 // The Chebyshev parameters b_m come from the FP64 root table once per block.
+#include <cudaTypedefs.h>
+
 #include "dim_ff.cuh"
 
 namespace dimk {
@@ -165,7 +167,9 @@ __device__ __forceinline__ int block_schedule(const DevParams &p, double tau, do
 struct HeatFF {
     float *T0, *V, *L, *va, *vb, *Ti, *Ia;
     float2 *Ai;
+    float *C0, *tV;  // T0 + tau V Ia and tau V: the constant terms of a predictor sweep
 };
+
 
 // The cells of the grid as (i, j, c), without an integer division per cell:
 // row chunks of blockDim.x cells, one chunk per block iteration (grids at
@@ -210,93 +214,196 @@ __device__ __forceinline__ Nb nb_of(const DevParams &p, int i, int j, int c)
 
 // Temporally blocked predictor sweeps of Eq. (LIM) for the heat stage.  A
 // round of up to HB sweeps loads each tile of the grid with a halo of HB
-// cells -- the starting iterate, T0, tau V, tau V Ia and the face
-// coefficients Lam_f / h^2 (zero at transmissive walls) -- into shared memory,
-// sweeps there, and writes the tile's cells of the last iterate back.  Each
-// sweep updates the whole region but its outermost ring; after j sweeps the
-// cells at least j cells inside the region are exact (their inputs were), so
-// the tile's cells (HB inside) are exact after HB sweeps.  One grid barrier per
-// round instead of one per sweep; the halo is swept redundantly.  Rounds
-// alternate between the two iterate planes, so no block overwrites a plane
-// another block may still read in the same round.  2D grids: regions of
-// RX x RY cells (tiles of RX - 2 HB by RY - 2 HB) swept by the block's 512
-// threads as 64 x 8; 1D grids: a line of RB cells.
-constexpr int HB = 4, RX = 64, RY = 40, RB = RX * RY;
-constexpr size_t LIM_SMEM = 7 * sizeof(float) * RB;
+// cells -- the starting iterate, C0 = T0 + tau V Ia, tau V and Lam -- into
+// shared memory, forms the face coefficients Lam_f / h^2 (zero across a
+// transmissive wall), sweeps there, and writes the tile's cells of the last
+// iterate back.  Each sweep updates the whole region but its outermost ring;
+// after j sweeps the cells at least j cells inside the region are exact (their
+// inputs were), so the tile's cells (HB inside) are exact after HB sweeps.  One
+// grid barrier per round instead of one per sweep; the halo is swept
+// redundantly.  Rounds alternate between the two iterate planes, so no block
+// overwrites a plane another block may still read in the same round.
+// 2D grids: regions of RX x RY cells (tiles of RX - 2 HB by RY - 2 HB) swept by
+// the block's 512 threads as 64 x 8; 1D grids: a line of RB cells.
+// With transmissive walls and rows of a multiple of 4 floats (16-byte TMA
+// rows and starts), a 2D grid's regions are loaded by the tensor-memory
+// accelerator: four 2D bulk copies per region onto an mbarrier, two region
+// buffers, the next tile's copies issued before the current tile is swept;
+// cells outside the grid arrive as zeros.  Otherwise, and for 1D grids, the
+// threads load the regions (periodic walls wrap).
+constexpr int HB = 4, RX = 64, RY = 36, RB = RX * RY;
+constexpr int NPL = 4;  // planes of a region: iterate, C0, tau V, Lam
+// region buffers: NPL planes x 2 (TMA double buffer), the second iterate, the x and y faces
+constexpr size_t LIM_SMEM = sizeof(float) * RB * (2 * NPL + 3) + 128;
 constexpr int HEAT_THREADS = 512;
 static_assert(HEAT_THREADS == RX * 8, "the 2D sweep maps the block as 64 x 8 threads");
+static_assert((RX - 2 * HB) % 4 == 0 && HB % 4 == 0, "TMA region starts must be multiples of 4 floats");
+constexpr long long kTmaWaitLimit = 1LL << 22;  // polls of an mbarrier before a wait gives up
 
-__device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Scalars *sc, int M, float tauf,
-                           const float *s_tb, const float *s_rd, float *sm, const float *&vlast)
+__device__ __forceinline__ unsigned smem_u32(const void *q) { return (unsigned)__cvta_generic_to_shared(q); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
 {
-    float *sv0 = sm, *sv1 = sm + RB, *sT = sm + 2 * RB, *stV = sm + 3 * RB, *stI = sm + 4 * RB;
-    float *sLx = sm + 5 * RB, *sLy = sm + 6 * RB;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of the given parity to complete
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
+{
+    for (long long i = 0; i < kTmaWaitLimit; i++)
+        if (mbar_test(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, unsigned long long *b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(smem_u32(b))
+        : "memory");
+}
+
+// the descriptors of the planes a round reads (addresses in the kernel's
+// parameter space)
+struct LimMapPtrs {
+    const CUtensorMap *va, *vb, *T0, *C0, *tV, *L;
+};
+
+__device__ __forceinline__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, LimMapPtrs tm,
+                                           bool use_tma, Scalars *sc, int M, const float *s_tb, const float *s_rd,
+                                           float *sm, const float *&vlast)
+{
+    __shared__ __align__(8) unsigned long long s_bar[2];
+    __shared__ int s_fail;
+    float *const base = (float *)(((size_t)sm + 127) & ~(size_t)127);  // TMA destinations: 128-byte aligned
+    // region buffers (v, C0, tau V, Lam) at base and base + NPL RB
+    float *vb = base + 2 * NPL * RB, *sLx = vb + RB, *sLy = sLx + RB;
     const bool ax = p.nx > 1, ay = p.ny > 1, two = ax && ay;
     const int wx = two ? RX : (ax ? RB : 1), wy = two ? RY : (ay ? RB : 1);  // region
     const int hx = ax ? HB : 0, hy = ay ? HB : 0;
     const int tx = wx - 2 * hx, ty = wy - 2 * hy;  // tile
     const int ntx = (p.nx + tx - 1) / tx, nty = (p.ny + ty - 1) / ty, ntiles = ntx * nty;
-    // this thread's cells of a region: (sx0 + k * dx_, sy0 + k * dy_)
     const int lx = threadIdx.x & (RX - 1), ly = threadIdx.x >> 6;
+    const bool per_x = p.bc[0] == DIM_BC_PERIODIC, per_y = p.bc[1] == DIM_BC_PERIODIC;
+    unsigned use0 = 0u, use1 = 0u;  // completed loads per TMA buffer (the mbarrier phase parity)
+    if (use_tma && threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     const float *vin = s.T0;
     int m0 = 0, r = 0;
     while (m0 < M) {
         const int kk = min(HB, M - m0);
         float *vout = (r & 1) ? s.vb : s.va;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const CUtensorMap *vmap = r == 0 ? tm.T0 : ((r & 1) ? tm.va : tm.vb);  // the plane vin is
+        auto issue = [&](int t, int buf) {  // one thread: the four bulk copies of tile t
+            const int tj = t / ntx, ti = t - tj * ntx;
+            const int x0 = ti * tx - HB, y0 = tj * ty - HB;
+            float *d = base + buf * NPL * RB;
+            unsigned long long *bar = buf ? &s_bar[1] : &s_bar[0];
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, (unsigned)(NPL * RB * sizeof(float)));
+            tma_load_2d(d, vmap, x0, y0, bar);
+            tma_load_2d(d + RB, tm.C0, x0, y0, bar);
+            tma_load_2d(d + 2 * RB, tm.tV, x0, y0, bar);
+            tma_load_2d(d + 3 * RB, tm.L, x0, y0, bar);
+        };
+        if (use_tma && threadIdx.x == 0) {
+            // the other blocks' iterate writes (ordered by the grid barrier) before
+            // this round's bulk copies read them
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        }
+        int k = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, k++) {
             const int tj = t / ntx, ti = t - tj * ntx;
             const int gx0 = ti * tx - hx, gy0 = tj * ty - hy;
-            auto load = [&](int sx, int sy) {
-                const int e = sy * wx + sx;
-                int gx = gx0 + sx, gy = gy0 + sy;
-                bool in = true;
-                if (gx < 0 || gx >= p.nx) {
-                    if (p.bc[0] == DIM_BC_PERIODIC) gx = (gx % p.nx + p.nx) % p.nx;
-                    else in = false;
+            const int buf = use_tma ? (k & 1) : 0;
+            float *sv = base + buf * NPL * RB, *sC = sv + RB, *stV = sv + 2 * RB, *sL = sv + 3 * RB;
+            if (use_tma) {
+                const unsigned ub = buf ? use1 : use0, uo = buf ? use0 : use1;
+                if (threadIdx.x == 0) {
+                    const int tn = t + gridDim.x;
+                    s_fail = 0;
+                    if (tn < ntiles) issue(tn, buf ^ 1);  // streams while this tile is swept
+                    if (!mbar_wait(buf ? &s_bar[1] : &s_bar[0], ub & 1u)) s_fail = 1;
                 }
-                if (gy < 0 || gy >= p.ny) {
-                    if (p.bc[1] == DIM_BC_PERIODIC) gy = (gy % p.ny + p.ny) % p.ny;
-                    else in = false;
+                __syncthreads();
+                if (s_fail) {
+                    // give up: flag, let the other buffer's copies land (bounded), leave
+                    if (threadIdx.x == 0) {
+                        atomicOr(&sc->status, DIM_ST_TIMEOUT);
+                        if (t + gridDim.x < ntiles) mbar_wait(buf ? &s_bar[0] : &s_bar[1], uo & 1u);
+                    }
+                    return false;
                 }
-                if (in) {
-                    const int c = gy * p.nx + gx;
-                    const float tv = tauf * s.V[c];
-                    sv0[e] = vin[c];
-                    sT[e] = s.T0[c];
-                    stV[e] = tv;
-                    stI[e] = tv * s.Ia[c];
-                    sv1[e] = s.L[c];
-                } else {  // outside a transmissive wall: no cell, no face (marked by Lam < 0)
-                    sv0[e] = sT[e] = stV[e] = stI[e] = 0.f;
-                    sv1[e] = -1.f;
+                if (buf) use1++;
+                else use0++;
+            } else {
+                auto load = [&](int sx, int sy) {
+                    const int e = sy * wx + sx;
+                    int gx = gx0 + sx, gy = gy0 + sy;
+                    bool in = true;
+                    if (gx < 0 || gx >= p.nx) {
+                        if (per_x) gx = (gx % p.nx + p.nx) % p.nx;
+                        else in = false;
+                    }
+                    if (gy < 0 || gy >= p.ny) {
+                        if (per_y) gy = (gy % p.ny + p.ny) % p.ny;
+                        else in = false;
+                    }
+                    if (in) {
+                        const int c = gy * p.nx + gx;
+                        sv[e] = vin[c];
+                        sC[e] = s.C0[c];
+                        stV[e] = s.tV[c];
+                        sL[e] = s.L[c];
+                    } else {  // outside a transmissive wall: no cell (its faces are zero)
+                        sv[e] = sC[e] = stV[e] = sL[e] = 0.f;
+                    }
+                };
+                if (two) {
+                    for (int sy = ly; sy < RY; sy += 8) load(lx, sy);
+                } else {
+                    for (int e = threadIdx.x; e < RB; e += blockDim.x) load(ax ? e : 0, ax ? 0 : e);
                 }
-            };
+            }
+            __syncthreads();
+            // face coefficients after each cell; zero where either cell lies
+            // beyond a transmissive wall
+            auto inside_x = [&](int sx) { const int g = gx0 + sx; return per_x || (g >= 0 && g < p.nx); };
+            auto inside_y = [&](int sy) { const int g = gy0 + sy; return per_y || (g >= 0 && g < p.ny); };
             auto faces = [&](int sx, int sy) {
                 const int e = sy * wx + sx;
-                const float Lc = sv1[e];
+                const float Lc = sL[e];
+                const bool in = inside_x(sx) && inside_y(sy);
                 float fx = 0.f, fy = 0.f;
-                if (ax && sx + 1 < wx) {
-                    const float Ln = sv1[e + 1];
-                    if (Lc >= 0.f && Ln >= 0.f) fx = 0.5f * (Lc + Ln) * f.idx2;
-                }
-                if (ay && sy + 1 < wy) {
-                    const float Ln = sv1[e + wx];
-                    if (Lc >= 0.f && Ln >= 0.f) fy = 0.5f * (Lc + Ln) * f.idy2;
-                }
+                if (ax && sx + 1 < wx && in && inside_x(sx + 1)) fx = 0.5f * (Lc + sL[e + 1]) * f.idx2;
+                if (ay && sy + 1 < wy && in && inside_y(sy + 1)) fy = 0.5f * (Lc + sL[e + wx]) * f.idy2;
                 sLx[e] = fx;
                 sLy[e] = fy;
             };
             if (two) {
-                for (int sy = ly; sy < RY; sy += 8) load(lx, sy);
-                __syncthreads();
                 for (int sy = ly; sy < RY; sy += 8) faces(lx, sy);
             } else {
-                for (int e = threadIdx.x; e < RB; e += blockDim.x) load(ax ? e : 0, ax ? 0 : e);
-                __syncthreads();
                 for (int e = threadIdx.x; e < RB; e += blockDim.x) faces(ax ? e : 0, ax ? 0 : e);
             }
             __syncthreads();
-            float *a = sv0, *b = sv1;
+            float *a = sv, *b = vb;
             for (int j = 1; j <= kk; j++) {
                 const float tb = s_tb[m0 + j - 1], rd = s_rd[m0 + j - 1];
                 auto cell = [&](int q) {
@@ -304,7 +411,7 @@ __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Sc
                     float lap = 0.f;
                     if (ax) lap += sLx[q] * (a[q + 1] - vc) - sLx[q - 1] * (vc - a[q - 1]);
                     if (ay) lap += sLy[q] * (a[q + wx] - vc) - sLy[q - wx] * (vc - a[q - wx]);
-                    b[q] = (sT[q] + tb * vc + stV[q] * lap + stI[q]) * rd;
+                    b[q] = (sC[q] + tb * vc + stV[q] * lap) * rd;
                 };
                 if (two) {
                     if (lx >= 1 && lx < RX - 1)
@@ -330,7 +437,7 @@ __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Sc
                     if (g < (ax ? p.nx : p.ny)) vout[g] = a[e + HB];
                 }
             }
-            __syncthreads();  // the region is reloaded by the block's next tile
+            __syncthreads();  // the region buffers are refilled for the block's next tiles
         }
         if (!grid_barrier(sc)) return false;
         vin = vout;
@@ -350,7 +457,7 @@ __device__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Sc
 // separate conversion pass
 __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s,
                                                          Scalars *sc, double dt_host, int trelax_first, int check,
-                                                         double *Ud)
+                                                         double *Ud, const __grid_constant__ LimMaps tm, int use_tma)
 {
     extern __shared__ float smem_lim[];
     __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
@@ -385,7 +492,10 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
         s.V[c] = V;
         s.L[c] = L;
         const float a2f = ff_f(a2);
-        s.Ia[c] = ff_f(ff_sub(ff_one(), a2)) * f.src[0] + a2f * f.src[1];
+        const float Ia = ff_f(ff_sub(ff_one(), a2)) * f.src[0] + a2f * f.src[1];
+        s.Ia[c] = Ia;
+        s.tV[c] = tauf * V;
+        s.C0[c] = T + tauf * V * Ia;
     }
     for (int it = 0; it < nout; it++) {
         if (!grid_barrier(sc)) return;
@@ -400,7 +510,8 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
             if (capped) st |= capped;
         }
         const float *vin = s.T0;
-        if (!lim_rounds(p, f, s, sc, 2 * P - 2, tauf, s_tb, s_rd, smem_lim, vin)) return;
+        const LimMapPtrs mp{&tm.va, &tm.vb, &tm.T0, &tm.C0, &tm.tV, &tm.L};
+        if (!lim_rounds(p, f, s, mp, use_tma != 0, sc, 2 * P - 2, s_tb, s_rd, smem_lim, vin)) return;
         const bool last = it == nout - 1;
         for_cells(p, [&](int i, int j, int c) {
             const float dq = tauf * (lapf(p, nb_of(p, i, j, c), c, vin, s.L, f.idx2, f.idy2) + s.Ia[c]);
@@ -446,7 +557,10 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
                 ff_heat_coeffs(f, m1, m2, s.Ti[c], a2, V, L);
                 s.V[c] = V;
                 s.L[c] = L;
-                s.Ia[c] = ff_f(ff_sub(ff_one(), a2)) * f.src[0] + ff_f(a2) * f.src[1];
+                const float Ia = ff_f(ff_sub(ff_one(), a2)) * f.src[0] + ff_f(a2) * f.src[1];
+                s.Ia[c] = Ia;
+                s.tV[c] = tauf * V;
+                s.C0[c] = s.T0[c] + tauf * V * Ia;
             }
         }
     }
@@ -754,17 +868,57 @@ static int coop_grid(int maxb, int n)
     return need < maxb ? need : maxb;
 }
 
-// the FP32 planes alias the context's FP64 scratch planes S (two floats per double)
-cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
-                           int trelax_first, int check, cudaStream_t st, double *Ud)
+// the heat stage's FP32 planes alias the context's FP64 scratch planes S (two
+// floats per double): T0, V, Lam, the two iterates, T_it, Ia, -, alpha_it (a
+// float pair), C0, tau V
+static HeatFF heat_planes(const DevParams &p, double *S)
 {
     const size_t n = (size_t)p.n;
     float *F = (float *)S;
-    HeatFF hs{F, F + n, F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n, F + 6 * n, (float2 *)(F + 8 * n)};
+    return HeatFF{F,         F + n,     F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n,
+                  F + 6 * n, (float2 *)(F + 8 * n), F + 10 * n, F + 11 * n};
+}
+
+// TMA descriptors of the heat planes when the grid allows them: 2D, both walls
+// transmissive (a region beyond a wall arrives as zeros), rows of a multiple
+// of 4 floats (16-byte strides; the regions start at multiples of 4 floats).
+// Returns 1 with the maps filled, 0 when the threads load the regions instead.
+int heat_tma_setup(const DevParams &p, double *S, LimMaps *m)
+{
+    if (p.nx < 2 || p.ny < 2 || p.bc[0] != DIM_BC_TRANSMISSIVE || p.bc[1] != DIM_BC_TRANSMISSIVE || p.nx % 4 != 0)
+        return 0;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return 0;
+    auto encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    const HeatFF h = heat_planes(p, S);
+    const cuuint64_t dim[2] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny};
+    const cuuint64_t stride[1] = {(cuuint64_t)p.nx * sizeof(float)};
+    const cuuint32_t box[2] = {RX, RY}, estr[2] = {1, 1};
+    float *planes[6] = {h.va, h.vb, h.T0, h.C0, h.tV, h.L};
+    CUtensorMap *maps[6] = {&m->va, &m->vb, &m->T0, &m->C0, &m->tV, &m->L};
+    for (int i = 0; i < 6; i++)
+        if (encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, planes[i], dim, stride, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return 0;
+    return 1;
+}
+
+cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
+                           int trelax_first, int check, cudaStream_t st, double *Ud, const LimMaps *tm, int use_tma)
+{
+    HeatFF hs = heat_planes(p, S);
     DevParams pp = p;
     FFP ff_ = f;
-    void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&hs, (void *)&sc, (void *)&dt_host,
-                    (void *)&trelax_first, (void *)&check, (void *)&Ud};
+    LimMaps maps;
+    if (use_tma) maps = *tm;
+    else memset(&maps, 0, sizeof(maps));
+    void *args[] = {(void *)&pp,  (void *)&ff_,          (void *)&U,     (void *)&hs,   (void *)&sc,
+                    (void *)&dt_host, (void *)&trelax_first, (void *)&check, (void *)&Ud, (void *)&maps,
+                    (void *)&use_tma};
     const int need = (p.n + HEAT_THREADS - 1) / HEAT_THREADS;
     return cudaLaunchCooperativeKernel((const void *)k_heatff, dim3(need < g_heatff_blocks ? need : g_heatff_blocks),
                                        dim3(HEAT_THREADS), args, LIM_SMEM, st);

@@ -31,8 +31,9 @@ cudaError_t launch_sweep_ff(const DevParams &p, const FFP &f, int axis, const fl
                             double dt_host, Scalars *sc, int relax, int check, cudaStream_t s);
 cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars *sc, int which, int check,
                             cudaStream_t s);
+int heat_tma_setup(const DevParams &p, double *S, LimMaps *m);
 cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
-                           int trelax_first, int check, cudaStream_t st, double *Ud = nullptr);
+                           int trelax_first, int check, cudaStream_t st, double *Ud, const LimMaps *tm, int use_tma);
 cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, const float2 *U, float2 *Uo, double *S,
                            Scalars *sc, double dt_host, int relax, int check, cudaStream_t st);
 }  // namespace dimk
@@ -71,6 +72,8 @@ struct dim_ctx {
     // steps run; U2 holds the other buffer of the sweeps' ping-pong
     float2 *Uf;
     dimk::FFP ffp;
+    dimk::LimMaps lim;  // TMA descriptors of the heat stage's planes (lim_tma != 0)
+    int lim_tma;
     Scalars *sc;
     int device;
     // profiling

@@ -21,6 +21,8 @@
 // Every operation below is an explicit round-to-nearest intrinsic, so the
 // compiler neither contracts nor reorders them.
 #pragma once
+#include <cuda.h>
+
 #include "dim_device.cuh"
 
 namespace dimk {
@@ -163,6 +165,12 @@ struct FFP {
     float cfl, idx, idy, idx2, idy2;
     float inv_Tref, k_exp;
     int k_pow;
+};
+
+// TMA descriptors of the FP32-bulk heat stage's planes (2D, nx x ny floats):
+// the two iterate planes, T0, C0 = T0 + tau V Ia, tau V and Lam
+struct LimMaps {
+    CUtensorMap va, vb, T0, C0, tV, L;
 };
 
 // ---------------------------------------------------------------------------
