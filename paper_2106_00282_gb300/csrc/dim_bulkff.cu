@@ -217,79 +217,46 @@ __device__ __forceinline__ Nb nb_of(const DevParams &p, int i, int j, int c)
 // cells -- the starting iterate, C0 = T0 + tau V Ia, tau V and Lam -- into
 // shared memory, forms the face coefficients Lam_f / h^2 (zero across a
 // transmissive wall), sweeps there, and writes the tile's cells of the last
-// iterate back.  Each sweep updates the whole region but its outermost ring;
-// after j sweeps the cells at least j cells inside the region are exact (their
-// inputs were), so the tile's cells (HB inside) are exact after HB sweeps.  One
-// grid barrier per round instead of one per sweep; the halo is swept
-// redundantly.  Rounds alternate between the two iterate planes, so no block
-// overwrites a plane another block may still read in the same round.
-// 2D grids: regions of RX x RY cells (tiles of RX - 2 HB by RY - 2 HB) swept by
-// the block's 512 threads as 64 x 8; 1D grids: a line of RB cells.
-// With transmissive walls and rows of a multiple of 4 floats (16-byte TMA
-// rows and starts), a 2D grid's regions are loaded by the tensor-memory
-// accelerator: four 2D bulk copies per region onto an mbarrier, two region
-// buffers, the next tile's copies issued before the current tile is swept;
-// cells outside the grid arrive as zeros.  Otherwise, and for 1D grids, the
-// threads load the regions (periodic walls wrap).
+// iterate back.  After j sweeps the cells at least j cells inside the region
+// are exact (their inputs were), so the tile's cells (HB inside) are exact
+// after HB sweeps.  One grid barrier per round instead of one per sweep; the
+// halo is swept redundantly.  Rounds alternate between the two iterate
+// planes, so no block overwrites a plane another block may still read in the
+// same round.
+//
+// Two forms:
+//  - lim_rounds: thread loads (periodic walls wrap).  2D grids: regions of
+//    RX x RY cells swept by a block's 512 threads as 64 x 8; 1D grids: a line
+//    of RB cells.
+//  - lim_rounds_tma: 2D grids with transmissive walls and rows of a multiple
+//    of 4 floats.  Regions of TX x TY = 128 x 34 cells arrive by four 2D bulk
+//    tensor copies onto an mbarrier (cells outside the grid as zeros), two
+//    region buffers, the next tile's copies issued before the current tile is
+//    swept.  A block of 1024 threads: warp w sweeps region row w + 1, each
+//    lane 4 adjacent cells with 16-byte shared loads, the x neighbours across
+//    lanes by warp shuffles; sweep j updates the rows j .. TY - 1 - j only.
 constexpr int HB = 4, RX = 64, RY = 36, RB = RX * RY;
-constexpr int NPL = 4;  // planes of a region: iterate, C0, tau V, Lam
-// region buffers: NPL planes x 2 (TMA double buffer), the second iterate, the x and y faces
-constexpr size_t LIM_SMEM = sizeof(float) * RB * (2 * NPL + 3) + 128;
+// region planes: iterate, C0, tau V, Lam, the second iterate, the x and y faces
+constexpr size_t LIM_SMEM = sizeof(float) * RB * 7;
 constexpr int HEAT_THREADS = 512;
 static_assert(HEAT_THREADS == RX * 8, "the 2D sweep maps the block as 64 x 8 threads");
-static_assert((RX - 2 * HB) % 4 == 0 && HB % 4 == 0, "TMA region starts must be multiples of 4 floats");
-constexpr long long kTmaWaitLimit = 1LL << 22;  // polls of an mbarrier before a wait gives up
 
-__device__ __forceinline__ unsigned smem_u32(const void *q) { return (unsigned)__cvta_generic_to_shared(q); }
-__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait for the phase of the given parity to complete
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
-{
-    for (long long i = 0; i < kTmaWaitLimit; i++)
-        if (mbar_test(b, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, unsigned long long *b)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(smem_u32(b))
-        : "memory");
-}
+constexpr int TX = 128, TY = 34, TB = TX * TY;
+constexpr int NPL = 4;  // planes of a TMA region: iterate, C0, tau V, Lam
+// two TMA region buffers, the second iterate, the x and y faces
+constexpr size_t LIM_SMEM_TMA = sizeof(float) * TB * (2 * NPL + 3) + 128;
+constexpr int HEAT_THREADS_TMA = 1024;
+static_assert(HEAT_THREADS_TMA / 32 == TY - 2 && TX == 32 * 4, "one warp per inner region row, 4 cells per lane");
+static_assert((TX - 2 * HB) % 4 == 0 && HB % 4 == 0, "TMA region starts must be multiples of 4 floats");
+static_assert((TB * sizeof(float)) % 128 == 0, "TMA destinations stay 128-byte aligned");
+// clock cycles an mbarrier wait polls before it gives up (~0.25 s at 2 GHz; each
+// try_wait may suspend the thread, so the bound is on time, not on polls)
+constexpr long long kTmaWaitClocks = 500000000LL;
 
-// the descriptors of the planes a round reads (addresses in the kernel's
-// parameter space)
-struct LimMapPtrs {
-    const CUtensorMap *va, *vb, *T0, *C0, *tV, *L;
-};
-
-__device__ __forceinline__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, LimMapPtrs tm,
-                                           bool use_tma, Scalars *sc, int M, const float *s_tb, const float *s_rd,
-                                           float *sm, const float *&vlast)
+__device__ __forceinline__ bool lim_rounds(const DevParams &p, const FFP &f, const HeatFF &s, Scalars *sc, int M,
+                                           const float *s_tb, const float *s_rd, float *sm, const float *&vlast)
 {
-    __shared__ __align__(8) unsigned long long s_bar[2];
-    __shared__ int s_fail;
-    float *const base = (float *)(((size_t)sm + 127) & ~(size_t)127);  // TMA destinations: 128-byte aligned
-    // region buffers (v, C0, tau V, Lam) at base and base + NPL RB
-    float *vb = base + 2 * NPL * RB, *sLx = vb + RB, *sLy = sLx + RB;
+    float *sv = sm, *sC = sv + RB, *stV = sC + RB, *sL = stV + RB, *vb = sL + RB, *sLx = vb + RB, *sLy = sLx + RB;
     const bool ax = p.nx > 1, ay = p.ny > 1, two = ax && ay;
     const int wx = two ? RX : (ax ? RB : 1), wy = two ? RY : (ay ? RB : 1);  // region
     const int hx = ax ? HB : 0, hy = ay ? HB : 0;
@@ -297,90 +264,40 @@ __device__ __forceinline__ bool lim_rounds(const DevParams &p, const FFP &f, con
     const int ntx = (p.nx + tx - 1) / tx, nty = (p.ny + ty - 1) / ty, ntiles = ntx * nty;
     const int lx = threadIdx.x & (RX - 1), ly = threadIdx.x >> 6;
     const bool per_x = p.bc[0] == DIM_BC_PERIODIC, per_y = p.bc[1] == DIM_BC_PERIODIC;
-    unsigned use0 = 0u, use1 = 0u;  // completed loads per TMA buffer (the mbarrier phase parity)
-    if (use_tma && threadIdx.x == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
     const float *vin = s.T0;
     int m0 = 0, r = 0;
     while (m0 < M) {
         const int kk = min(HB, M - m0);
         float *vout = (r & 1) ? s.vb : s.va;
-        const CUtensorMap *vmap = r == 0 ? tm.T0 : ((r & 1) ? tm.va : tm.vb);  // the plane vin is
-        auto issue = [&](int t, int buf) {  // one thread: the four bulk copies of tile t
-            const int tj = t / ntx, ti = t - tj * ntx;
-            const int x0 = ti * tx - HB, y0 = tj * ty - HB;
-            float *d = base + buf * NPL * RB;
-            unsigned long long *bar = buf ? &s_bar[1] : &s_bar[0];
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(bar, (unsigned)(NPL * RB * sizeof(float)));
-            tma_load_2d(d, vmap, x0, y0, bar);
-            tma_load_2d(d + RB, tm.C0, x0, y0, bar);
-            tma_load_2d(d + 2 * RB, tm.tV, x0, y0, bar);
-            tma_load_2d(d + 3 * RB, tm.L, x0, y0, bar);
-        };
-        if (use_tma && threadIdx.x == 0) {
-            // the other blocks' iterate writes (ordered by the grid barrier) before
-            // this round's bulk copies read them
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-        }
-        int k = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, k++) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const int tj = t / ntx, ti = t - tj * ntx;
             const int gx0 = ti * tx - hx, gy0 = tj * ty - hy;
-            const int buf = use_tma ? (k & 1) : 0;
-            float *sv = base + buf * NPL * RB, *sC = sv + RB, *stV = sv + 2 * RB, *sL = sv + 3 * RB;
-            if (use_tma) {
-                const unsigned ub = buf ? use1 : use0, uo = buf ? use0 : use1;
-                if (threadIdx.x == 0) {
-                    const int tn = t + gridDim.x;
-                    s_fail = 0;
-                    if (tn < ntiles) issue(tn, buf ^ 1);  // streams while this tile is swept
-                    if (!mbar_wait(buf ? &s_bar[1] : &s_bar[0], ub & 1u)) s_fail = 1;
+            auto load = [&](int sx, int sy) {
+                const int e = sy * wx + sx;
+                int gx = gx0 + sx, gy = gy0 + sy;
+                bool in = true;
+                if (gx < 0 || gx >= p.nx) {
+                    if (per_x) gx = (gx % p.nx + p.nx) % p.nx;
+                    else in = false;
                 }
-                __syncthreads();
-                if (s_fail) {
-                    // give up: flag, let the other buffer's copies land (bounded), leave
-                    if (threadIdx.x == 0) {
-                        atomicOr(&sc->status, DIM_ST_TIMEOUT);
-                        if (t + gridDim.x < ntiles) mbar_wait(buf ? &s_bar[0] : &s_bar[1], uo & 1u);
-                    }
-                    return false;
+                if (gy < 0 || gy >= p.ny) {
+                    if (per_y) gy = (gy % p.ny + p.ny) % p.ny;
+                    else in = false;
                 }
-                if (buf) use1++;
-                else use0++;
+                if (in) {
+                    const int c = gy * p.nx + gx;
+                    sv[e] = vin[c];
+                    sC[e] = s.C0[c];
+                    stV[e] = s.tV[c];
+                    sL[e] = s.L[c];
+                } else {  // outside a transmissive wall: no cell (its faces are zero)
+                    sv[e] = sC[e] = stV[e] = sL[e] = 0.f;
+                }
+            };
+            if (two) {
+                for (int sy = ly; sy < RY; sy += 8) load(lx, sy);
             } else {
-                auto load = [&](int sx, int sy) {
-                    const int e = sy * wx + sx;
-                    int gx = gx0 + sx, gy = gy0 + sy;
-                    bool in = true;
-                    if (gx < 0 || gx >= p.nx) {
-                        if (per_x) gx = (gx % p.nx + p.nx) % p.nx;
-                        else in = false;
-                    }
-                    if (gy < 0 || gy >= p.ny) {
-                        if (per_y) gy = (gy % p.ny + p.ny) % p.ny;
-                        else in = false;
-                    }
-                    if (in) {
-                        const int c = gy * p.nx + gx;
-                        sv[e] = vin[c];
-                        sC[e] = s.C0[c];
-                        stV[e] = s.tV[c];
-                        sL[e] = s.L[c];
-                    } else {  // outside a transmissive wall: no cell (its faces are zero)
-                        sv[e] = sC[e] = stV[e] = sL[e] = 0.f;
-                    }
-                };
-                if (two) {
-                    for (int sy = ly; sy < RY; sy += 8) load(lx, sy);
-                } else {
-                    for (int e = threadIdx.x; e < RB; e += blockDim.x) load(ax ? e : 0, ax ? 0 : e);
-                }
+                for (int e = threadIdx.x; e < RB; e += blockDim.x) load(ax ? e : 0, ax ? 0 : e);
             }
             __syncthreads();
             // face coefficients after each cell; zero where either cell lies
@@ -437,6 +354,219 @@ __device__ __forceinline__ bool lim_rounds(const DevParams &p, const FFP &f, con
                     if (g < (ax ? p.nx : p.ny)) vout[g] = a[e + HB];
                 }
             }
+            __syncthreads();  // the region buffers are refilled for the block's next tile
+        }
+        if (!grid_barrier(sc)) return false;
+        vin = vout;
+        m0 += kk;
+        r++;
+    }
+    vlast = vin;
+    return true;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *q) { return (unsigned)__cvta_generic_to_shared(q); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of the given parity to complete
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(b, parity))
+        if (clock64() - t0 > kTmaWaitClocks) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, unsigned long long *b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(smem_u32(b))
+        : "memory");
+}
+
+// the descriptors of the planes a round reads (addresses in the kernel's
+// parameter space)
+struct LimMapPtrs {
+    const CUtensorMap *va, *vb, *T0, *C0, *tV, *L;
+};
+
+__device__ __forceinline__ float4 lds4(const float *q) { return *reinterpret_cast<const float4 *>(q); }
+__device__ __forceinline__ void sts4(float *q, float4 v) { *reinterpret_cast<float4 *>(q) = v; }
+
+__device__ __forceinline__ bool lim_rounds_tma(const DevParams &p, const FFP &f, const HeatFF &s, LimMapPtrs tm,
+                                               Scalars *sc, int M, const float *s_tb, const float *s_rd, float *sm,
+                                               const float *&vlast)
+{
+    __shared__ __align__(8) unsigned long long s_bar[2];
+    __shared__ int s_fail;
+    constexpr unsigned FULL = 0xffffffffu;
+    float *const base = (float *)(((size_t)sm + 127) & ~(size_t)127);  // TMA destinations: 128-byte aligned
+    // region buffers (v, C0, tau V, Lam) at base and base + NPL TB
+    float *const vb = base + 2 * NPL * TB, *const sLx = vb + TB, *const sLy = sLx + TB;
+    constexpr int tx = TX - 2 * HB, ty = TY - 2 * HB;  // tile
+    const int ntx = (p.nx + tx - 1) / tx, nty = (p.ny + ty - 1) / ty, ntiles = ntx * nty;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cx = 4 * lane;  // the lane's first column in the region
+    const float idx2 = f.idx2, idy2 = f.idy2;
+    unsigned use0 = 0u, use1 = 0u;  // completed loads per buffer (the mbarrier phase parity)
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const float *vin = s.T0;
+    int m0 = 0, r = 0;
+    while (m0 < M) {
+        const int kk = min(HB, M - m0);
+        float *vout = (r & 1) ? s.vb : s.va;
+        const CUtensorMap *vmap = r == 0 ? tm.T0 : ((r & 1) ? tm.va : tm.vb);  // the plane vin is
+        auto issue = [&](int t, int buf) {  // one thread: the four bulk copies of tile t
+            const int tj = t / ntx, ti = t - tj * ntx;
+            const int x0 = ti * tx - HB, y0 = tj * ty - HB;
+            float *d = base + buf * NPL * TB;
+            unsigned long long *bar = buf ? &s_bar[1] : &s_bar[0];
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, (unsigned)(NPL * TB * sizeof(float)));
+            tma_load_2d(d, vmap, x0, y0, bar);
+            tma_load_2d(d + TB, tm.C0, x0, y0, bar);
+            tma_load_2d(d + 2 * TB, tm.tV, x0, y0, bar);
+            tma_load_2d(d + 3 * TB, tm.L, x0, y0, bar);
+        };
+        if (threadIdx.x == 0) {
+            // the other blocks' iterate writes (ordered by the grid barrier) before
+            // this round's bulk copies read them
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        }
+        int k = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, k++) {
+            const int tj = t / ntx, ti = t - tj * ntx;
+            const int gx0 = ti * tx - HB, gy0 = tj * ty - HB;
+            const int buf = k & 1;
+            float *const sv = base + buf * NPL * TB, *const sC = sv + TB, *const stV = sv + 2 * TB,
+                         *const sL = sv + 3 * TB;
+            {
+                const unsigned ub = buf ? use1 : use0, uo = buf ? use0 : use1;
+                if (threadIdx.x == 0) {
+                    const int tn = t + gridDim.x;
+                    s_fail = 0;
+                    if (tn < ntiles) issue(tn, buf ^ 1);  // streams while this tile is swept
+                    if (!mbar_wait(buf ? &s_bar[1] : &s_bar[0], ub & 1u)) s_fail = 1;
+                }
+                __syncthreads();
+                if (s_fail) {
+                    // give up: flag, let the other buffer's copies land (bounded), leave
+                    if (threadIdx.x == 0) {
+                        atomicOr(&sc->status, DIM_ST_TIMEOUT);
+                        if (t + gridDim.x < ntiles) mbar_wait(buf ? &s_bar[0] : &s_bar[1], uo & 1u);
+                    }
+                    return false;
+                }
+                if (buf) use1++;
+                else use0++;
+            }
+            // face coefficients after each cell (x: columns 0..126, y: rows 0..32),
+            // zero where either cell lies beyond a transmissive wall
+            const bool edge = gx0 < 0 || gy0 < 0 || gx0 + TX > p.nx || gy0 + TY > p.ny;
+            for (int ry = w; ry < TY; ry += 32) {
+                const int q = ry * TX + cx;
+                const float4 Lc = lds4(sL + q);
+                const float Le = __shfl_down_sync(FULL, Lc.x, 1);
+                float4 fx = make_float4(0.5f * (Lc.x + Lc.y) * idx2, 0.5f * (Lc.y + Lc.z) * idx2,
+                                        0.5f * (Lc.z + Lc.w) * idx2, lane < 31 ? 0.5f * (Lc.w + Le) * idx2 : 0.f);
+                float4 fy = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ry + 1 < TY) {
+                    const float4 Ld = lds4(sL + q + TX);
+                    fy = make_float4(0.5f * (Lc.x + Ld.x) * idy2, 0.5f * (Lc.y + Ld.y) * idy2,
+                                     0.5f * (Lc.z + Ld.z) * idy2, 0.5f * (Lc.w + Ld.w) * idy2);
+                }
+                if (edge) {
+                    const int gy = gy0 + ry, gx = gx0 + cx;
+                    const bool row_in = gy >= 0 && gy < p.ny, down_in = gy + 1 < p.ny;
+                    auto in_x = [&](int g) { return g >= 0 && g < p.nx; };
+                    if (!(row_in && in_x(gx) && in_x(gx + 1))) fx.x = 0.f;
+                    if (!(row_in && in_x(gx + 1) && in_x(gx + 2))) fx.y = 0.f;
+                    if (!(row_in && in_x(gx + 2) && in_x(gx + 3))) fx.z = 0.f;
+                    if (!(row_in && in_x(gx + 3) && in_x(gx + 4))) fx.w = 0.f;
+                    if (!(row_in && down_in)) fy = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!in_x(gx)) fy.x = 0.f;
+                    if (!in_x(gx + 1)) fy.y = 0.f;
+                    if (!in_x(gx + 2)) fy.z = 0.f;
+                    if (!in_x(gx + 3)) fy.w = 0.f;
+                }
+                sts4(sLx + q, fx);
+                sts4(sLy + q, fy);
+            }
+            __syncthreads();
+            float *a = sv, *b = vb;
+            const int ry = w + 1, q = ry * TX + cx;
+            for (int j = 1; j <= kk; j++) {
+                if (ry >= j && ry <= TY - 1 - j) {  // warp-uniform
+                    const float tb = s_tb[m0 + j - 1], rd = s_rd[m0 + j - 1];
+                    const float4 c = lds4(a + q), Lx = lds4(sLx + q);
+                    // x neighbours of the lane's first and last cells; the region's
+                    // columns 0 and TX - 1 are never exact, so lanes 0 and 31 take
+                    // any finite value there
+                    const float aw = __shfl_up_sync(FULL, c.w, 1), ae = __shfl_down_sync(FULL, c.x, 1);
+                    // (every lane takes part in each shuffle; lane 0's west face is set after)
+                    const float fwl = __shfl_up_sync(FULL, Lx.w, 1);
+                    const float fw = lane > 0 ? fwl : 0.f;
+                    float4 l;  // the Laplacian: x faces, the face above, the face below
+                    l.x = Lx.x * (c.y - c.x) - fw * (c.x - aw);
+                    l.y = Lx.y * (c.z - c.y) - Lx.x * (c.y - c.x);
+                    l.z = Lx.z * (c.w - c.z) - Lx.y * (c.z - c.y);
+                    l.w = Lx.w * (ae - c.w) - Lx.z * (c.w - c.z);
+                    {
+                        const float4 u = lds4(a + q - TX), Lu = lds4(sLy + q - TX);
+                        l.x -= Lu.x * (c.x - u.x);
+                        l.y -= Lu.y * (c.y - u.y);
+                        l.z -= Lu.z * (c.z - u.z);
+                        l.w -= Lu.w * (c.w - u.w);
+                    }
+                    {
+                        const float4 d = lds4(a + q + TX), Ly = lds4(sLy + q);
+                        l.x += Ly.x * (d.x - c.x);
+                        l.y += Ly.y * (d.y - c.y);
+                        l.z += Ly.z * (d.z - c.z);
+                        l.w += Ly.w * (d.w - c.w);
+                    }
+                    const float4 C = lds4(sC + q), V = lds4(stV + q);
+                    float4 o;
+                    o.x = (C.x + tb * c.x + V.x * l.x) * rd;
+                    o.y = (C.y + tb * c.y + V.y * l.y) * rd;
+                    o.z = (C.z + tb * c.z + V.z * l.z) * rd;
+                    o.w = (C.w + tb * c.w + V.w * l.w) * rd;
+                    sts4(b + q, o);
+                }
+                __syncthreads();
+                float *tmp = a;
+                a = b;
+                b = tmp;
+            }
+            // the tile: rows HB .. TY - 1 - HB, columns HB .. TX - 1 - HB (lanes 1..30)
+            if (ry >= HB && ry < TY - HB && lane >= 1 && lane < 31) {
+                const int gx = gx0 + cx, gy = gy0 + ry;
+                if (gx < p.nx && gy < p.ny)
+                    *reinterpret_cast<float4 *>(vout + (size_t)gy * p.nx + gx) = lds4(a + q);
+            }
             __syncthreads();  // the region buffers are refilled for the block's next tiles
         }
         if (!grid_barrier(sc)) return false;
@@ -455,9 +585,12 @@ __device__ __forceinline__ bool lim_rounds(const DevParams &p, const FFP &f, con
 // Ud (may be null): the end state is written there as FP64 planes (all 8)
 // instead of to the FF planes -- the last step of a call, which then needs no
 // separate conversion pass
-__global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s,
-                                                         Scalars *sc, double dt_host, int trelax_first, int check,
-                                                         double *Ud, const __grid_constant__ LimMaps tm, int use_tma)
+// TMA: the rounds of lim_rounds_tma (blocks of HEAT_THREADS_TMA threads), else
+// those of lim_rounds (HEAT_THREADS)
+template <bool TMA>
+__global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
+    k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s, Scalars *sc, double dt_host, int trelax_first,
+             int check, double *Ud, const __grid_constant__ LimMaps tm)
 {
     extern __shared__ float smem_lim[];
     __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
@@ -510,8 +643,12 @@ __global__ void __launch_bounds__(HEAT_THREADS) k_heatff(const DevParams p, cons
             if (capped) st |= capped;
         }
         const float *vin = s.T0;
-        const LimMapPtrs mp{&tm.va, &tm.vb, &tm.T0, &tm.C0, &tm.tV, &tm.L};
-        if (!lim_rounds(p, f, s, mp, use_tma != 0, sc, 2 * P - 2, s_tb, s_rd, smem_lim, vin)) return;
+        if constexpr (TMA) {
+            const LimMapPtrs mp{&tm.va, &tm.vb, &tm.T0, &tm.C0, &tm.tV, &tm.L};
+            if (!lim_rounds_tma(p, f, s, mp, sc, 2 * P - 2, s_tb, s_rd, smem_lim, vin)) return;
+        } else {
+            if (!lim_rounds(p, f, s, sc, 2 * P - 2, s_tb, s_rd, smem_lim, vin)) return;
+        }
         const bool last = it == nout - 1;
         for_cells(p, [&](int i, int j, int c) {
             const float dq = tauf * (lapf(p, nb_of(p, i, j, c), c, vin, s.L, f.idx2, f.idy2) + s.Ia[c]);
@@ -736,7 +873,7 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
 constexpr int SXF_TN = 128, SXF_TL = 1;
 constexpr int SYF_TN = 32, SYF_TL = 8;
 
-static int g_heatff_blocks = 0, g_viscff_blocks[2] = {0, 0};
+static int g_heatff_blocks[2] = {0, 0}, g_viscff_blocks[2] = {0, 0};
 
 static ff host_split(double x)
 {
@@ -794,11 +931,16 @@ cudaError_t bulkff_setup(int nsm)
     cudaError_t e = sweepff_setup();
     if (e != cudaSuccess) return e;
     int b = 0;
-    e = cudaFuncSetAttribute(k_heatff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIM_SMEM);
+    e = cudaFuncSetAttribute(k_heatff<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIM_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff, HEAT_THREADS, LIM_SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff<false>, HEAT_THREADS, LIM_SMEM);
     if (e != cudaSuccess) return e;
-    g_heatff_blocks = b * nsm;
+    g_heatff_blocks[0] = b * nsm;
+    e = cudaFuncSetAttribute(k_heatff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIM_SMEM_TMA);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff<true>, HEAT_THREADS_TMA, LIM_SMEM_TMA);
+    if (e != cudaSuccess) return e;
+    g_heatff_blocks[1] = b * nsm;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<0>, 256, 0);
     if (e != cudaSuccess) return e;
     g_viscff_blocks[0] = b * nsm;
@@ -896,7 +1038,7 @@ int heat_tma_setup(const DevParams &p, double *S, LimMaps *m)
     const HeatFF h = heat_planes(p, S);
     const cuuint64_t dim[2] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny};
     const cuuint64_t stride[1] = {(cuuint64_t)p.nx * sizeof(float)};
-    const cuuint32_t box[2] = {RX, RY}, estr[2] = {1, 1};
+    const cuuint32_t box[2] = {TX, TY}, estr[2] = {1, 1};
     float *planes[6] = {h.va, h.vb, h.T0, h.C0, h.tV, h.L};
     CUtensorMap *maps[6] = {&m->va, &m->vb, &m->T0, &m->C0, &m->tV, &m->L};
     for (int i = 0; i < 6; i++)
@@ -916,12 +1058,13 @@ cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *
     LimMaps maps;
     if (use_tma) maps = *tm;
     else memset(&maps, 0, sizeof(maps));
-    void *args[] = {(void *)&pp,  (void *)&ff_,          (void *)&U,     (void *)&hs,   (void *)&sc,
-                    (void *)&dt_host, (void *)&trelax_first, (void *)&check, (void *)&Ud, (void *)&maps,
-                    (void *)&use_tma};
-    const int need = (p.n + HEAT_THREADS - 1) / HEAT_THREADS;
-    return cudaLaunchCooperativeKernel((const void *)k_heatff, dim3(need < g_heatff_blocks ? need : g_heatff_blocks),
-                                       dim3(HEAT_THREADS), args, LIM_SMEM, st);
+    void *args[] = {(void *)&pp,      (void *)&ff_,          (void *)&U,     (void *)&hs, (void *)&sc,
+                    (void *)&dt_host, (void *)&trelax_first, (void *)&check, (void *)&Ud, (void *)&maps};
+    const int threads = use_tma ? HEAT_THREADS_TMA : HEAT_THREADS, maxb = g_heatff_blocks[use_tma ? 1 : 0];
+    const int need = (p.n + threads - 1) / threads;
+    return cudaLaunchCooperativeKernel(use_tma ? (const void *)k_heatff<true> : (const void *)k_heatff<false>,
+                                       dim3(need < maxb ? need : maxb), dim3(threads), args,
+                                       use_tma ? LIM_SMEM_TMA : LIM_SMEM, st);
 }
 
 cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, const float2 *U, float2 *Uo, double *S,

@@ -66,6 +66,10 @@ CASES = {
     "overbee_impact": lambda I: _with(I.impact(160, 80), limiter=I.LIMITER_OVERBEE),
     "heat_source": lambda I: _with(I.shock_tube(n=400), src=(1e12, 1e10)),
     "spitzer_like": lambda I: I.conduction_disc(n=96, k_exp=2.5),
+    # the heat stage's blocked rounds with thread loads: periodic walls, and rows
+    # not a multiple of 4 floats (the transmissive 2D cases above load by TMA)
+    "conduction_periodic_96": lambda I: _with(I.conduction_disc(n=96), bc=(I.BC_PERIODIC, I.BC_PERIODIC)),
+    "conduction_98": lambda I: I.conduction_disc(n=98),
 }
 
 
