@@ -410,11 +410,13 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud
     if (vis) {
         if (sx) {
             TIMED(c, K_VISC_X,
-                  dimk::launch_visc_ff(p, f, 0, cur, oth, c->S, c->sc, 0.0, !sy, last == LAST_VX, c->stream));
+                  dimk::launch_visc_ff(p, f, 0, cur, oth, c->S, c->sc, 0.0, !sy, last == LAST_VX, sy ? 1 : 0,
+                                       c->stream));
             float2 *t = cur; cur = oth; oth = t;
         }
         if (sy) {
-            TIMED(c, K_VISC_Y, dimk::launch_visc_ff(p, f, 1, cur, oth, c->S, c->sc, 0.0, 1, last == LAST_VY, c->stream));
+            TIMED(c, K_VISC_Y, dimk::launch_visc_ff(p, f, 1, cur, oth, c->S, c->sc, 0.0, 1, last == LAST_VY,
+                                                    sx ? 2 : 0, c->stream));
             float2 *t = cur; cur = oth; oth = t;
         }
     }
@@ -596,7 +598,7 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
         if (f32) {
             TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
             TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y,
-                  dimk::launch_visc_ff(c->p, c->ffp, axis, c->Uf, ff_other(c), c->S, c->sc, dt, 0, 0, c->stream));
+                  dimk::launch_visc_ff(c->p, c->ffp, axis, c->Uf, ff_other(c), c->S, c->sc, dt, 0, 0, 0, c->stream));
             TIMED(c, K_CONVERT, dimk::launch_ff_out(ff_other(c), U, state_len(c), c->stream));
         } else {
             TIMED(c, axis == 0 ? K_VISC_X : K_VISC_Y, run_visc(c, axis, U, dt, 0, 0));

@@ -45,6 +45,18 @@ __device__ __forceinline__ float block_dt(const Scalars *sc, double dt_host)
     return s_dt;
 }
 
+// L2 prefetch of elements [i0, i1) of a plane (one thread; a bulk prefetch,
+// fire and forget).  The range is widened to 16-byte boundaries, which stays
+// inside the allocation: every plane set here (the FF state, the scratch) ends
+// on a 16-byte boundary or is followed by another plane.
+template <class T>
+__device__ __forceinline__ void l2_prefetch(const T *plane, size_t i0, size_t i1)
+{
+    if (i1 <= i0) return;
+    const size_t a = (size_t)(plane + i0) & ~(size_t)15, e = ((size_t)(plane + i1) + 15) & ~(size_t)15;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+
 // CFL bound (Sec. 3.1) and input check.  FROM_D: the state is read from the
 // caller's FP64 planes Ud and written to the FF planes U on the way (the first
 // step of a call), instead of a separate conversion pass.
@@ -174,18 +186,31 @@ struct HeatFF {
 // The cells of the grid as (i, j, c), without an integer division per cell:
 // row chunks of blockDim.x cells, one chunk per block iteration (grids at
 // least one block wide), else a grid-stride loop.
-template <class F>
-__device__ __forceinline__ void for_cells(const DevParams &p, F &&fn)
+// pf(c0, c1), when given, runs on thread 0 at the start of each chunk with the
+// cells [c0, c1) of the block's next chunk (for L2 prefetches).
+struct NoPf {
+    __device__ void operator()(int, int) const {}
+};
+template <class F, class PF = NoPf>
+__device__ __forceinline__ void for_cells(const DevParams &p, F &&fn, PF pf = PF())
 {
     if (p.nx >= (int)blockDim.x) {
         const int nch = (p.nx + blockDim.x - 1) / blockDim.x;
         const int nw = p.ny * nch;
         for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+            if (threadIdx.x == 0 && w + (int)gridDim.x < nw) {
+                const int wn = w + gridDim.x, jn = wn / nch, in = (wn - jn * nch) * blockDim.x;
+                pf(jn * p.nx + in, jn * p.nx + min(in + (int)blockDim.x, p.nx));
+            }
             const int j = w / nch, i = (w - j * nch) * blockDim.x + threadIdx.x;
             if (i < p.nx) fn(i, j, j * p.nx + i);
         }
     } else {
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < p.n; c += gridDim.x * blockDim.x) {
+            if (threadIdx.x == 0) {
+                const int cn = c + gridDim.x * blockDim.x;
+                if (cn < p.n) pf(cn, min(cn + (int)blockDim.x, p.n));
+            }
             const int j = c / p.nx;
             fn(c - j * p.nx, j, c);
         }
@@ -605,6 +630,14 @@ __global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
     unsigned st = 0;
 
     for (int c = t0; c < n; c += nt) {
+        if (threadIdx.x == 0 && c + nt < n) {  // the block's next chunk of the planes read here
+            const size_t c0 = (size_t)c + nt, c1 = min(c0 + blockDim.x, (size_t)n);
+            l2_prefetch(U, c0, c1);
+            l2_prefetch(U + n, c0, c1);
+            l2_prefetch(U + 4 * (size_t)n, c0, c1);
+            l2_prefetch(U + 5 * (size_t)n, c0, c1);
+            l2_prefetch(U + 7 * (size_t)n, c0, c1);
+        }
         const ff M1 = ld_ff(U, c), M2 = ld_ff(U, n + (size_t)c);
         const float m1 = ff_f(M1), m2 = ff_f(M2);
         ff E1 = ld_ff(U, 4 * (size_t)n + c), E2 = ld_ff(U, 5 * (size_t)n + c), a2 = ld_ff(U, 7 * (size_t)n + c);
@@ -684,6 +717,19 @@ __global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
                 s.Ti[c] = T;
                 st_ff(s.Ai, c, a2);
             }
+        }, [&](int c0, int c1) {  // the planes of the block's next chunk
+            l2_prefetch(U, c0, c1);
+            l2_prefetch(U + n, c0, c1);
+            l2_prefetch(U + 4 * (size_t)n, c0, c1);
+            l2_prefetch(U + 5 * (size_t)n, c0, c1);
+            l2_prefetch(U + 6 * (size_t)n, c0, c1);
+            if (last && Ud) {
+                l2_prefetch(U + 2 * (size_t)n, c0, c1);
+                l2_prefetch(U + 3 * (size_t)n, c0, c1);
+            }
+            l2_prefetch(s.Ia, c0, c1);
+            l2_prefetch(vin, c0, c1);
+            l2_prefetch(s.L, c0, c1);
         });
         if (!last) {
             if (!grid_barrier(sc)) return;
@@ -719,7 +765,7 @@ struct ViscFF {
 template <int AXIS>
 __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, const float2 *__restrict__ U,
                                                 float2 *__restrict__ Uo, ViscFF s, Scalars *sc, double dt_host,
-                                                int relax, int check)
+                                                int relax, int check, int lam_mode)
 {
     __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
     constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
@@ -753,17 +799,37 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
         cm = AXIS == 0 ? nb.xm : nb.ym;
         cp = AXIS == 0 ? nb.xp : nb.yp;
     };
-    float lm = 0.f;
-    for (int c = t0; c < n; c += nt) {
-        int cm, cp;
-        nbs(c, cm, cp);
-        const float lc = 4.f / 3.f * mu_at(c);
-        const float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_at(cm) + lc) : 0.f;
-        const float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_at(cp)) : 0.f;
-        lm = fmaxf(lm, 2.f * __fdividef(1.f, rho_at(c)) * ((fl + fr) * ih2));
+    if (lam_mode != 2) {
+        // lambda_max of this axis; lam_mode 1: also that of the other axis, whose
+        // solve follows on a state with the same densities and fractions
+        constexpr int OSLOT = AXIS == 0 ? LAM_VY : LAM_VX;
+        const float ih2o = AXIS == 0 ? f.idy2 : f.idx2;
+        float lm = 0.f, lmo = 0.f;
+        for (int c = t0; c < n; c += nt) {
+            if (threadIdx.x == 0 && c + nt < n) {  // the block's next chunk of m_1, m_2, alpha_2
+                const size_t c0 = (size_t)c + nt, c1 = min(c0 + blockDim.x, (size_t)n);
+                l2_prefetch(U, c0, c1);
+                l2_prefetch(U + n, c0, c1);
+                l2_prefetch(U + 7 * (size_t)n, c0, c1);
+            }
+            const Nb nb = neighbours(p, c);
+            const int cm = AXIS == 0 ? nb.xm : nb.ym, cp = AXIS == 0 ? nb.xp : nb.yp;
+            const float lc = 4.f / 3.f * mu_at(c);
+            const float ir = __fdividef(1.f, rho_at(c));
+            const float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_at(cm) + lc) : 0.f;
+            const float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_at(cp)) : 0.f;
+            lm = fmaxf(lm, 2.f * ir * ((fl + fr) * ih2));
+            if (lam_mode == 1) {
+                const int om = AXIS == 0 ? nb.ym : nb.xm, op = AXIS == 0 ? nb.yp : nb.xp;
+                const float gl = om >= 0 ? 0.5f * (4.f / 3.f * mu_at(om) + lc) : 0.f;
+                const float gr = op >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_at(op)) : 0.f;
+                lmo = fmaxf(lmo, 2.f * ir * ((gl + gr) * ih2o));
+            }
+        }
+        block_max_to_f(&sc->lam[SLOT], lm);
+        if (lam_mode == 1) block_max_to_f(&sc->lam[OSLOT], lmo);
+        if (!grid_barrier(sc)) return;
     }
-    block_max_to_f(&sc->lam[SLOT], lm);
-    if (!grid_barrier(sc)) return;
     unsigned capped;
     const int P = block_schedule(p, tau, read_acc(&sc->lam[SLOT]), true, s_tb, s_rd, capped);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -820,10 +886,27 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
         }
     };
     for (int c = t0; c < n; c += nt) {
+        if (threadIdx.x == 0 && c + nt < n) {  // the block's next chunk of the state
+            const size_t c0 = (size_t)c + nt, c1 = min(c0 + blockDim.x, (size_t)n);
+#pragma unroll
+            for (int k = 0; k < NQ; k++) l2_prefetch(U + k * (size_t)n, c0, c1);
+        }
         int cm, cp;
         nbs(c, cm, cp);
+        // the cell's state first (one round trip), its velocities and fractions from it
+        ff q[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
         float uc, wc, a1c, a2c;
-        cell(c, uc, wc, a1c, a2c);
+        if (P > 1) {
+            cell(c, uc, wc, a1c, a2c);
+        } else {
+            const float rho = ff_f(q[0]) + ff_f(q[1]);
+            uc = __fdividef(ff_f(q[QN]), rho);
+            wc = __fdividef(ff_f(q[QT]), rho);
+            a2c = ff_f(q[7]);
+            a1c = ff_f(ff_sub(ff_one(), q[7]));
+        }
         const float mc = a1c * mu0 + a2c * mu1;
         float Fn[2], Ft[2], W[2], aF1[2], aF2[2];
 #pragma unroll
@@ -845,9 +928,6 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
             aF2[sd] = 0.5f * (a2n + a2c);
         }
         const float ti = tauf * ih;
-        ff q[NQ];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
         q[QN] = ff_add_f(q[QN], ti * (Fn[1] - Fn[0]));
         q[QT] = ff_add_f(q[QT], ti * (Ft[1] - Ft[0]));
         q[6] = ff_add_f(q[6], ti * (W[1] - W[0]));
@@ -1068,15 +1148,15 @@ cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *
 }
 
 cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, const float2 *U, float2 *Uo, double *S,
-                           Scalars *sc, double dt_host, int relax, int check, cudaStream_t st)
+                           Scalars *sc, double dt_host, int relax, int check, int lam_mode, cudaStream_t st)
 {
     const size_t n = (size_t)p.n;
     float *F = (float *)S;
     ViscFF vs{F, F + n, F + 2 * n, F + 3 * n, F + 4 * n, F + 5 * n, F + 6 * n, F + 7 * n, F + 8 * n};
     DevParams pp = p;
     FFP ff_ = f;
-    void *args[] = {(void *)&pp, (void *)&ff_, (void *)&U, (void *)&Uo, (void *)&vs, (void *)&sc, (void *)&dt_host,
-                    (void *)&relax, (void *)&check};
+    void *args[] = {(void *)&pp,      (void *)&ff_,   (void *)&U,     (void *)&Uo,      (void *)&vs,
+                    (void *)&sc,      (void *)&dt_host, (void *)&relax, (void *)&check, (void *)&lam_mode};
     const void *fn = axis == 0 ? (const void *)k_viscff<0> : (const void *)k_viscff<1>;
     return cudaLaunchCooperativeKernel(fn, dim3(coop_grid(g_viscff_blocks[axis], p.n)), dim3(256), args, 0, st);
 }
