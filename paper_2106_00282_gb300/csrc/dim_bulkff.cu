@@ -269,11 +269,11 @@ static_assert(HEAT_THREADS == RX * 8, "the 2D sweep maps the block as 64 x 8 thr
 constexpr int TX = 128, TY = 34, TB = TX * TY;
 constexpr int NPL = 4;  // planes of a TMA region: iterate, C0, tau V, Lam
 // two TMA region buffers, the second iterate, the x and y faces
-constexpr size_t LIM_SMEM_TMA = sizeof(float) * TB * (2 * NPL + 3) + 128;
+constexpr size_t LIM_SMEM_TMA = sizeof(float) * TB * (2 * NPL + 3) + 128;  // + the alignment slack
 constexpr int HEAT_THREADS_TMA = 1024;
 static_assert(HEAT_THREADS_TMA / 32 == TY - 2 && TX == 32 * 4, "one warp per inner region row, 4 cells per lane");
 static_assert((TX - 2 * HB) % 4 == 0 && HB % 4 == 0, "TMA region starts must be multiples of 4 floats");
-static_assert((TB * sizeof(float)) % 128 == 0, "TMA destinations stay 128-byte aligned");
+static_assert((TB * sizeof(float)) % 128 == 0, "region planes keep the 128-byte alignment of TMA destinations");
 // clock cycles an mbarrier wait polls before it gives up (~0.25 s at 2 GHz; each
 // try_wait may suspend the thread, so the bound is on time, not on polls)
 constexpr long long kTmaWaitClocks = 500000000LL;
@@ -442,8 +442,12 @@ __device__ __forceinline__ bool lim_rounds_tma(const DevParams &p, const FFP &f,
     __shared__ __align__(8) unsigned long long s_bar[2];
     __shared__ int s_fail;
     constexpr unsigned FULL = 0xffffffffu;
-    float *const base = (float *)(((size_t)sm + 127) & ~(size_t)127);  // TMA destinations: 128-byte aligned
-    // region buffers (v, C0, tau V, Lam) at base and base + NPL TB
+    // region buffers (v, C0, tau V, Lam) at base and base + NPL TB.  Bulk tensor
+    // copies write 128-byte aligned shared destinations: base is the first such
+    // address of the dynamic array, formed as an element offset so that every
+    // region pointer stays derived from the shared array (the accesses compile
+    // to shared-memory instructions)
+    float *const base = sm + ((128u - (smem_u32(sm) & 127u)) & 127u) / sizeof(float);
     float *const vb = base + 2 * NPL * TB, *const sLx = vb + TB, *const sLy = sLx + TB;
     constexpr int tx = TX - 2 * HB, ty = TY - 2 * HB;  // tile
     const int ntx = (p.nx + tx - 1) / tx, nty = (p.ny + ty - 1) / ty, ntiles = ntx * nty;
@@ -451,6 +455,10 @@ __device__ __forceinline__ bool lim_rounds_tma(const DevParams &p, const FFP &f,
     const int cx = 4 * lane;  // the lane's first column in the region
     const float idx2 = f.idx2, idy2 = f.idy2;
     unsigned use0 = 0u, use1 = 0u;  // completed loads per buffer (the mbarrier phase parity)
+    if (smem_u32(base) & 127u) {  // not expected: flag and leave before any copy
+        if (threadIdx.x == 0) atomicOr(&sc->status, DIM_ST_TIMEOUT);
+        return false;
+    }
     if (threadIdx.x == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
