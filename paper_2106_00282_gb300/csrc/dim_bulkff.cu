@@ -268,8 +268,8 @@ static_assert(HEAT_THREADS == RX * 8, "the 2D sweep maps the block as 64 x 8 thr
 
 constexpr int TX = 128, TY = 34, TB = TX * TY;
 constexpr int NPL = 4;  // planes of a TMA region: iterate, C0, tau V, Lam
-// two TMA region buffers, the second iterate, the x and y faces
-constexpr size_t LIM_SMEM_TMA = sizeof(float) * TB * (2 * NPL + 3) + 128;  // + the alignment slack
+// two TMA region buffers and the second iterate
+constexpr size_t LIM_SMEM_TMA = sizeof(float) * TB * (2 * NPL + 1) + 128;  // + the alignment slack
 constexpr int HEAT_THREADS_TMA = 1024;
 static_assert(HEAT_THREADS_TMA / 32 == TY - 2 && TX == 32 * 4, "one warp per inner region row, 4 cells per lane");
 static_assert((TX - 2 * HB) % 4 == 0 && HB % 4 == 0, "TMA region starts must be multiples of 4 floats");
@@ -448,7 +448,7 @@ __device__ __forceinline__ bool lim_rounds_tma(const DevParams &p, const FFP &f,
     // region pointer stays derived from the shared array (the accesses compile
     // to shared-memory instructions)
     float *const base = sm + ((128u - (smem_u32(sm) & 127u)) & 127u) / sizeof(float);
-    float *const vb = base + 2 * NPL * TB, *const sLx = vb + TB, *const sLy = sLx + TB;
+    float *const vb = base + 2 * NPL * TB;
     constexpr int tx = TX - 2 * HB, ty = TY - 2 * HB;  // tile
     const int ntx = (p.nx + tx - 1) / tx, nty = (p.ny + ty - 1) / ty, ntiles = ntx * nty;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -516,89 +516,90 @@ __device__ __forceinline__ bool lim_rounds_tma(const DevParams &p, const FFP &f,
                 if (buf) use1++;
                 else use0++;
             }
-            // face coefficients after each cell (x: columns 0..126, y: rows 0..32),
-            // zero where either cell lies beyond a transmissive wall
-            const bool edge = gx0 < 0 || gy0 < 0 || gx0 + TX > p.nx || gy0 + TY > p.ny;
-            for (int ry = w; ry < TY; ry += 32) {
-                const int q = ry * TX + cx;
-                const float4 Lc = lds4(sL + q);
-                const float Le = __shfl_down_sync(FULL, Lc.x, 1);
-                float4 fx = make_float4(0.5f * (Lc.x + Lc.y) * idx2, 0.5f * (Lc.y + Lc.z) * idx2,
-                                        0.5f * (Lc.z + Lc.w) * idx2, lane < 31 ? 0.5f * (Lc.w + Le) * idx2 : 0.f);
-                float4 fy = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ry + 1 < TY) {
-                    const float4 Ld = lds4(sL + q + TX);
-                    fy = make_float4(0.5f * (Lc.x + Ld.x) * idy2, 0.5f * (Lc.y + Ld.y) * idy2,
-                                     0.5f * (Lc.z + Ld.z) * idy2, 0.5f * (Lc.w + Ld.w) * idy2);
-                }
-                if (edge) {
-                    const int gy = gy0 + ry, gx = gx0 + cx;
-                    const bool row_in = gy >= 0 && gy < p.ny, down_in = gy + 1 < p.ny;
-                    auto in_x = [&](int g) { return g >= 0 && g < p.nx; };
-                    if (!(row_in && in_x(gx) && in_x(gx + 1))) fx.x = 0.f;
-                    if (!(row_in && in_x(gx + 1) && in_x(gx + 2))) fx.y = 0.f;
-                    if (!(row_in && in_x(gx + 2) && in_x(gx + 3))) fx.z = 0.f;
-                    if (!(row_in && in_x(gx + 3) && in_x(gx + 4))) fx.w = 0.f;
-                    if (!(row_in && down_in)) fy = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (!in_x(gx)) fy.x = 0.f;
-                    if (!in_x(gx + 1)) fy.y = 0.f;
-                    if (!in_x(gx + 2)) fy.z = 0.f;
-                    if (!in_x(gx + 3)) fy.w = 0.f;
-                }
-                sts4(sLx + q, fx);
-                sts4(sLy + q, fy);
-            }
-            __syncthreads();
-            float *a = sv, *b = vb;
+            // Warp w owns region row ry = w + 1 for all sweeps of the tile: its face
+            // coefficients (x faces after each of its cells, the y faces above and
+            // below), C0, tau V and its current iterate stay in registers, so a
+            // sweep reads only the rows above and below from shared memory and
+            // writes its own row.  Faces are zero where either cell lies beyond a
+            // transmissive wall.
             const int ry = w + 1, q = ry * TX + cx;
-            for (int j = 1; j <= kk; j++) {
-                if (ry >= j && ry <= TY - 1 - j) {  // warp-uniform
-                    const float tb = s_tb[m0 + j - 1], rd = s_rd[m0 + j - 1];
-                    const float4 c = lds4(a + q), Lx = lds4(sLx + q);
-                    // x neighbours of the lane's first and last cells; the region's
-                    // columns 0 and TX - 1 are never exact, so lanes 0 and 31 take
-                    // any finite value there
-                    const float aw = __shfl_up_sync(FULL, c.w, 1), ae = __shfl_down_sync(FULL, c.x, 1);
-                    // (every lane takes part in each shuffle; lane 0's west face is set after)
-                    const float fwl = __shfl_up_sync(FULL, Lx.w, 1);
-                    const float fw = lane > 0 ? fwl : 0.f;
-                    float4 l;  // the Laplacian: x faces, the face above, the face below
-                    l.x = Lx.x * (c.y - c.x) - fw * (c.x - aw);
-                    l.y = Lx.y * (c.z - c.y) - Lx.x * (c.y - c.x);
-                    l.z = Lx.z * (c.w - c.z) - Lx.y * (c.z - c.y);
-                    l.w = Lx.w * (ae - c.w) - Lx.z * (c.w - c.z);
-                    {
-                        const float4 u = lds4(a + q - TX), Lu = lds4(sLy + q - TX);
-                        l.x -= Lu.x * (c.x - u.x);
-                        l.y -= Lu.y * (c.y - u.y);
-                        l.z -= Lu.z * (c.z - u.z);
-                        l.w -= Lu.w * (c.w - u.w);
-                    }
-                    {
-                        const float4 d = lds4(a + q + TX), Ly = lds4(sLy + q);
-                        l.x += Ly.x * (d.x - c.x);
-                        l.y += Ly.y * (d.y - c.y);
-                        l.z += Ly.z * (d.z - c.z);
-                        l.w += Ly.w * (d.w - c.w);
-                    }
-                    const float4 C = lds4(sC + q), V = lds4(stV + q);
-                    float4 o;
-                    o.x = (C.x + tb * c.x + V.x * l.x) * rd;
-                    o.y = (C.y + tb * c.y + V.y * l.y) * rd;
-                    o.z = (C.z + tb * c.z + V.z * l.z) * rd;
-                    o.w = (C.w + tb * c.w + V.w * l.w) * rd;
-                    sts4(b + q, o);
+            float4 Lx, Ly, Lu;  // faces: x (after each cell), y below, y above, times 1/h^2
+            {
+                const float4 Lc = lds4(sL + q), Ld = lds4(sL + q + TX), La = lds4(sL + q - TX);
+                const float Le = __shfl_down_sync(FULL, Lc.x, 1);
+                Lx = make_float4(0.5f * (Lc.x + Lc.y) * idx2, 0.5f * (Lc.y + Lc.z) * idx2, 0.5f * (Lc.z + Lc.w) * idx2,
+                                 lane < 31 ? 0.5f * (Lc.w + Le) * idx2 : 0.f);
+                Ly = make_float4(0.5f * (Lc.x + Ld.x) * idy2, 0.5f * (Lc.y + Ld.y) * idy2, 0.5f * (Lc.z + Ld.z) * idy2,
+                                 0.5f * (Lc.w + Ld.w) * idy2);
+                Lu = make_float4(0.5f * (La.x + Lc.x) * idy2, 0.5f * (La.y + Lc.y) * idy2, 0.5f * (La.z + Lc.z) * idy2,
+                                 0.5f * (La.w + Lc.w) * idy2);
+                if (gx0 < 0 || gy0 < 0 || gx0 + TX > p.nx || gy0 + TY > p.ny) {  // a region that crosses a wall
+                    const int gy = gy0 + ry, gx = gx0 + cx;
+                    auto in_x = [&](int g) { return g >= 0 && g < p.nx; };
+                    auto in_y = [&](int g) { return g >= 0 && g < p.ny; };
+                    const bool row_in = in_y(gy);
+                    if (!(row_in && in_x(gx) && in_x(gx + 1))) Lx.x = 0.f;
+                    if (!(row_in && in_x(gx + 1) && in_x(gx + 2))) Lx.y = 0.f;
+                    if (!(row_in && in_x(gx + 2) && in_x(gx + 3))) Lx.z = 0.f;
+                    if (!(row_in && in_x(gx + 3) && in_x(gx + 4))) Lx.w = 0.f;
+                    if (!(row_in && in_y(gy + 1))) Ly = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!(row_in && in_y(gy - 1))) Lu = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!in_x(gx)) Ly.x = Lu.x = 0.f;
+                    if (!in_x(gx + 1)) Ly.y = Lu.y = 0.f;
+                    if (!in_x(gx + 2)) Ly.z = Lu.z = 0.f;
+                    if (!in_x(gx + 3)) Ly.w = Lu.w = 0.f;
                 }
-                __syncthreads();
-                float *tmp = a;
-                a = b;
-                b = tmp;
             }
-            // the tile: rows HB .. TY - 1 - HB, columns HB .. TX - 1 - HB (lanes 1..30)
+            // the west face of the lane's first cell (every lane takes part in the
+            // shuffle; the region's column 0 is never exact, so lane 0 takes 0)
+            const float fwl = __shfl_up_sync(FULL, Lx.w, 1);
+            const float fw = lane > 0 ? fwl : 0.f;
+            const float4 C = lds4(sC + q), V = lds4(stV + q);
+            float *const p0 = sv + q, *const p1 = vb + q;  // the row in the two iterate planes
+            float4 c = lds4(p0);
+#pragma unroll
+            for (int j = 1; j <= HB; j++) {
+                if (j <= kk) {  // block-uniform
+                    const float *const src = (j & 1) ? p0 : p1;
+                    float *const dst = (j & 1) ? p1 : p0;
+                    if (ry >= j && ry <= TY - 1 - j) {  // warp-uniform
+                        const float tb = s_tb[m0 + j - 1], rd = s_rd[m0 + j - 1];
+                        // x neighbours of the lane's first and last cells (lanes 0 and
+                        // 31 take any finite value: columns 0 and TX - 1 are never exact)
+                        const float aw = __shfl_up_sync(FULL, c.w, 1), ae = __shfl_down_sync(FULL, c.x, 1);
+                        float4 l;  // the Laplacian: x faces, the face above, the face below
+                        l.x = Lx.x * (c.y - c.x) - fw * (c.x - aw);
+                        l.y = Lx.y * (c.z - c.y) - Lx.x * (c.y - c.x);
+                        l.z = Lx.z * (c.w - c.z) - Lx.y * (c.z - c.y);
+                        l.w = Lx.w * (ae - c.w) - Lx.z * (c.w - c.z);
+                        {
+                            const float4 u = lds4(src - TX);
+                            l.x -= Lu.x * (c.x - u.x);
+                            l.y -= Lu.y * (c.y - u.y);
+                            l.z -= Lu.z * (c.z - u.z);
+                            l.w -= Lu.w * (c.w - u.w);
+                        }
+                        {
+                            const float4 d = lds4(src + TX);
+                            l.x += Ly.x * (d.x - c.x);
+                            l.y += Ly.y * (d.y - c.y);
+                            l.z += Ly.z * (d.z - c.z);
+                            l.w += Ly.w * (d.w - c.w);
+                        }
+                        c.x = (C.x + tb * c.x + V.x * l.x) * rd;
+                        c.y = (C.y + tb * c.y + V.y * l.y) * rd;
+                        c.z = (C.z + tb * c.z + V.z * l.z) * rd;
+                        c.w = (C.w + tb * c.w + V.w * l.w) * rd;
+                        if (j < kk) sts4(dst, c);  // the last sweep's rows leave from registers
+                    }
+                    if (j < kk) __syncthreads();
+                }
+            }
+            // the tile: rows HB .. TY - 1 - HB, columns HB .. TX - 1 - HB (lanes 1..30),
+            // updated by every sweep of the round
             if (ry >= HB && ry < TY - HB && lane >= 1 && lane < 31) {
                 const int gx = gx0 + cx, gy = gy0 + ry;
-                if (gx < p.nx && gy < p.ny)
-                    *reinterpret_cast<float4 *>(vout + (size_t)gy * p.nx + gx) = lds4(a + q);
+                if (gx < p.nx && gy < p.ny) *reinterpret_cast<float4 *>(vout + (size_t)gy * p.nx + gx) = c;
             }
             __syncthreads();  // the region buffers are refilled for the block's next tiles
         }
