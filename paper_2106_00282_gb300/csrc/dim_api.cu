@@ -399,24 +399,28 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud
     if (Ud_in) TIMED(c, K_WAVE, dimk::launch_wave_ff_in(p, f, Ud_in, cur, c->sc, c->stream));
     else TIMED(c, K_WAVE, dimk::launch_wave_ff(p, f, cur, c->sc, c->stream));
     *out_done = false;
+    // the last hyperbolic sweep of a step with a viscous stage also records max
+    // 1/rho and max mu, from which the viscous kernel that follows may certify
+    // P = 1 without its lambda pass
     if (sx) {
-        TIMED(c, K_SWEEP_X, dimk::launch_sweep_ff(p, f, 0, cur, oth, 0.0, c->sc, 1, last == LAST_SX, c->stream));
+        TIMED(c, K_SWEEP_X, dimk::launch_sweep_ff_bound(p, f, 0, cur, oth, 0.0, c->sc, 1, last == LAST_SX,
+                                                        vis && !sy, c->stream));
         float2 *t = cur; cur = oth; oth = t;
     }
     if (sy) {
-        TIMED(c, K_SWEEP_Y, dimk::launch_sweep_ff(p, f, 1, cur, oth, 0.0, c->sc, 1, last == LAST_SY, c->stream));
+        TIMED(c, K_SWEEP_Y,
+              dimk::launch_sweep_ff_bound(p, f, 1, cur, oth, 0.0, c->sc, 1, last == LAST_SY, vis, c->stream));
         float2 *t = cur; cur = oth; oth = t;
     }
     if (vis) {
         if (sx) {
             TIMED(c, K_VISC_X,
-                  dimk::launch_visc_ff(p, f, 0, cur, oth, c->S, c->sc, 0.0, !sy, last == LAST_VX, sy ? 1 : 0,
-                                       c->stream));
+                  dimk::launch_visc_ff(p, f, 0, cur, oth, c->S, c->sc, 0.0, !sy, last == LAST_VX, 3, c->stream));
             float2 *t = cur; cur = oth; oth = t;
         }
         if (sy) {
             TIMED(c, K_VISC_Y, dimk::launch_visc_ff(p, f, 1, cur, oth, c->S, c->sc, 0.0, 1, last == LAST_VY,
-                                                    sx ? 2 : 0, c->stream));
+                                                    sx ? 2 : 3, c->stream));
             float2 *t = cur; cur = oth; oth = t;
         }
     }

@@ -110,14 +110,15 @@ __global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f,
     }
 }
 
-template <int AXIS, int TN, int TL>
+template <int AXIS, int TN, int TL, bool BOUND>
 __global__ void __launch_bounds__(TN *TL) k_sweepff(const DevParams p, const FFP f, const float2 *__restrict__ Uin,
                                                     float2 *__restrict__ Uout, double dt_host, Scalars *sc,
                                                     int relax, int check)
 {
     extern __shared__ float4 smem_ff[];
     const float dtdx = block_dt(sc, dt_host) * (AXIS == 0 ? f.idx : f.idy);
-    sweepff_tile<AXIS, TN, TL>(p, f, Uin, Uout, dtdx, sc, relax, check, blockIdx.x * TN, blockIdx.y * TL, smem_ff);
+    sweepff_tile<AXIS, TN, TL, BOUND>(p, f, Uin, Uout, dtdx, sc, relax, check, blockIdx.x * TN, blockIdx.y * TL,
+                                      smem_ff);
 }
 
 // pointwise relaxation in place: DIM_RELAX_PRESSURE (Sec. 3.3) or
@@ -424,6 +425,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
             smem_u32(dst)),
         "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(smem_u32(b))
         : "memory");
+}
+
+// bulk copy of `bytes` (a multiple of 16) from global src to shared dst, both
+// 16-byte aligned, completing on the mbarrier
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"((unsigned long long)src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
 }
 
 // the descriptors of the planes a round reads (addresses in the kernel's
@@ -771,11 +782,18 @@ struct ViscFF {
 // With P = 1 (no predictor sweep, u_hat = u^n) the last sweep reads the state
 // directly and no scratch plane is written.  Out of place: the stage reads U
 // and writes all 8 planes of Uo (the last sweep reads neighbours' momenta).
+// staged conservative sweep of the viscous kernels: chunk of VB cells (the
+// block size), window capacity VW cells (the chunk, 2 either side, rounding to
+// even bounds), two buffers of NQ planes
+constexpr int VB = 256, VW = VB + 8;
+constexpr size_t VISC_SMEM = sizeof(float2) * 2 * NQ * VW;
+
 template <int AXIS>
 __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, const float2 *__restrict__ U,
                                                 float2 *__restrict__ Uo, ViscFF s, Scalars *sc, double dt_host,
                                                 int relax, int check, int lam_mode)
 {
+    extern __shared__ float4 smem_visc[];
     __shared__ float s_tb[2 * PMAX], s_rd[2 * PMAX];
     constexpr int QN = AXIS == 0 ? 2 : 3, QT = AXIS == 0 ? 3 : 2;
     constexpr int SLOT = AXIS == 0 ? LAM_VX : LAM_VY;
@@ -808,9 +826,24 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
         cm = AXIS == 0 ? nb.xm : nb.ym;
         cp = AXIS == 0 ? nb.xp : nb.yp;
     };
-    if (lam_mode != 2) {
-        // lambda_max of this axis; lam_mode 1: also that of the other axis, whose
-        // solve follows on a state with the same densities and fractions
+    // lam_mode 3: sc->vbound holds the minimum density of this state (the step's
+    // last sweep).  The mixture viscosity a_1 mu_1 + a_2 mu_2 is at most max(mu_1,
+    // mu_2), every face coefficient at most 4/3 of that, so lambda_max of either
+    // axis is at most 16/3 max(mu_k) / rho_min max(1/h^2); when twice that still
+    // gives P = 1, both solves have P = 1, whose one Chebyshev coefficient is 0
+    // whatever lambda_max is: the lambda pass is skipped (the accumulators stay 0,
+    // from which P = 1 follows here and in the other axis's kernel).
+    bool certified = false;
+    if (lam_mode == 3 && sc->vbound != 0u) {
+        const double rmin = (double)__uint_as_float(0x7f800000u - sc->vbound);
+        const double ih2max = fmax(p.nx > 1 ? (double)f.idx2 : 0.0, p.ny > 1 ? (double)f.idy2 : 0.0);
+        const double lb = 2.0 * (16.0 / 3.0) * fmax((double)f.mu[0], (double)f.mu[1]) / rmin * ih2max;
+        unsigned cp;
+        certified = rmin > 0.0 && isfinite(lb) && cheb_P_visc(p, tau, lb, cp) == 1;
+    }
+    if (lam_mode != 2 && !certified) {
+        // lambda_max of this axis; lam_mode 1 or 3: also that of the other axis,
+        // whose solve follows on a state with the same densities and fractions
         constexpr int OSLOT = AXIS == 0 ? LAM_VY : LAM_VX;
         const float ih2o = AXIS == 0 ? f.idy2 : f.idx2;
         float lm = 0.f, lmo = 0.f;
@@ -828,7 +861,7 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
             const float fl = cm >= 0 ? 0.5f * (4.f / 3.f * mu_at(cm) + lc) : 0.f;
             const float fr = cp >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_at(cp)) : 0.f;
             lm = fmaxf(lm, 2.f * ir * ((fl + fr) * ih2));
-            if (lam_mode == 1) {
+            if (lam_mode != 0) {
                 const int om = AXIS == 0 ? nb.ym : nb.xm, op = AXIS == 0 ? nb.yp : nb.xp;
                 const float gl = om >= 0 ? 0.5f * (4.f / 3.f * mu_at(om) + lc) : 0.f;
                 const float gr = op >= 0 ? 0.5f * (lc + 4.f / 3.f * mu_at(op)) : 0.f;
@@ -836,7 +869,7 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
             }
         }
         block_max_to_f(&sc->lam[SLOT], lm);
-        if (lam_mode == 1) block_max_to_f(&sc->lam[OSLOT], lmo);
+        if (lam_mode != 0) block_max_to_f(&sc->lam[OSLOT], lmo);
         if (!grid_barrier(sc)) return;
     }
     unsigned capped;
@@ -894,18 +927,11 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
             alpha_at(c, a1, a2);
         }
     };
-    for (int c = t0; c < n; c += nt) {
-        if (threadIdx.x == 0 && c + nt < n) {  // the block's next chunk of the state
-            const size_t c0 = (size_t)c + nt, c1 = min(c0 + blockDim.x, (size_t)n);
-#pragma unroll
-            for (int k = 0; k < NQ; k++) l2_prefetch(U + k * (size_t)n, c0, c1);
-        }
+    // the conservative last sweep of cell c, whose 8 planes are in q[]; nb(cn,
+    // u, w, a1, a2) gives a neighbour's velocities and fractions
+    auto last_sweep = [&](int c, ff *q, auto &&nb) {
         int cm, cp;
         nbs(c, cm, cp);
-        // the cell's state first (one round trip), its velocities and fractions from it
-        ff q[NQ];
-#pragma unroll
-        for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
         float uc, wc, a1c, a2c;
         if (P > 1) {
             cell(c, uc, wc, a1c, a2c);
@@ -926,7 +952,7 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
                 continue;
             }
             float un, wn, a1n, a2n;
-            cell(cn, un, wn, a1n, a2n);
+            nb(cn, un, wn, a1n, a2n);
             const float lmf = 0.5f * (mc + (a1n * mu0 + a2n * mu1));
             // face between cl and cr: cl = cn, cr = c on the minus side
             const float du = sd == 0 ? uc - un : un - uc, dw = sd == 0 ? wc - wn : wn - wc;
@@ -952,6 +978,101 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
         if (check) st |= ff_check(f, q);
 #pragma unroll
         for (int k = 0; k < NQ; k++) st_ff(Uo, k * (size_t)n + c, q[k]);
+    };
+    // P = 1 with an even cell count: the state arrives in shared memory by bulk
+    // copies, one chunk of VB cells (with 2 cells either side) per block
+    // iteration, two buffers, the next chunk's copies issued before the current
+    // one is swept; neighbours outside the window (across rows) are read from
+    // global memory.  Otherwise the loop reads the planes directly.
+    float2 *const vbuf = reinterpret_cast<float2 *>(smem_visc);
+    if (P == 1 && (n & 1) == 0 && (smem_u32(vbuf) & 15u) == 0) {
+        __shared__ __align__(8) unsigned long long v_bar[2];
+        __shared__ int v_fail;
+        const int nch = (n + VB - 1) / VB;
+        auto window = [&](int ch, int &w0, int &w1) {  // even bounds: 16-byte aligned copies
+            const int c0 = ch * VB;
+            w0 = max(c0 - 2, 0) & ~1;
+            w1 = min(c0 + VB + 2, n);
+            w1 = (w1 + 1) & ~1;  // <= n (n even)
+        };
+        auto issue = [&](int ch, int buf) {  // one thread
+            int w0, w1;
+            window(ch, w0, w1);
+            const unsigned bytes = (unsigned)(w1 - w0) * (unsigned)sizeof(float2);
+            unsigned long long *bar = buf ? &v_bar[1] : &v_bar[0];
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, NQ * bytes);
+#pragma unroll
+            for (int k = 0; k < NQ; k++)
+                bulk_load(vbuf + (buf * NQ + k) * VW, U + k * (size_t)n + w0, bytes, bar);
+        };
+        if (threadIdx.x == 0) {
+            mbar_init(&v_bar[0], 1);
+            mbar_init(&v_bar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if ((int)blockIdx.x < nch) issue(blockIdx.x, 0);
+        }
+        __syncthreads();
+        unsigned use0 = 0u, use1 = 0u;
+        int k = 0;
+        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x, k++) {
+            const int buf = k & 1;
+            const unsigned ub = buf ? use1 : use0, uo = buf ? use0 : use1;
+            if (threadIdx.x == 0) {
+                v_fail = 0;
+                if (ch + (int)gridDim.x < nch) issue(ch + gridDim.x, buf ^ 1);
+                if (!mbar_wait(buf ? &v_bar[1] : &v_bar[0], ub & 1u)) v_fail = 1;
+            }
+            __syncthreads();
+            if (v_fail) {  // give up: flag, let the other buffer's copies land (bounded), leave
+                if (threadIdx.x == 0) {
+                    atomicOr(&sc->status, DIM_ST_TIMEOUT);
+                    if (ch + (int)gridDim.x < nch) mbar_wait(buf ? &v_bar[0] : &v_bar[1], uo & 1u);
+                }
+                return;
+            }
+            if (buf) use1++;
+            else use0++;
+            int w0, w1;
+            window(ch, w0, w1);
+            const float2 *const sb = vbuf + buf * NQ * VW;
+            const int c = ch * VB + threadIdx.x;
+            if (c < n) {
+                ff q[NQ];
+#pragma unroll
+                for (int kq = 0; kq < NQ; kq++) {
+                    const float2 v = sb[kq * VW + (c - w0)];
+                    q[kq] = ff{v.x, v.y};
+                }
+                last_sweep(c, q, [&](int cn, float &u, float &w, float &a1, float &a2) {
+                    if (cn >= w0 && cn < w1) {  // the same arithmetic as cell()
+                        const float2 *e = sb + (cn - w0);
+                        const float rho = ff_f(ff{e[0].x, e[0].y}) + ff_f(ff{e[VW].x, e[VW].y});
+                        u = __fdividef(ff_f(ff{e[QN * VW].x, e[QN * VW].y}), rho);
+                        w = __fdividef(ff_f(ff{e[QT * VW].x, e[QT * VW].y}), rho);
+                        const ff a{e[7 * VW].x, e[7 * VW].y};
+                        a2 = ff_f(a);
+                        a1 = ff_f(ff_sub(ff_one(), a));
+                    } else {
+                        cell(cn, u, w, a1, a2);
+                    }
+                });
+            }
+            __syncthreads();  // the buffer is refilled for the block's chunk after next
+        }
+    } else {
+        for (int c = t0; c < n; c += nt) {
+            if (threadIdx.x == 0 && c + nt < n) {  // the block's next chunk of the state
+                const size_t c0 = (size_t)c + nt, c1 = min(c0 + blockDim.x, (size_t)n);
+#pragma unroll
+                for (int k = 0; k < NQ; k++) l2_prefetch(U + k * (size_t)n, c0, c1);
+            }
+            // the cell's state first (one round trip), its velocities and fractions from it
+            ff q[NQ];
+#pragma unroll
+            for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * (size_t)n + c);
+            last_sweep(c, q, cell);
+        }
     }
     flag(sc, st);
 }
@@ -1008,11 +1129,13 @@ FFP ffp_of(const DevParams &p)
 // the sweep kernels' shared-memory limit (once per device)
 cudaError_t sweepff_setup()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sweepff<0, SXF_TN, SXF_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sweepff_smem(SXF_TN, SXF_TL));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sweepff<1, SYF_TN, SYF_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweepff_smem(SYF_TN, SYF_TL));
+    const int smx = (int)sweepff_smem(SXF_TN, SXF_TL), smy = (int)sweepff_smem(SYF_TN, SYF_TL);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_sweepff<0, SXF_TN, SXF_TL, false>, at, smx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweepff<0, SXF_TN, SXF_TL, true>, at, smx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweepff<1, SYF_TN, SYF_TL, false>, at, smy);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweepff<1, SYF_TN, SYF_TL, true>, at, smy);
+    return e;
 }
 
 cudaError_t bulkff_setup(int nsm)
@@ -1030,10 +1153,10 @@ cudaError_t bulkff_setup(int nsm)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff<true>, HEAT_THREADS_TMA, LIM_SMEM_TMA);
     if (e != cudaSuccess) return e;
     g_heatff_blocks[1] = b * nsm;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<0>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<0>, 256, VISC_SMEM);
     if (e != cudaSuccess) return e;
     g_viscff_blocks[0] = b * nsm;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<1>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<1>, 256, VISC_SMEM);
     if (e != cudaSuccess) return e;
     g_viscff_blocks[1] = b * nsm;
     return cudaSuccess;
@@ -1071,19 +1194,34 @@ cudaError_t launch_wave_ff_in(const DevParams &p, const FFP &f, const double *Ud
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep_ff_bound(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
+                                  double dt_host, Scalars *sc, int relax, int check, int bound, cudaStream_t s)
+{
+    const size_t smx = sweepff_smem(SXF_TN, SXF_TL), smy = sweepff_smem(SYF_TN, SYF_TL);
+    if (axis == 0) {
+        dim3 grid((p.nx + SXF_TN - 1) / SXF_TN, (p.ny + SXF_TL - 1) / SXF_TL);
+        if (bound)
+            k_sweepff<0, SXF_TN, SXF_TL, true><<<grid, SXF_TN * SXF_TL, smx, s>>>(p, f, Uin, Uout, dt_host, sc, relax,
+                                                                                check);
+        else
+            k_sweepff<0, SXF_TN, SXF_TL, false><<<grid, SXF_TN * SXF_TL, smx, s>>>(p, f, Uin, Uout, dt_host, sc,
+                                                                                 relax, check);
+    } else {
+        dim3 grid((p.ny + SYF_TN - 1) / SYF_TN, (p.nx + SYF_TL - 1) / SYF_TL);
+        if (bound)
+            k_sweepff<1, SYF_TN, SYF_TL, true><<<grid, SYF_TN * SYF_TL, smy, s>>>(p, f, Uin, Uout, dt_host, sc, relax,
+                                                                                check);
+        else
+            k_sweepff<1, SYF_TN, SYF_TL, false><<<grid, SYF_TN * SYF_TL, smy, s>>>(p, f, Uin, Uout, dt_host, sc,
+                                                                                 relax, check);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_ff(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
                             double dt_host, Scalars *sc, int relax, int check, cudaStream_t s)
 {
-    if (axis == 0) {
-        dim3 grid((p.nx + SXF_TN - 1) / SXF_TN, (p.ny + SXF_TL - 1) / SXF_TL);
-        k_sweepff<0, SXF_TN, SXF_TL><<<grid, SXF_TN * SXF_TL, sweepff_smem(SXF_TN, SXF_TL), s>>>(
-            p, f, Uin, Uout, dt_host, sc, relax, check);
-    } else {
-        dim3 grid((p.ny + SYF_TN - 1) / SYF_TN, (p.nx + SYF_TL - 1) / SYF_TL);
-        k_sweepff<1, SYF_TN, SYF_TL><<<grid, SYF_TN * SYF_TL, sweepff_smem(SYF_TN, SYF_TL), s>>>(
-            p, f, Uin, Uout, dt_host, sc, relax, check);
-    }
-    return cudaGetLastError();
+    return launch_sweep_ff_bound(p, f, axis, Uin, Uout, dt_host, sc, relax, check, 0, s);
 }
 
 cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars *sc, int which, int check,
@@ -1167,7 +1305,8 @@ cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, const flo
     void *args[] = {(void *)&pp,      (void *)&ff_,   (void *)&U,     (void *)&Uo,      (void *)&vs,
                     (void *)&sc,      (void *)&dt_host, (void *)&relax, (void *)&check, (void *)&lam_mode};
     const void *fn = axis == 0 ? (const void *)k_viscff<0> : (const void *)k_viscff<1>;
-    return cudaLaunchCooperativeKernel(fn, dim3(coop_grid(g_viscff_blocks[axis], p.n)), dim3(256), args, 0, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(coop_grid(g_viscff_blocks[axis], p.n)), dim3(256), args, VISC_SMEM,
+                                       st);
 }
 
 }  // namespace dimk

@@ -29,6 +29,8 @@ cudaError_t launch_wave_ff_in(const DevParams &p, const FFP &f, const double *Ud
                               cudaStream_t s);
 cudaError_t launch_sweep_ff(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
                             double dt_host, Scalars *sc, int relax, int check, cudaStream_t s);
+cudaError_t launch_sweep_ff_bound(const DevParams &p, const FFP &f, int axis, const float2 *Uin, float2 *Uout,
+                                  double dt_host, Scalars *sc, int relax, int check, int bound, cudaStream_t s);
 cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars *sc, int which, int check,
                             cudaStream_t s);
 int heat_tma_setup(const DevParams &p, double *S, LimMaps *m);

@@ -51,6 +51,10 @@ struct Scalars {
     unsigned long long smax;     // max (|u|+c)/h of the step (bits of a non-negative double)
     unsigned long long lam[12];  // Gershgorin lambda_max per LIM solve (heat iterations 0..7, viscous x, y)
     int P[12];                   // Chebyshev parameter count used: [0] heat, [1] viscous x, [2] viscous y
+    // FP32-bulk form: the minimum density of the state after the step's last
+    // hyperbolic sweep, as bits(+inf) - bits(rho_min) (0: none recorded); it
+    // bounds lambda_max of the viscous solves
+    unsigned int vbound;
     float dt32;                  // FP32-bulk form: cfl / smax, written once per step by the CFL kernel
     unsigned int wave_blocks;    // FP32-bulk form: blocks of the CFL kernel that have finished
     unsigned int bar_count;      // grid barrier: arrivals of the current generation

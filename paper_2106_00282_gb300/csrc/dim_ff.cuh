@@ -414,6 +414,19 @@ __device__ __forceinline__ void block_max_to_f(unsigned long long *acc, float v)
     }
 }
 
+// warp-wide minimum of positive floats (NaN ignored) into an accumulator that
+// holds bits(+inf) - bits(min) (a max accumulator, 0 when empty: the map is
+// decreasing for positive floats), without a block barrier; the atomic is
+// issued only when the warp's value improves on the accumulator's, which after
+// the first warps of a launch it rarely does
+__device__ __forceinline__ void warp_min_pos_bits(unsigned *acc, float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const unsigned key = 0x7f800000u - __float_as_uint(v);
+    if ((threadIdx.x & 31) == 0 && v > 0.f && key > *(volatile unsigned *)acc) atomicMax(acc, key);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 face arithmetic of the sweep (MUSCL + HLLC), as the FP64 kernel but in
 // FP32 on the thermal and kinetic energies (the cold energies travel with the
@@ -529,7 +542,9 @@ __host__ __device__ constexpr size_t sweepff_smem(int TN, int TL)
 // (alpha_2, m_1, m_2, u_n, u_t, p_1, p_2), HLLC fluxes, the update with the
 // non-conservative term R(U_i) du* (Sec. 3.1), and the pressure relaxation
 // (Sec. 3.3) when relax != 0.  dtdx = dt / h of the axis.  States in FF planes.
-template <int AXIS, int TN, int TL>
+// BOUND: also the minimum density of the updated cells into sc->vbound (the
+// last sweep of a step that runs the viscous stage)
+template <int AXIS, int TN, int TL, bool BOUND = false>
 __device__ __forceinline__ void sweepff_tile(const DevParams &p, const FFP &f, const float2 *Uin, float2 *Uout,
                                              float dtdx, Scalars *sc, int relax, int check, int a0, int t0,
                                              void *smem)
@@ -640,6 +655,7 @@ __device__ __forceinline__ void sweepff_tile(const DevParams &p, const FFP &f, c
     __syncthreads();
 
     unsigned st = 0;
+    float rmin = __int_as_float(0x7f800000);  // +inf
     for (int oi = threadIdx.x; oi < TN * TL; oi += blockDim.x) {
         int i, l;
         if (AXIS == 0) {
@@ -684,12 +700,14 @@ __device__ __forceinline__ void sweepff_tile(const DevParams &p, const FFP &f, c
             st |= s & DIM_ST_NAN;
         }
         if (check) st |= ff_check(f, o);
+        if constexpr (BOUND) rmin = fminf(rmin, ff_f(o[0]) + ff_f(o[1]));  // the viscous kernels' rho
         const int x = AXIS == 0 ? al : tr, y = AXIS == 0 ? tr : al;
         const size_t c = (size_t)y * p.nx + x;
 #pragma unroll
         for (int k = 0; k < NQ; k++) st_ff(Uout, k * (size_t)n + c, o[k]);
     }
     flag(sc, st);
+    if constexpr (BOUND) warp_min_pos_bits(&sc->vbound, rmin);
     __syncthreads();  // the shared tile is reused by the next tile of a persistent block
 }
 
