@@ -317,10 +317,12 @@ __device__ __forceinline__ unsigned ff_prelax(const FFP &f, ff *q)
 // the common pressure.  With y = p + pinf_2 and B_1 = pinf_1 - pinf_2 it is the
 // quadratic C y^2 + (C B_1 - G_1 C_1 W_1 - G_2 C_2 W_2) y - G_2 C_2 W_2 B_1 = 0,
 // whose middle coefficient cancels to about -C p where a stiff phase dominates:
-// it is formed in FF, the positive root taken in FP32, and one Newton step on
-// F evaluated in FF gives y to FF precision.  Then g_k = G_k C_k / (p + pinf_k),
-// T = 1 / (g_1 + g_2), a_2 = g_2 / (g_1 + g_2) (the minor phase's fraction
-// directly, the major one as 1 - minor), and
+// it is formed in FF, the positive root taken in FP32, and in mixed cells one
+// Newton step on F evaluated in FF gives y to FF precision.  Then
+// g_k = G_k C_k / (p + pinf_k), T = 1 / (g_1 + g_2), a_2 = g_2 / (g_1 + g_2) (the
+// minor phase's fraction directly, the major one as 1 - minor; in FF in mixed
+// cells, from FP32 quotients where the minor fraction is below kNewtonFraction),
+// and
 // E_k = a_k p / (g_k - 1) + a_k cold_k, the second E_k = rho e - the first.
 // Returns T (FP32), a_2 and the phase energies.
 __device__ __forceinline__ unsigned ff_equilibrium(const FFP &f, ff m1, ff m2, ff rhoe, float &T, ff &a2n, ff &E1,
@@ -347,18 +349,28 @@ __device__ __forceinline__ unsigned ff_equilibrium(const FFP &f, ff m1, ff m2, f
     // Newton step on F in FF, in mixed cells (the minor fraction g_m / (g_1 + g_2)
     // estimated in FP32 from the root)
     const float g1e = __fdividef(ff_f(GC1), ff_f(Y1)), g2e = __fdividef(ff_f(GC2), y);
+    bool minor2;
     if (fminf(g1e, g2e) >= kNewtonFraction * (g1e + g2e)) {
         const ff t1 = ff_div(GW1, Y1), t2 = ff_div(GW2, Y2);
         const float dF = -__fdividef(ff_f(t1), ff_f(Y1)) - __fdividef(ff_f(t2), y);
         const float dy = -__fdividef(ff_f(ff_sub(ff_add(t1, t2), C)), dF);
         Yb = ff_add_f(Y2, dy);
         Ya = ff_add_f(Y1, dy);
+        const ff g1 = ff_div(GC1, Ya), g2 = ff_div(GC2, Yb);
+        const ff gs = ff_add(g1, g2);
+        T = __fdividef(1.f, ff_f(gs));
+        minor2 = ff_f(g2) <= ff_f(g1);
+        a2n = minor2 ? ff_div(g2, gs) : ff_sub(ff_one(), ff_div(g1, gs));
+    } else {
+        // a nearly pure cell: T and the minor fraction from the FP32 quotients
+        // (their FP32 digits are all the state keeps of a fraction below
+        // kNewtonFraction), the major fraction as 1 - minor in FF
+        const float gs = g1e + g2e;
+        T = __fdividef(1.f, gs);
+        minor2 = g2e <= g1e;
+        const float am = __fdividef(minor2 ? g2e : g1e, gs);
+        a2n = minor2 ? ff_of(am) : ff_add_f(ff_one(), -am);
     }
-    const ff g1 = ff_div(GC1, Ya), g2 = ff_div(GC2, Yb);
-    const ff gs = ff_add(g1, g2);
-    T = __fdividef(1.f, ff_f(gs));
-    const bool minor2 = ff_f(g2) <= ff_f(g1);
-    a2n = minor2 ? ff_div(g2, gs) : ff_sub(ff_one(), ff_div(g1, gs));
     const ff a1n = ff_sub(ff_one(), a2n);
     const float p = ff_f(ff_sub(Yb, f.pinf_ff[1]));  // y - pinf_2
     if (minor2) {
