@@ -147,3 +147,53 @@ def test_viscous_update_by_hand_with_alpha_gradient(O, I):
     # (the face weights are not the cell fractions)
     dE = U1[4, 0] - U[4, 0] + U1[5, 0] - U[5, 0]
     assert np.max(np.abs((U1[5, 0] - U[5, 0]) - a2 * dE)) > 1e-3 * np.abs(dE).max()
+
+
+def _visc_P(O, params, U, dx, dy, axis, tau):
+    return O.viscous(params, U, dx, dy, axis, tau)[2]
+
+
+def test_viscous_P1_certificate_bound(O, I):
+    """The FP32-bulk step skips the exact viscous lambda_max pass when a bound
+    proves P = 1.  The mixture viscosity a_1 mu_1 + a_2 mu_2 is at most max mu_k,
+    so every face coefficient is at most 4/3 of it, and the Gershgorin bound of
+    the viscous operator (Sec. 3.2) gives lambda_max <= 16/3 max(mu_k) / rho_min
+    max(1/h^2).  With P = ceil(pi/4 sqrt(tau lambda + 1)), P = 1 exactly when
+    tau lambda <= (4/pi)^2 - 1.  The oracle's own choice of P pins the bound: at
+    the time step where twice the bound meets that limit, the oracle chooses
+    P = 1 on heterogeneous states along either axis.  A uniform state, where the
+    bound is attained, shows it is tight: P = 2 once tau lambda_bound passes
+    the limit."""
+    lim = (4.0 / math.pi) ** 2 - 1.0
+    rng = np.random.default_rng(7)
+    nx, ny = 24, 16
+    dx, dy = 1.0 / nx, 0.5 / ny
+    ih2 = max(1.0 / dx ** 2, 1.0 / dy ** 2)
+    for mu in ((1e-3, 1.8e-5), (500.0, 1.0), (0.2, 3.0)):
+        params = I.Params(gamma=(4.4, 1.4), pinf=(6e8, 0.0), cv=(950.0, 718.0), mu=mu, bc=(0, 1),
+                          p_policy=I.P_FORMULA, p_max=24)
+        prim = np.zeros((5, ny, nx))
+        prim[0] = rng.uniform(1e-6, 1.0 - 1e-6, size=(ny, nx))
+        prim[1] = rng.uniform(5e4, 5e5, size=(ny, nx))
+        prim[2] = rng.uniform(250.0, 3000.0, size=(ny, nx))
+        prim[3] = rng.uniform(-50.0, 50.0, size=(ny, nx))
+        prim[4] = rng.uniform(-50.0, 50.0, size=(ny, nx))
+        U = O.from_primitive(params, prim)
+        rho = U[0] + U[1]
+        lam_b = 16.0 / 3.0 * max(mu) / rho.min() * ih2
+        tau = lim / (2.0 * lam_b)
+        for axis in (0, 1):
+            assert _visc_P(O, params, U, dx, dy, axis, tau) == 1, (mu, axis)
+    # uniform state, periodic x: every face coefficient is 4/3 mu, lambda_max equals the bound
+    params = I.Params(gamma=(1.4, 1.4), pinf=(0.0, 0.0), cv=(714.0, 714.0), mu=(0.5, 0.5), bc=(1, 1),
+                      p_policy=I.P_FORMULA, p_max=24)
+    prim = np.zeros((5, 1, 64))
+    prim[0] = 0.5
+    prim[1] = 1e5
+    prim[2] = 300.0
+    U = O.from_primitive(params, prim)
+    rho = U[0, 0, 0] + U[1, 0, 0]
+    h = 1.0 / 64
+    lam_b = 16.0 / 3.0 * 0.5 / rho / h ** 2
+    assert _visc_P(O, params, U, h, h, 0, 0.99 * lim / lam_b) == 1
+    assert _visc_P(O, params, U, h, h, 0, 1.01 * lim / lam_b) == 2
