@@ -36,7 +36,7 @@ extern "C" {
                              m_k <= 0, p + pinf_k <= 0, or a NaN */
 #define DIM_ENOROOT (-4)  /* a relaxation quadratic had no real root */
 #define DIM_ETIMEOUT (-5) /* a bounded grid-wide wait inside a kernel gave up */
-#define DIM_ENOTIMPL (-6) /* entry point not implemented in this build */
+#define DIM_ENOTIMPL (-6) /* entry point not implemented by this library */
 #define DIM_ETOOLARGE (-7) /* grid larger than the fixed scratch of dim_hllc_sweep_noalloc */
 
 /* device status word bits (dim_status) */
