@@ -70,6 +70,10 @@ CASES = {
     # not a multiple of 4 floats (the transmissive 2D cases above load by TMA)
     "conduction_periodic_96": lambda I: _with(I.conduction_disc(n=96), bc=(I.BC_PERIODIC, I.BC_PERIODIC)),
     "conduction_98": lambda I: I.conduction_disc(n=98),
+    # TMA rounds on a grid lower than one region (most of each box beyond the
+    # walls), with P fixed so that the blocked sweeps run
+    "thin_tma_128x12": lambda I: _with(I.smooth_mixture(128, 12, bc=(I.BC_TRANSMISSIVE, I.BC_TRANSMISSIVE)),
+                                       p_policy=I.P_FIXED, p_fixed=4),
 }
 
 
