@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f,
 }
 
 template <int AXIS, int TN, int TL, bool BOUND>
-__global__ void __launch_bounds__(TN *TL) k_sweepff(const DevParams p, const FFP f, const float2 *__restrict__ Uin,
+// one thread per staged cell (TN + 4 along the sweep): the load phase takes one
+// cell per thread
+__global__ void __launch_bounds__((TN + 4) * TL) k_sweepff(const DevParams p, const FFP f, const float2 *__restrict__ Uin,
                                                     float2 *__restrict__ Uout, double dt_host, Scalars *sc,
                                                     int relax, int check)
 {
@@ -1080,8 +1082,8 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
 // ---------------------------------------------------------------------------
 // host side: constants, set-up, launchers
 // ---------------------------------------------------------------------------
-constexpr int SXF_TN = 128, SXF_TL = 1;
-constexpr int SYF_TN = 32, SYF_TL = 8;
+constexpr int SXF_TN = 124, SXF_TL = 1;
+constexpr int SYF_TN = 28, SYF_TL = 8;
 
 static int g_heatff_blocks[2] = {0, 0}, g_viscff_blocks[2] = {0, 0};
 
@@ -1201,19 +1203,19 @@ cudaError_t launch_sweep_ff_bound(const DevParams &p, const FFP &f, int axis, co
     if (axis == 0) {
         dim3 grid((p.nx + SXF_TN - 1) / SXF_TN, (p.ny + SXF_TL - 1) / SXF_TL);
         if (bound)
-            k_sweepff<0, SXF_TN, SXF_TL, true><<<grid, SXF_TN * SXF_TL, smx, s>>>(p, f, Uin, Uout, dt_host, sc, relax,
-                                                                                check);
+            k_sweepff<0, SXF_TN, SXF_TL, true><<<grid, (SXF_TN + 4) * SXF_TL, smx, s>>>(p, f, Uin, Uout, dt_host, sc,
+                                                                                      relax, check);
         else
-            k_sweepff<0, SXF_TN, SXF_TL, false><<<grid, SXF_TN * SXF_TL, smx, s>>>(p, f, Uin, Uout, dt_host, sc,
-                                                                                 relax, check);
+            k_sweepff<0, SXF_TN, SXF_TL, false><<<grid, (SXF_TN + 4) * SXF_TL, smx, s>>>(p, f, Uin, Uout, dt_host,
+                                                                                       sc, relax, check);
     } else {
         dim3 grid((p.ny + SYF_TN - 1) / SYF_TN, (p.nx + SYF_TL - 1) / SYF_TL);
         if (bound)
-            k_sweepff<1, SYF_TN, SYF_TL, true><<<grid, SYF_TN * SYF_TL, smy, s>>>(p, f, Uin, Uout, dt_host, sc, relax,
-                                                                                check);
+            k_sweepff<1, SYF_TN, SYF_TL, true><<<grid, (SYF_TN + 4) * SYF_TL, smy, s>>>(p, f, Uin, Uout, dt_host, sc,
+                                                                                      relax, check);
         else
-            k_sweepff<1, SYF_TN, SYF_TL, false><<<grid, SYF_TN * SYF_TL, smy, s>>>(p, f, Uin, Uout, dt_host, sc,
-                                                                                 relax, check);
+            k_sweepff<1, SYF_TN, SYF_TL, false><<<grid, (SYF_TN + 4) * SYF_TL, smy, s>>>(p, f, Uin, Uout, dt_host,
+                                                                                       sc, relax, check);
     }
     return cudaGetLastError();
 }
