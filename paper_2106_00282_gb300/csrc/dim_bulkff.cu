@@ -1082,6 +1082,8 @@ __global__ void __launch_bounds__(256) k_viscff(const DevParams p, const FFP f, 
 // ---------------------------------------------------------------------------
 // host side: constants, set-up, launchers
 // ---------------------------------------------------------------------------
+// sweep tiles: TN cells along the sweep, TL lines; a block has (TN + 4) TL
+// threads, one per staged cell (128 along x, 256 along y)
 constexpr int SXF_TN = 124, SXF_TL = 1;
 constexpr int SYF_TN = 28, SYF_TL = 8;
 
