@@ -382,7 +382,11 @@ static int step_once(dim_ctx *c, double *U, StepMarks *mk = nullptr)
 // (may be null): the CFL kernel converts this FP64 state into *cur first.
 // Ud_out (may be null): the heat kernel, if the step ends with it, writes the
 // end state there in FP64; *out_done tells whether it did.
-static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud_in, double *Ud_out, bool *out_done)
+// cfl_ready: the previous step's heat kernel formed this step's CFL maximum and
+// time step (no CFL kernel); *cfl_formed: this step's heat kernel forms the
+// next one's (requested by cfl_next)
+static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud_in, double *Ud_out, bool *out_done,
+                        bool cfl_ready, bool cfl_next, bool *cfl_formed)
 {
     const dim_params &h = c->hp;
     const DevParams &p = c->p;
@@ -395,9 +399,17 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud
     else if (vis) last = sy ? LAST_VY : LAST_VX;
     else last = sy ? LAST_SY : LAST_SX;
 
-    TRY(reset_accumulators(c));
-    if (Ud_in) TIMED(c, K_WAVE, dimk::launch_wave_ff_in(p, f, Ud_in, cur, c->sc, c->stream));
-    else TIMED(c, K_WAVE, dimk::launch_wave_ff(p, f, cur, c->sc, c->stream));
+    *cfl_formed = false;
+    if (cfl_ready && !Ud_in) {
+        // this step's smax and dt32 are in place: clear the other accumulators only
+        if (cudaMemsetAsync(c->sc->lam, 0, offsetof(Scalars, dt32) - offsetof(Scalars, lam), c->stream) !=
+            cudaSuccess)
+            return DIM_ECUDA;
+    } else {
+        TRY(reset_accumulators(c));
+        if (Ud_in) TIMED(c, K_WAVE, dimk::launch_wave_ff_in(p, f, Ud_in, cur, c->sc, c->stream));
+        else TIMED(c, K_WAVE, dimk::launch_wave_ff(p, f, cur, c->sc, c->stream));
+    }
     *out_done = false;
     // the last hyperbolic sweep of a step with a viscous stage also records max
     // 1/rho and max mu, from which the viscous kernel that follows may certify
@@ -425,8 +437,9 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud
         }
     }
     if (heat) {
-        TIMED(c, K_HEAT,
-              dimk::launch_heat_ff(p, f, cur, c->S, c->sc, 0.0, 1, 1, c->stream, Ud_out, &c->lim, c->lim_tma));
+        TIMED(c, K_HEAT, dimk::launch_heat_ff(p, f, cur, c->S, c->sc, 0.0, 1, 1, c->stream, Ud_out, &c->lim,
+                                              c->lim_tma, cfl_next ? 1 : 0));
+        *cfl_formed = cfl_next;
         *out_done = Ud_out != nullptr;
     } else if (trx) {
         TIMED(c, K_RELAX, dimk::launch_relax_ff(p, f, cur, c->sc, DIM_RELAX_TEMPERATURE, 1, c->stream));
@@ -441,10 +454,13 @@ static int step_once_ff(dim_ctx *c, float2 *&cur, float2 *&oth, const double *Ud
 static int steps_ff(dim_ctx *c, double *U, int nsteps)
 {
     float2 *cur = c->Uf, *oth = ff_other(c);
-    bool out_done = false;
+    bool out_done = false, ready = false;
     for (int s = 0; s < nsteps; s++) {
-        int r = step_once_ff(c, cur, oth, s == 0 ? U : nullptr, s == nsteps - 1 ? U : nullptr, &out_done);
+        bool formed = false;
+        int r = step_once_ff(c, cur, oth, s == 0 ? U : nullptr, s == nsteps - 1 ? U : nullptr, &out_done, ready,
+                             s < nsteps - 1, &formed);
         if (r != DIM_OK) return r;
+        ready = formed;
     }
     if (!out_done) TIMED(c, K_CONVERT, dimk::launch_ff_out(cur, U, state_len(c), c->stream));
     return DIM_OK;
@@ -458,6 +474,9 @@ static cudaError_t clear_barrier_if_timeout(dim_ctx *c, unsigned st)
     if (!(st & DIM_ST_TIMEOUT)) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(&c->sc->bar_count, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&c->sc->bar_gen, 0, sizeof(unsigned), c->stream);
+    // and the FP32-bulk heat kernel's next-step CFL accumulator and block count
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->sc->smax_next, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->sc->heat_blocks, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e;
 }
@@ -587,7 +606,7 @@ int dim_cheb_parabolic(dim_ctx *c, double *U, int kind, double dt, int *P_used)
         if (f32) {
             TIMED(c, K_CONVERT, dimk::launch_ff_in(U, c->Uf, state_len(c), c->stream));
             TIMED(c, K_HEAT, dimk::launch_heat_ff(c->p, c->ffp, c->Uf, c->S, c->sc, dt, 0, 0, c->stream, nullptr,
-                                                  &c->lim, c->lim_tma));
+                                                  &c->lim, c->lim_tma, 0));
             TIMED(c, K_CONVERT, dimk::launch_ff_out(c->Uf, U, state_len(c), c->stream));
         } else {
             TIMED(c, K_HEAT, run_heat(c, U, dt, 0, 0));

@@ -57,6 +57,34 @@ __device__ __forceinline__ void l2_prefetch(const T *plane, size_t i0, size_t i1
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
 }
 
+// max over the active axes of (|u_axis| + c)/h_axis for one FF state (Sec. 3.1,
+// the mixture sound speed of Eq. AK), NaN flagged in st: the per-cell arithmetic
+// of the CFL kernel, shared with the heat kernel that forms the next step's
+// maximum.  Every operation after the phase pressures is an intrinsic, which
+// the compiler never contracts, so both kernels round it alike and give the
+// same time step.
+__device__ __forceinline__ float ff_wave_speed(const DevParams &p, const FFP &f, const ff *q, unsigned &st)
+{
+    const ff a1 = ff_sub(ff_one(), q[7]);
+    const float p1 = ff_phase_p(f, 0, q[4], a1), p2 = ff_phase_p(f, 1, q[5], q[7]);
+    const float rho = __fadd_rn(ff_f(q[0]), ff_f(q[1]));
+    const float A1 = __fmul_rn(__fmul_rn(ff_f(a1), f.g[0]), __fadd_rn(p1, f.pinf[0]));
+    const float A2 = __fmul_rn(__fmul_rn(ff_f(q[7]), f.g[1]), __fadd_rn(p2, f.pinf[1]));
+    const float cs = sqrtf(__fdividef(__fadd_rn(A1, A2), rho));
+    float m = 0.f;
+    if (p.nx > 1) {
+        const float s = __fmul_rn(__fadd_rn(fabsf(__fdividef(ff_f(q[2]), rho)), cs), f.idx);
+        m = fmaxf(m, s);
+        if (isnan(s)) st |= DIM_ST_NAN;
+    }
+    if (p.ny > 1) {
+        const float s = __fmul_rn(__fadd_rn(fabsf(__fdividef(ff_f(q[3]), rho)), cs), f.idy);
+        m = fmaxf(m, s);
+        if (isnan(s)) st |= DIM_ST_NAN;
+    }
+    return m;
+}
+
 // CFL bound (Sec. 3.1) and input check.  FROM_D: the state is read from the
 // caller's FP64 planes Ud and written to the FF planes U on the way (the first
 // step of a call), instead of a separate conversion pass.
@@ -79,20 +107,7 @@ __global__ void __launch_bounds__(256) k_wave_ff(const DevParams p, const FFP f,
             }
         }
         st |= ff_check(f, q);
-        const ff a1 = ff_sub(ff_one(), q[7]);
-        const float p1 = ff_phase_p(f, 0, q[4], a1), p2 = ff_phase_p(f, 1, q[5], q[7]);
-        const float rho = ff_f(q[0]) + ff_f(q[1]);
-        const float cs = ff_sound(f, ff_f(a1), ff_f(q[7]), p1, p2, rho);
-        if (p.nx > 1) {
-            const float s = (fabsf(__fdividef(ff_f(q[2]), rho)) + cs) * f.idx;
-            m = fmaxf(m, s);
-            if (isnan(s)) st |= DIM_ST_NAN;
-        }
-        if (p.ny > 1) {
-            const float s = (fabsf(__fdividef(ff_f(q[3]), rho)) + cs) * f.idy;
-            m = fmaxf(m, s);
-            if (isnan(s)) st |= DIM_ST_NAN;
-        }
+        m = fmaxf(m, ff_wave_speed(p, f, q, st));
     }
     block_max_to_f(&sc->smax, m);
     flag(sc, st);
@@ -634,7 +649,10 @@ __device__ __forceinline__ bool lim_rounds_tma(const DevParams &p, const FFP &f,
 // separate conversion pass
 // TMA: the rounds of lim_rounds_tma (blocks of HEAT_THREADS_TMA threads), else
 // those of lim_rounds (HEAT_THREADS)
-template <bool TMA>
+// CFL: the kernel also forms the next step's CFL maximum and time step (a step
+// inside a multi-step call); a separate instantiation, so that the others keep
+// their code
+template <bool TMA, bool CFL>
 __global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
     k_heatff(const DevParams p, const FFP f, float2 *U, HeatFF s, Scalars *sc, double dt_host, int trelax_first,
              int check, double *Ud, const __grid_constant__ LimMaps tm)
@@ -685,6 +703,7 @@ __global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
         s.tV[c] = tauf * V;
         s.C0[c] = T + tauf * V * Ia;
     }
+    float mcfl = 0.f;  // CFL: the next step's CFL maximum over this block's cells
     for (int it = 0; it < nout; it++) {
         if (!grid_barrier(sc)) return;
         float lm = 0.f;
@@ -721,9 +740,12 @@ __global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
                 q[5] = E2n;
                 q[6] = ff_add_f(ld_ff(U, 6 * (size_t)n + c), dq);
                 q[7] = a2;
-                if (Ud) {
+                if (Ud || CFL) {
                     q[2] = ld_ff(U, 2 * (size_t)n + c);
                     q[3] = ld_ff(U, 3 * (size_t)n + c);
+                }
+                if constexpr (CFL) mcfl = fmaxf(mcfl, ff_wave_speed(p, f, q, st));
+                if (Ud) {
 #pragma unroll
                     for (int k = 0; k < NQ; k++) Ud[k * (size_t)n + c] = ff_to_d(q[k]);
                 } else {
@@ -745,7 +767,7 @@ __global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
             l2_prefetch(U + 4 * (size_t)n, c0, c1);
             l2_prefetch(U + 5 * (size_t)n, c0, c1);
             l2_prefetch(U + 6 * (size_t)n, c0, c1);
-            if (last && Ud) {
+            if (last && (Ud || CFL)) {
                 l2_prefetch(U + 2 * (size_t)n, c0, c1);
                 l2_prefetch(U + 3 * (size_t)n, c0, c1);
             }
@@ -753,6 +775,26 @@ __global__ void __launch_bounds__(TMA ? HEAT_THREADS_TMA : HEAT_THREADS)
             l2_prefetch(vin, c0, c1);
             l2_prefetch(s.L, c0, c1);
         });
+        if (CFL && last) {
+            // the next step's maximum (Sec. 3.1) from this step's end state; the last
+            // block to finish publishes it and dt = cfl / S for the next step (every
+            // block read this step's time step at its start)
+            block_max_to_f(&sc->smax_next, mcfl);
+            __shared__ bool s_last_h;
+            if (threadIdx.x == 0) {
+                __threadfence();
+                s_last_h = atomicAdd(&sc->heat_blocks, 1u) == gridDim.x - 1;
+            }
+            __syncthreads();
+            if (s_last_h && threadIdx.x == 0) {
+                __threadfence();
+                sc->smax = *(volatile unsigned long long *)&sc->smax_next;
+                sc->dt32 = (float)(p.cfl / read_acc(&sc->smax));
+                sc->smax_next = 0ull;
+                sc->heat_blocks = 0u;
+                __threadfence();
+            }
+        }
         if (!last) {
             if (!grid_barrier(sc)) return;
             for (int c = t0; c < n; c += nt) {
@@ -1142,19 +1184,31 @@ cudaError_t sweepff_setup()
     return e;
 }
 
+// co-resident blocks of a heat kernel: the smaller of its two CFL instantiations
+template <bool TMA>
+static cudaError_t heat_blocks_per_sm(int *b)
+{
+    const int threads = TMA ? HEAT_THREADS_TMA : HEAT_THREADS;
+    const size_t smem = TMA ? LIM_SMEM_TMA : LIM_SMEM;
+    int b0 = 0, b1 = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_heatff<TMA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_heatff<TMA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_heatff<TMA, false>, threads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_heatff<TMA, true>, threads, smem);
+    *b = b0 < b1 ? b0 : b1;
+    return e;
+}
+
 cudaError_t bulkff_setup(int nsm)
 {
     cudaError_t e = sweepff_setup();
     if (e != cudaSuccess) return e;
     int b = 0;
-    e = cudaFuncSetAttribute(k_heatff<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIM_SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff<false>, HEAT_THREADS, LIM_SMEM);
+    e = heat_blocks_per_sm<false>(&b);
     if (e != cudaSuccess) return e;
     g_heatff_blocks[0] = b * nsm;
-    e = cudaFuncSetAttribute(k_heatff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIM_SMEM_TMA);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_heatff<true>, HEAT_THREADS_TMA, LIM_SMEM_TMA);
+    e = heat_blocks_per_sm<true>(&b);
     if (e != cudaSuccess) return e;
     g_heatff_blocks[1] = b * nsm;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_viscff<0>, 256, VISC_SMEM);
@@ -1281,7 +1335,8 @@ int heat_tma_setup(const DevParams &p, double *S, LimMaps *m)
 }
 
 cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
-                           int trelax_first, int check, cudaStream_t st, double *Ud, const LimMaps *tm, int use_tma)
+                           int trelax_first, int check, cudaStream_t st, double *Ud, const LimMaps *tm, int use_tma,
+                           int cfl_next)
 {
     HeatFF hs = heat_planes(p, S);
     DevParams pp = p;
@@ -1293,7 +1348,10 @@ cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *
                     (void *)&dt_host, (void *)&trelax_first, (void *)&check, (void *)&Ud, (void *)&maps};
     const int threads = use_tma ? HEAT_THREADS_TMA : HEAT_THREADS, maxb = g_heatff_blocks[use_tma ? 1 : 0];
     const int need = (p.n + threads - 1) / threads;
-    return cudaLaunchCooperativeKernel(use_tma ? (const void *)k_heatff<true> : (const void *)k_heatff<false>,
+    // the grid fits both CFL instantiations (the smaller occupancy of the two)
+    const void *fn = use_tma ? (cfl_next ? (const void *)k_heatff<true, true> : (const void *)k_heatff<true, false>)
+                             : (cfl_next ? (const void *)k_heatff<false, true> : (const void *)k_heatff<false, false>);
+    return cudaLaunchCooperativeKernel(fn,
                                        dim3(need < maxb ? need : maxb), dim3(threads), args,
                                        use_tma ? LIM_SMEM_TMA : LIM_SMEM, st);
 }

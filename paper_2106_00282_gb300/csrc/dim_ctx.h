@@ -35,7 +35,8 @@ cudaError_t launch_relax_ff(const DevParams &p, const FFP &f, float2 *U, Scalars
                             cudaStream_t s);
 int heat_tma_setup(const DevParams &p, double *S, LimMaps *m);
 cudaError_t launch_heat_ff(const DevParams &p, const FFP &f, float2 *U, double *S, Scalars *sc, double dt_host,
-                           int trelax_first, int check, cudaStream_t st, double *Ud, const LimMaps *tm, int use_tma);
+                           int trelax_first, int check, cudaStream_t st, double *Ud, const LimMaps *tm, int use_tma,
+                           int cfl_next);
 cudaError_t launch_visc_ff(const DevParams &p, const FFP &f, int axis, const float2 *U, float2 *Uo, double *S,
                            Scalars *sc, double dt_host, int relax, int check, int lam_mode, cudaStream_t st);
 }  // namespace dimk

@@ -60,6 +60,11 @@ struct Scalars {
     unsigned int bar_count;      // grid barrier: arrivals of the current generation
     unsigned int status;         // DIM_ST_* bits
     unsigned int bar_gen;        // grid barrier: generation
+    // FP32-bulk form, outside the per-step reset: a heat kernel that also forms
+    // the next step's CFL maximum accumulates it here and counts its finished
+    // blocks; the last one moves it to smax (with dt32) and clears both
+    unsigned long long smax_next;
+    unsigned int heat_blocks;
 };
 constexpr int LAM_VX = 8, LAM_VY = 9;
 
