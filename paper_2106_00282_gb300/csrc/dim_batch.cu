@@ -87,14 +87,7 @@ __device__ void stage_wave(const BatchDev &d)
 #pragma unroll
             for (int k = 0; k < NQ; k++) q[k] = ld_ff(U, k * n + c);
             st |= ff_check(f, q);
-            const ff a1 = ff_sub(ff_one(), q[7]);
-            const float p1 = ff_phase_p(f, 0, q[4], a1), p2 = ff_phase_p(f, 1, q[5], q[7]);
-            const float rho = ff_f(q[0]) + ff_f(q[1]);
-            const float cs = ff_sound(f, ff_f(a1), ff_f(q[7]), p1, p2, rho);
-            const float sx = (fabsf(__fdividef(ff_f(q[2]), rho)) + cs) * f.idx;
-            const float sy = (fabsf(__fdividef(ff_f(q[3]), rho)) + cs) * f.idy;
-            m = fmaxf(m, fmaxf(sx, sy));
-            if (isnan(sx) || isnan(sy)) st |= DIM_ST_NAN;
+            m = fmaxf(m, ff_wave_speed(d.prm[i], f, q, st));  // the per-grid CFL kernel's arithmetic
         }
         block_max_to_f(&d.sc[i].smax, m);
         flag(&d.sc[i], st);

@@ -209,6 +209,34 @@ __device__ __forceinline__ float ff_cond(const FFP &f, int k, float T)
     return f.k0[k] * __powf(t, f.k_exp);
 }
 
+// max over the active axes of (|u_axis| + c)/h_axis for one FF state (Sec. 3.1,
+// the mixture sound speed of Eq. AK), NaN flagged in st: the per-cell arithmetic
+// of the CFL kernel, of the heat kernel that forms the next step's maximum and
+// of the batched step.  Every operation after the phase pressures is an
+// intrinsic, which the compiler never contracts, so all of them round it alike
+// and give the same time step.
+__device__ __forceinline__ float ff_wave_speed(const DevParams &p, const FFP &f, const ff *q, unsigned &st)
+{
+    const ff a1 = ff_sub(ff_one(), q[7]);
+    const float p1 = ff_phase_p(f, 0, q[4], a1), p2 = ff_phase_p(f, 1, q[5], q[7]);
+    const float rho = __fadd_rn(ff_f(q[0]), ff_f(q[1]));
+    const float A1 = __fmul_rn(__fmul_rn(ff_f(a1), f.g[0]), __fadd_rn(p1, f.pinf[0]));
+    const float A2 = __fmul_rn(__fmul_rn(ff_f(q[7]), f.g[1]), __fadd_rn(p2, f.pinf[1]));
+    const float cs = sqrtf(__fdividef(__fadd_rn(A1, A2), rho));
+    float m = 0.f;
+    if (p.nx > 1) {
+        const float s = __fmul_rn(__fadd_rn(fabsf(__fdividef(ff_f(q[2]), rho)), cs), f.idx);
+        m = fmaxf(m, s);
+        if (isnan(s)) st |= DIM_ST_NAN;
+    }
+    if (p.ny > 1) {
+        const float s = __fmul_rn(__fadd_rn(fabsf(__fdividef(ff_f(q[3]), rho)), cs), f.idy);
+        m = fmaxf(m, s);
+        if (isnan(s)) st |= DIM_ST_NAN;
+    }
+    return m;
+}
+
 // end-of-step admissibility of an FF state (q in the global plane order):
 // alpha_2 and alpha_1 = 1 - alpha_2 positive, m_k > 0, E_k > alpha_k pinf_k, no NaN
 __device__ __forceinline__ unsigned ff_check(const FFP &f, const ff *q)
